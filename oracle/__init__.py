@@ -1,0 +1,207 @@
+"""GED-Walk CPU oracle: a ctypes front-end to oracle.c (double and long double).
+
+TEST INFRASTRUCTURE ONLY. The oracle restates the paper's definitions in plain, slow
+C so that the CUDA library can be checked against it. Only ``tests/``,
+``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may import it; the
+library never does, and the oracle never imports the library.
+
+Graphs are any object with ``row_ptr`` (int32[n+1]) and ``col_idx`` (int32[nnz]) numpy
+arrays describing an undirected CSR. Every routine cites the passage it follows in
+oracle_impl.inc / oracle.c.
+
+Parity status: every routine here is pinned by tests/test_oracle.py (brute force,
+closed forms, propositions, long-double agreement); none is "parity unpinned".
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRCS = [os.path.join(_HERE, "oracle.c"), os.path.join(_HERE, "oracle_impl.inc")]
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_f64p = ctypes.POINTER(ctypes.c_double)
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain C11, no vendor code, portable to x86 and Arm)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    newest = max(os.path.getmtime(s) for s in _SRCS)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRCS[0], "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            G = [ctypes.c_int32, _i32p, _i32p]
+            lib.orc_dmax.restype = ctypes.c_int32
+            lib.orc_dmax.argtypes = [ctypes.c_int32, _i32p]
+            lib.orc_walk_totals_d.restype = ctypes.c_int
+            lib.orc_walk_totals_d.argtypes = G + [ctypes.c_double, ctypes.c_int32, _f64p, _f64p]
+            lib.orc_select_L_d.restype = ctypes.c_int32
+            lib.orc_select_L_d.argtypes = G + [ctypes.c_double, ctypes.c_double, ctypes.c_int32, _f64p]
+            lib.orc_comb_bound_d.restype = ctypes.c_double
+            lib.orc_comb_bound_d.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_double]
+            lib.orc_score_d.restype = ctypes.c_double
+            lib.orc_score_d.argtypes = G + [_i32p, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, _f64p]
+            lib.orc_score_ld_as_d.restype = ctypes.c_double
+            lib.orc_score_ld_as_d.argtypes = G + [_i32p, ctypes.c_int32, ctypes.c_double, ctypes.c_int32]
+            lib.orc_score_by_complement_d.restype = ctypes.c_double
+            lib.orc_score_by_complement_d.argtypes = G + [_i32p, ctypes.c_int32, ctypes.c_double, ctypes.c_int32]
+            lib.orc_gain_d.restype = ctypes.c_double
+            lib.orc_gain_d.argtypes = G + [_i32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_int32]
+            lib.orc_gain_ld_as_d.restype = ctypes.c_double
+            lib.orc_gain_ld_as_d.argtypes = G + [_i32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                                 ctypes.c_int32]
+            lib.orc_upper_bounds_d.restype = ctypes.c_int
+            lib.orc_upper_bounds_d.argtypes = G + [_i32p, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, _f64p]
+            lib.orc_greedy_d.restype = ctypes.c_int
+            lib.orc_greedy_d.argtypes = G + [ctypes.c_int32, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
+                                             _i32p, ctypes.c_int32, _i32p, _f64p, _i64p]
+            lib.orc_brute_phi.restype = ctypes.c_int
+            lib.orc_brute_phi.argtypes = G + [_i32p, ctypes.c_int32, ctypes.c_int32, _u64p, _u64p]
+            lib.orc_brute_gain.restype = ctypes.c_int
+            lib.orc_brute_gain.argtypes = G + [_i32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _u64p]
+            _lib = lib
+    return _lib
+
+
+def _g(graph):
+    rp = np.ascontiguousarray(graph.row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(graph.col_idx, dtype=np.int32)
+    if ci.size == 0:
+        ci = np.zeros(1, dtype=np.int32)
+    return rp.shape[0] - 1, rp, ci
+
+
+def _ptr(a, t):
+    return a.ctypes.data_as(t)
+
+
+def _S(S):
+    s = np.ascontiguousarray(np.asarray(S if S is not None else [], dtype=np.int32).ravel())
+    if s.size == 0:
+        return np.zeros(1, dtype=np.int32), 0
+    return s, int(s.size)
+
+
+def dmax(graph) -> int:
+    n, rp, _ = _g(graph)
+    return int(_load().orc_dmax(n, _ptr(rp, _i32p)))
+
+
+def default_alpha(graph) -> float:
+    """alpha = 1/(1 + d_max): below 1/d_max, as the combinatorial bound requires (Sec. 3.1.2)."""
+    return 1.0 / (1.0 + dmax(graph))
+
+
+def walk_totals(graph, alpha: float, L: int):
+    """(t, Wa): t[r, x] = alpha^r omega_r(x) (Eq. katz-def terms), Wa[r] = alpha^r W_r."""
+    n, rp, ci = _g(graph)
+    t = np.zeros((L + 1, max(n, 1)), dtype=np.float64)
+    Wa = np.zeros(L + 1, dtype=np.float64)
+    rc = _load().orc_walk_totals_d(n, _ptr(rp, _i32p), _ptr(ci, _i32p), alpha, L, _ptr(t, _f64p), _ptr(Wa, _f64p))
+    if rc != 0:
+        raise MemoryError("oracle walk_totals failed")
+    return t[:, :n], Wa
+
+
+def comb_bound(graph, alpha: float, Wa_l: float) -> float:
+    """B_l of Eq. comb-bound from Wa_l = alpha^l W_l."""
+    return float(_load().orc_comb_bound_d(dmax(graph), alpha, Wa_l))
+
+
+def select_L(graph, alpha: float, eps: float, Lcap: int = 400):
+    """(L, B_L): smallest l >= 1 with B_l < eps (Algorithm 1 stop test). L = -1 if none."""
+    n, rp, ci = _g(graph)
+    B = ctypes.c_double(float("nan"))
+    L = _load().orc_select_L_d(n, _ptr(rp, _i32p), _ptr(ci, _i32p), alpha, eps, Lcap, ctypes.byref(B))
+    return int(L), float(B.value)
+
+
+def score(graph, S, alpha: float, L: int, terms: bool = False, long_double: bool = False):
+    """GED_{<=L}(S) by the two-state recurrences (Sec. 3.1.1). terms=True also returns alpha^i phi_i."""
+    n, rp, ci = _g(graph)
+    s, sl = _S(S)
+    lib = _load()
+    if long_double:
+        return float(lib.orc_score_ld_as_d(n, _ptr(rp, _i32p), _ptr(ci, _i32p), _ptr(s, _i32p), sl, alpha, L))
+    tv = np.zeros(L + 1, dtype=np.float64)
+    val = float(lib.orc_score_d(n, _ptr(rp, _i32p), _ptr(ci, _i32p), _ptr(s, _i32p), sl, alpha, L, _ptr(tv, _f64p)))
+    return (val, tv) if terms else val
+
+
+def score_by_complement(graph, S, alpha: float, L: int) -> float:
+    """GED_{<=L}(S) as sum_i alpha^i (W_i - M_i) (Def. ged-walk; cancels for small S)."""
+    n, rp, ci = _g(graph)
+    s, sl = _S(S)
+    return float(_load().orc_score_by_complement_d(n, _ptr(rp, _i32p), _ptr(ci, _i32p), _ptr(s, _i32p), sl,
+                                                   alpha, L))
+
+
+def gain(graph, S, x: int, alpha: float, L: int, long_double: bool = False) -> float:
+    """GED_{<=L}(S, x), counted directly as the weighted walks through x avoiding S."""
+    n, rp, ci = _g(graph)
+    s, sl = _S(S)
+    lib = _load()
+    f = lib.orc_gain_ld_as_d if long_double else lib.orc_gain_d
+    return float(f(n, _ptr(rp, _i32p), _ptr(ci, _i32p), _ptr(s, _i32p), sl, int(x), alpha, L))
+
+
+def upper_bounds(graph, S, alpha: float, L: int) -> np.ndarray:
+    """sum_{i<=L} alpha^i P_i(S, x) for every x (Lemma initialize)."""
+    n, rp, ci = _g(graph)
+    s, sl = _S(S)
+    ub = np.zeros(max(n, 1), dtype=np.float64)
+    _load().orc_upper_bounds_d(n, _ptr(rp, _i32p), _ptr(ci, _i32p), _ptr(s, _i32p), sl, alpha, L, _ptr(ub, _f64p))
+    return ub[:n]
+
+
+def greedy(graph, k: int, alpha: float, L: int, mode: str = "all", init=None):
+    """Greedy maximisation at fixed L: (group, gains, evaluations). mode 'all' or 'lazy'."""
+    n, rp, ci = _g(graph)
+    ini, il = _S(init)
+    group = np.zeros(max(k, 1), dtype=np.int32)
+    gains = np.zeros(max(k, 1), dtype=np.float64)
+    ev = ctypes.c_int64(0)
+    rc = _load().orc_greedy_d(n, _ptr(rp, _i32p), _ptr(ci, _i32p), k, alpha, L, 0 if mode == "all" else 1,
+                              _ptr(ini, _i32p), il, _ptr(group, _i32p), _ptr(gains, _f64p), ctypes.byref(ev))
+    if rc != 0:
+        raise ValueError("oracle greedy: invalid arguments")
+    return group[:k].copy(), gains[:k].copy(), int(ev.value)
+
+
+def brute_phi(graph, S, i: int):
+    """(phi_i(S), W_i) by enumerating every i-walk (exact integers)."""
+    n, rp, ci = _g(graph)
+    s, sl = _S(S)
+    phi, w = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    _load().orc_brute_phi(n, _ptr(rp, _i32p), _ptr(ci, _i32p), _ptr(s, _i32p), sl, i, ctypes.byref(phi),
+                          ctypes.byref(w))
+    return int(phi.value), int(w.value)
+
+
+def brute_gain(graph, S, x: int, i: int) -> int:
+    """Number of i-walks that visit x and avoid S, by enumeration."""
+    n, rp, ci = _g(graph)
+    s, sl = _S(S)
+    out = ctypes.c_uint64(0)
+    _load().orc_brute_gain(n, _ptr(rp, _i32p), _ptr(ci, _i32p), _ptr(s, _i32p), sl, int(x), i, ctypes.byref(out))
+    return int(out.value)

@@ -1,0 +1,119 @@
+/*
+ * GED-Walk CPU oracle (Angriman et al., "Group Centrality Maximization for
+ * Large-scale Graphs", ALENEX 2020).
+ *
+ * TEST INFRASTRUCTURE ONLY: a plain, slow, obviously correct restatement of the
+ * paper's definitions and recurrences, used to check the CUDA library. It
+ * shares no code, header, table or helper with the library and must never be
+ * linked into it; only tests/, the smoke check and the benchmark's CPU-baseline
+ * leg load it.
+ *
+ * The numeric routines live in oracle_impl.inc and are compiled twice: in
+ * double (suffix _d) and in long double (suffix _ld).
+ *
+ * Pins (see tests/test_oracle.py): brute-force walk enumeration on graphs of at
+ * most 12 vertices, closed forms (complete graph, star, cycle, path),
+ * Prop. katz-relation, monotonicity and submodularity (Prop. ged_submod), the
+ * Lemma-initialize upper bound and its equality at L = 1, exhaustive best
+ * groups for k <= 3, and double against long double.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define REAL double
+#define ORC(name) orc_##name##_d
+#include "oracle_impl.inc"
+#undef ORC
+#undef REAL
+
+#define REAL long double
+#define ORC(name) orc_##name##_ld
+#include "oracle_impl.inc"
+#undef ORC
+#undef REAL
+
+/* maximum degree (the d_max of Eq. comb-bound) */
+int32_t orc_dmax(int32_t n, const int32_t* rp) {
+  int32_t d = 0;
+  for (int32_t v = 0; v < n; ++v)
+    if (rp[v + 1] - rp[v] > d) d = rp[v + 1] - rp[v];
+  return d;
+}
+
+/*
+ * Brute force (Def. ed-walk): enumerate every walk (x_0, ..., x_i) with
+ * (x_{j-1}, x_j) in E by depth-first search and count, in exact integers, the
+ * walks that contain at least one vertex of S (phi_i(S)) and all walks (W_i).
+ * Exponential; for graphs of at most ~12 vertices and short lengths.
+ */
+static void brute_rec(const int32_t* rp, const int32_t* ci, const unsigned char* in, int32_t v, int32_t left,
+                      int hit, uint64_t* phi, uint64_t* all) {
+  if (left == 0) {
+    *all += 1;
+    if (hit) *phi += 1;
+    return;
+  }
+  for (int32_t j = rp[v]; j < rp[v + 1]; ++j) {
+    const int32_t u = ci[j];
+    brute_rec(rp, ci, in, u, left - 1, hit || in[u], phi, all);
+  }
+}
+
+int orc_brute_phi(int32_t n, const int32_t* rp, const int32_t* ci, const int32_t* S, int32_t s_len, int32_t i,
+                  uint64_t* phi_out, uint64_t* walks_out) {
+  unsigned char* in = (unsigned char*)calloc((size_t)(n > 0 ? n : 1), 1);
+  if (!in) return -1;
+  for (int32_t j = 0; j < s_len; ++j)
+    if (S[j] >= 0 && S[j] < n) in[S[j]] = 1;
+  uint64_t phi = 0, all = 0;
+  for (int32_t v = 0; v < n; ++v) brute_rec(rp, ci, in, v, i, in[v], &phi, &all);
+  free(in);
+  *phi_out = phi;
+  *walks_out = all;
+  return 0;
+}
+
+/*
+ * Brute force for the marginal gain: the number of i-walks that visit x and
+ * avoid S (proof of Prop. ged_submod), by enumeration.
+ */
+static void brute_gain_rec(const int32_t* rp, const int32_t* ci, const unsigned char* in, int32_t x, int32_t v,
+                           int32_t left, int seen, uint64_t* cnt) {
+  if (left == 0) {
+    if (seen) *cnt += 1;
+    return;
+  }
+  for (int32_t j = rp[v]; j < rp[v + 1]; ++j) {
+    const int32_t u = ci[j];
+    if (in[u]) continue;
+    brute_gain_rec(rp, ci, in, x, u, left - 1, seen || u == x, cnt);
+  }
+}
+
+int orc_brute_gain(int32_t n, const int32_t* rp, const int32_t* ci, const int32_t* S, int32_t s_len, int32_t x,
+                   int32_t i, uint64_t* out) {
+  unsigned char* in = (unsigned char*)calloc((size_t)(n > 0 ? n : 1), 1);
+  if (!in) return -1;
+  for (int32_t j = 0; j < s_len; ++j)
+    if (S[j] >= 0 && S[j] < n) in[S[j]] = 1;
+  uint64_t cnt = 0;
+  if (!in[x])
+    for (int32_t v = 0; v < n; ++v)
+      if (!in[v]) brute_gain_rec(rp, ci, in, x, v, i, v == x, &cnt);
+  free(in);
+  *out = cnt;
+  return 0;
+}
+
+/* long-double entry points exchange values as double for the ctypes wrapper */
+double orc_score_ld_as_d(int32_t n, const int32_t* rp, const int32_t* ci, const int32_t* S, int32_t s_len,
+                         double alpha, int32_t L) {
+  return (double)orc_score_ld(n, rp, ci, S, s_len, alpha, L, NULL);
+}
+
+double orc_gain_ld_as_d(int32_t n, const int32_t* rp, const int32_t* ci, const int32_t* S, int32_t s_len, int32_t x,
+                        double alpha, int32_t L) {
+  return (double)orc_gain_ld(n, rp, ci, S, s_len, x, alpha, L);
+}

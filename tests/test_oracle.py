@@ -1,0 +1,342 @@
+"""Pins for the CPU oracle: checks against what the paper and the mathematics fix.
+
+None of these compare the oracle with itself: brute-force walk enumeration, hand-derived
+walk counts (tests/golden/hand_walks.txt), closed forms, Prop. katz-relation evaluated by
+dense matrix powers, Prop. ged_submod, Lemma initialize, exhaustive optima and the
+long-double build bound each routine from outside.
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "hand_walks.txt")
+
+
+def _rel(a, b):
+    return abs(a - b) / max(abs(b), 1e-300)
+
+
+def _small_graphs():
+    out = []
+    for seed in range(8):
+        n = 5 + seed % 5
+        out.append(gg.random_graph_small(n, 0.45, seed))
+    out += [gg.complete(5), gg.star(4), gg.path(6), gg.cycle(5)]
+    return out
+
+
+def _parse_golden():
+    recs = []
+    for line in open(GOLDEN):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        f = [x.strip() for x in line.split(";")]
+        n = int(f[2])
+        edges = [tuple(int(v) for v in e.split("-")) for e in f[3].split(",")]
+        S = [int(v) for v in f[4].split(",")]
+        if f[0] == "phi":
+            recs.append(("phi", f[1], n, edges, S, None, [int(v) for v in f[5].split()]))
+        else:
+            recs.append(("gain", f[1], n, edges, S, int(f[5]), [int(v) for v in f[6].split()]))
+    return recs
+
+
+@pytest.mark.parametrize("rec", _parse_golden(), ids=lambda r: f"{r[0]}-{r[1]}-{r[4]}")
+def test_hand_enumerated_counts(rec):
+    kind, _, n, edges, S, x, want = rec
+    g = gg.from_edges(n, edges)
+    alpha = 0.5  # a power of two keeps alpha^i * count exact in binary floating point
+    for i, w in enumerate(want, start=1):
+        if kind == "phi":
+            assert oracle.brute_phi(g, S, i)[0] == w
+            _, terms = oracle.score(g, S, alpha, i, terms=True)
+            assert terms[i] == alpha ** i * w
+        else:
+            assert oracle.brute_gain(g, S, x, i) == w
+    if kind == "gain":
+        L = len(want)
+        assert oracle.gain(g, S, x, alpha, L) == sum(alpha ** i * w for i, w in enumerate(want, start=1))
+
+
+@pytest.mark.parametrize("gi", range(12))
+def test_two_state_recurrence_matches_brute_force(gi):
+    g = _small_graphs()[gi]
+    rng = np.random.default_rng(100 + gi)
+    alpha = 0.5
+    for _ in range(4):
+        s = int(rng.integers(0, g.n + 1))
+        S = sorted(rng.choice(g.n, size=s, replace=False).tolist())
+        L = 5
+        _, terms = oracle.score(g, S, alpha, L, terms=True)
+        for i in range(1, L + 1):
+            phi, _ = oracle.brute_phi(g, S, i)
+            assert terms[i] == alpha ** i * phi, (S, i)
+
+
+@pytest.mark.parametrize("n,s", [(4, 1), (6, 2), (7, 3), (9, 0), (9, 9)])
+def test_complete_graph_closed_form(n, s):
+    # walks avoiding S on K_n are exactly the walks of K_{n-s}: phi_i = n(n-1)^i - (n-s)(n-s-1)^i
+    g = gg.complete(n)
+    alpha = 0.125
+    L = 6
+    _, terms = oracle.score(g, list(range(s)), alpha, L, terms=True)
+    for i in range(1, L + 1):
+        want = n * (n - 1) ** i - (n - s) * max(n - s - 1, 0) ** i
+        assert terms[i] == alpha ** i * want
+
+
+def test_walk_total_closed_forms():
+    L = 8
+    # complete graph: n (n-1)^i
+    _, Wa = oracle.walk_totals(gg.complete(6), 1.0, L)
+    assert [round(w) for w in Wa[1:]] == [6 * 5 ** i for i in range(1, L + 1)]
+    # star K_{1,m}: m^ceil(i/2) + m^(floor(i/2)+1)
+    m = 5
+    _, Wa = oracle.walk_totals(gg.star(m), 1.0, L)
+    assert [round(w) for w in Wa[1:]] == [m ** math.ceil(i / 2) + m ** (i // 2 + 1) for i in range(1, L + 1)]
+    # cycle C_n: n 2^i
+    _, Wa = oracle.walk_totals(gg.cycle(7), 1.0, L)
+    assert [round(w) for w in Wa[1:]] == [7 * 2 ** i for i in range(1, L + 1)]
+    # path P_n: sum_k (1^T u_k)^2 (2 cos(k pi/(n+1)))^i with u_k the normalised sine eigenvectors
+    n = 6
+    _, Wa = oracle.walk_totals(gg.path(n), 1.0, L)
+    j = np.arange(1, n + 1)
+    for i in range(1, L + 1):
+        tot = 0.0
+        for k in range(1, n + 1):
+            u = np.sin(j * k * np.pi / (n + 1)) * math.sqrt(2.0 / (n + 1))
+            tot += u.sum() ** 2 * (2 * math.cos(k * math.pi / (n + 1))) ** i
+        assert abs(Wa[i] - tot) < 1e-9 * max(1.0, tot)
+
+
+@pytest.mark.parametrize("gi", range(12))
+def test_katz_relation(gi):
+    # Prop. katz-relation (1): GED(V) = sum_x KC(x); truncated at L both sides, with the Katz
+    # terms alpha^i (A^i 1)(x) taken from dense integer matrix powers
+    g = _small_graphs()[gi]
+    A = g.to_dense()
+    alpha = 1.0 / (1 + max(g.d_max, 1))
+    L = 7
+    katz = 0.0
+    Ai = np.eye(g.n, dtype=np.int64)
+    for i in range(1, L + 1):
+        Ai = Ai @ A
+        katz += alpha ** i * float(Ai.sum())
+    ged = oracle.score(g, list(range(g.n)), alpha, L)
+    assert _rel(ged, katz) < 1e-13
+
+
+def test_two_forms_and_long_double_agree():
+    g = gg.erdos_renyi(1000, 10, 1)
+    alpha = oracle.default_alpha(g)
+    L, _ = oracle.select_L(g, alpha, 1e-6)
+    rng = np.random.default_rng(42)
+    for _ in range(4):
+        S = rng.choice(g.n, size=5, replace=False)
+        a = oracle.score(g, S, alpha, L)
+        b = oracle.score(g, S, alpha, L, long_double=True)
+        c = oracle.score_by_complement(g, S, alpha, L)
+        assert _rel(a, b) < 1e-13
+        # the complement form cancels; its error is ~u * GED(V) / GED(S)
+        gv = oracle.score(g, np.arange(g.n), alpha, L)
+        assert abs(c - b) < 64 * 2.2e-16 * gv * L
+
+
+@pytest.mark.parametrize("gi", range(12))
+def test_gain_matches_brute_force_and_difference(gi):
+    g = _small_graphs()[gi]
+    rng = np.random.default_rng(7 + gi)
+    alpha = 0.25
+    L = 5
+    for _ in range(3):
+        s = int(rng.integers(0, g.n))
+        S = sorted(rng.choice(g.n, size=s, replace=False).tolist())
+        for x in range(g.n):
+            want = sum(alpha ** i * oracle.brute_gain(g, S, x, i) for i in range(1, L + 1))
+            got = oracle.gain(g, S, x, alpha, L)
+            assert got == want or _rel(got, want) < 1e-14
+            if x not in S:
+                diff = oracle.score(g, S + [x], alpha, L) - oracle.score(g, S, alpha, L)
+                assert abs(diff - got) <= 1e-13 * max(1.0, oracle.score(g, S + [x], alpha, L))
+            else:
+                assert got == 0.0
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_monotone_and_submodular(seed):
+    # Prop. ged_submod on random triples S subset T, x outside T
+    g = gg.erdos_renyi(40, 4, seed)
+    alpha = oracle.default_alpha(g)
+    L = 6
+    rng = np.random.default_rng(seed)
+    for _ in range(30):
+        t = int(rng.integers(1, 10))
+        T = rng.choice(g.n, size=t, replace=False).tolist()
+        S = T[: int(rng.integers(0, t + 1))]
+        rest = [v for v in range(g.n) if v not in T]
+        x = int(rng.choice(rest))
+        assert oracle.score(g, T, alpha, L) >= oracle.score(g, S, alpha, L) - 1e-15
+        assert oracle.gain(g, S, x, alpha, L) >= oracle.gain(g, T, x, alpha, L) - 1e-15
+
+
+@pytest.mark.parametrize("gi", range(12))
+def test_upper_bound_lemma_initialize(gi):
+    g = _small_graphs()[gi]
+    alpha = 1.0 / (1 + g.d_max)
+    rng = np.random.default_rng(gi)
+    S = sorted(rng.choice(g.n, size=int(rng.integers(0, g.n // 2 + 1)), replace=False).tolist())
+    for L in (1, 3, 6):
+        ub = oracle.upper_bounds(g, S, alpha, L)
+        for x in range(g.n):
+            gx = oracle.gain(g, S, x, alpha, L)
+            assert ub[x] >= gx * (1 - 1e-14)
+            if L == 1:  # P_1 counts each 1-walk through x once when there are no self-loops
+                assert abs(ub[x] - gx) <= 1e-15 * max(gx, 1e-300)
+            if x in S:
+                assert ub[x] == 0.0
+
+
+def test_upper_bound_brute_multiplicity():
+    # P_i counts walks through x weighted by the number of visits of x (proof of Lemma initialize)
+    g = gg.random_graph_small(6, 0.6, 3)
+    S = [0]
+    alpha = 1.0
+    for i in range(1, 5):
+        ub_i = oracle.upper_bounds(g, S, alpha, i) - (oracle.upper_bounds(g, S, alpha, i - 1) if i > 1 else 0)
+        inS = np.zeros(g.n, bool)
+        inS[S] = True
+        for x in range(g.n):
+            if inS[x]:
+                continue
+            cnt = 0
+            for walk in itertools.product(range(g.n), repeat=i + 1):
+                if any(inS[v] for v in walk):
+                    continue
+                if all(walk[j + 1] in g.col_idx[g.row_ptr[walk[j]]:g.row_ptr[walk[j] + 1]] for j in range(i)):
+                    cnt += walk.count(x)
+            assert round(ub_i[x]) == cnt
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_tail_bound_holds(seed):
+    # Eq. comb-bound: GED_{>l}(S) <= B_l; the true tail is taken from a long FP64 run
+    g = gg.erdos_renyi(60, 5, seed)
+    alpha = oracle.default_alpha(g)
+    S = list(range(0, 60, 7))
+    _, Wa = oracle.walk_totals(g, alpha, 12)
+    full = oracle.score(g, S, alpha, 400)
+    for l in range(1, 12):
+        tail = full - oracle.score(g, S, alpha, l)
+        assert tail <= oracle.comb_bound(g, alpha, Wa[l]) * (1 + 1e-12)
+    # and the whole-graph tail equals sum_{i>l} alpha^i W_i, also below the bound
+    fullV = oracle.score(g, list(range(60)), alpha, 400)
+    for l in range(1, 12):
+        tailV = fullV - oracle.score(g, list(range(60)), alpha, l)
+        assert tailV <= oracle.comb_bound(g, alpha, Wa[l]) * (1 + 1e-12)
+
+
+def test_select_L_is_first_crossing_and_monotone():
+    g = gg.erdos_renyi(1000, 10, 1)
+    alpha = oracle.default_alpha(g)
+    _, Wa = oracle.walk_totals(g, alpha, 60)
+    prev = 0
+    for eps in (1e-2, 1e-4, 1e-6, 1e-8, 1e-10):
+        L, B = oracle.select_L(g, alpha, eps)
+        assert L >= prev
+        prev = L
+        assert oracle.comb_bound(g, alpha, Wa[L]) < eps
+        assert L == 1 or oracle.comb_bound(g, alpha, Wa[L - 1]) >= eps
+    # alpha*dmax >= 1 voids the combinatorial bound
+    assert oracle.select_L(g, 1.0 / g.d_max, 1e-4)[0] == -1
+
+
+@pytest.mark.parametrize("kind,seed", [("er", 1), ("er", 2), ("ba", 3), ("ba", 4), ("rmat", 5)])
+def test_greedy_all_vertex_equals_lazy(kind, seed):
+    if kind == "er":
+        g = gg.erdos_renyi(300, 6, seed)
+    elif kind == "ba":
+        g = gg.barabasi_albert(300, 3, seed)
+    else:
+        g = gg.rmat(9, 8, seed=seed)
+    alpha = oracle.default_alpha(g)
+    L = 6
+    a = oracle.greedy(g, 8, alpha, L, "all")
+    b = oracle.greedy(g, 8, alpha, L, "lazy")
+    assert list(a[0]) == list(b[0])
+    assert np.allclose(a[1], b[1], rtol=1e-14, atol=0)
+    assert b[2] < a[2]  # the lazy mode evaluates fewer vertices
+
+
+def test_greedy_gains_are_score_differences_and_resume():
+    g = gg.erdos_renyi(200, 8, 3)
+    alpha = oracle.default_alpha(g)
+    L = 7
+    grp, gains, _ = oracle.greedy(g, 6, alpha, L, "lazy")
+    for j in range(6):
+        d = oracle.score(g, grp[: j + 1], alpha, L) - oracle.score(g, grp[:j], alpha, L)
+        assert _rel(gains[j], d) < 1e-12
+    # resuming from a prefix reproduces the rest
+    grp2, gains2, _ = oracle.greedy(g, 3, alpha, L, "lazy", init=grp[:3])
+    assert list(grp2) == list(grp[3:])
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_greedy_against_exhaustive_optimum(seed):
+    g = gg.random_graph_small(9, 0.35, 50 + seed)
+    alpha = 1.0 / (1 + max(g.d_max, 1))
+    L = 6
+    for k in (1, 2, 3):
+        grp, _, _ = oracle.greedy(g, k, alpha, L, "all")
+        best = max(oracle.score(g, list(c), alpha, L) for c in itertools.combinations(range(g.n), k))
+        got = oracle.score(g, list(grp), alpha, L)
+        # Prop. greedy_approx applies to the truncated objective (itself monotone submodular)
+        assert got >= (1 - 1 / math.e) * best - 1e-12
+        if k == 1:
+            assert abs(got - best) <= 1e-12 * best
+
+
+def test_greedy_tie_break_lowest_id():
+    # K_n: all gains tie exactly (alpha a power of two keeps the arithmetic exact)
+    g = gg.complete(7)
+    for mode in ("all", "lazy"):
+        grp, _, _ = oracle.greedy(g, 4, 0.125, 4, mode)
+        assert list(grp) == [0, 1, 2, 3]
+
+
+def test_greedy_small_alpha_follows_group_degree():
+    # Thm. hardness: for tiny alpha GED degrades to group degree, so every greedy pick covers the
+    # largest number of still-uncovered edges (ties among those are settled by the alpha^2 terms)
+    g = gg.erdos_renyi(50, 4, 9)
+    alpha = 1.0 / (g.n ** 3 + g.n + 1)
+    grp, _, _ = oracle.greedy(g, 6, alpha, 4, "all")
+    A = g.to_dense().astype(bool)
+    covered = np.zeros_like(A)
+    for v in grp:
+        new = lambda u: int((A[u] & ~covered[u]).sum())
+        assert new(v) == max(new(u) for u in range(g.n) if u not in grp[: list(grp).index(v)])
+        covered[v, :] = True
+        covered[:, v] = True
+
+
+def test_star_first_pick_is_centre():
+    g = gg.star(9)
+    grp, gains, _ = oracle.greedy(g, 2, 1.0 / 10, 5, "lazy")
+    assert grp[0] == 0
+    # with the centre in S every remaining gain is 0; the lowest id (leaf 1) follows
+    assert grp[1] == 1 and gains[1] == 0.0
+
+
+def test_empty_group_and_isolated_vertices():
+    g = gg.from_edges(6, [(0, 1), (1, 2)])  # vertices 3,4,5 isolated
+    alpha = 0.25
+    assert oracle.score(g, [], alpha, 5) == 0.0
+    assert oracle.score(g, [4], alpha, 5) == 0.0
+    assert oracle.gain(g, [], 3, alpha, 5) == 0.0
+    assert oracle.upper_bounds(g, [], alpha, 5)[3] == 0.0
