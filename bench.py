@@ -1,0 +1,334 @@
+#!/usr/bin/env python3
+"""GED-Walk benchmark: greedy maximisation, batched scoring and serving on one GB300.
+
+Default (no flags): the headline workload — greedy GED-Walk maximisation, k = 100, FP32
+walk vectors with FP64 sums, on an R-MAT graph of scale 22, edge factor 16 (a=0.57,
+b=c=0.19, d=0.05; symmetrised, deduplicated, self-loops removed, labels permuted),
+alpha = 1/(1+d_max), epsilon = 1e-4 (L from the bound at epsilon/k). One "step" is one
+whole maximisation with the graph resident in HBM. It prints ONE JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload rmat|ba|ba64|batch|serve|small]
+  python bench.py --impl reference ...   # the CPU oracle on this host's cores, same metric
+
+Metric: GTEPS = k * 2L * nnz / seconds (per greedy step the method must at least
+recompute the L walk vectors for the new group and the L walk columns of the chosen
+vertex; each such sweep traverses every directed entry once).
+Multi-GPU: the path does not shard; every rank runs an independent replica (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "greedy k=100 seconds & GTEPS, % HBM peak; group-score queries/s, p50/p99"
+L2_BYTES = 129 * 2 ** 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rmat", choices=["rmat", "ba", "ba64", "batch", "serve", "small"])
+    ap.add_argument("--scale", type=int, default=22, help="R-MAT scale (22 is the configured size)")
+    ap.add_argument("--k", type=int, default=100)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- workloads
+def workload_spec(args):
+    if args.workload == "rmat":
+        return dict(name=f"R-MAT scale {args.scale}, edge factor 16 (0.57/0.19/0.19/0.05), greedy k={args.k} FP32",
+                    kind="greedy", graph=("rmat", args.scale), k=args.k, precision="fp32", eps=1e-4)
+    if args.workload in ("ba", "ba64"):
+        prec = "fp64" if args.workload == "ba64" else "fp32"
+        return dict(name=f"Barabasi-Albert n=1M m=8, greedy k={args.k} {prec.upper()}", kind="greedy",
+                    graph=("ba", 1_000_000, 8), k=args.k, precision=prec, eps=1e-4)
+    if args.workload == "small":
+        return dict(name="Erdos-Renyi n=1000 avg degree 10, greedy k=5 FP64", kind="greedy",
+                    graph=("er", 1000, 10), k=5, precision="fp64", eps=1e-6)
+    if args.workload == "batch":
+        return dict(name="Barabasi-Albert n=1M m=8, 4096 groups |S|~U{1..100}, batched FP32 scoring",
+                    kind="batch", graph=("ba", 1_000_000, 8), groups=4096, eps=1e-4)
+    return dict(name="serving: 8 ER/BA graphs, Poisson score/maximize mix", kind="serve", eps=1e-4)
+
+
+def make_graph(spec):
+    import graphgen as gg
+
+    kind = spec[0]
+    if kind == "rmat":
+        return gg.rmat(spec[1], 16, 0.57, 0.19, 0.19, seed=1)
+    if kind == "ba":
+        return gg.barabasi_albert(spec[1], spec[2], seed=1)
+    return gg.erdos_renyi(spec[1], spec[2], seed=1)
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, throttle reasons)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------- distributed
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def dist_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+# ----------------------------------------------------------------------------- CPU oracle baseline
+def oracle_greedy_sample(g, spec, L, budget_s=20.0):
+    """The oracle's lazy greedy on the same graph for as many steps as fit the budget (>= 1)."""
+    import oracle
+
+    alpha = oracle.default_alpha(g)
+    t0 = time.perf_counter()
+    steps = 0
+    S = []
+    while True:
+        grp, _, _ = oracle.greedy(g, 1, alpha, L, "lazy", init=S or None)
+        S.append(int(grp[0]))
+        steps += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or steps >= spec["k"] or el / steps * (steps + 1) > budget_s * 1.5:
+            break
+    t = time.perf_counter() - t0
+    gteps = steps * 2 * L * g.nnz / t / 1e9
+    return {"value": gteps, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+            "sample": f"{steps} of {spec['k']} greedy steps (lazy oracle, FP64, single thread) on the same graph, "
+                      f"{t:.1f} s"}
+
+
+# ----------------------------------------------------------------------------- greedy workload
+def run_greedy(args, spec, rank, world, local):
+    import torch
+
+    from paper_1910_13874_gb300 import gedwalk
+
+    g = make_graph(spec["graph"])
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    t_up = time.perf_counter()
+    G = gedwalk.Graph.from_host(g)
+    upload_s = time.perf_counter() - t_up
+    params = gedwalk.make_params(epsilon=spec["eps"], precision=spec["precision"], stream=stream.cuda_stream)
+    k = spec["k"]
+    for _ in range(args.warmup):
+        grp, gains, score, L = G.maximize(k, params=params)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    gedwalk.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        grp, gains, score, L = G.maximize(k, params=params)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    prof = gedwalk.profile_read()
+    gedwalk.profile(False)
+    clk = clocks.stop()
+    stats = G.maximize_stats()
+    t_step = dist_max(e0.elapsed_time(e1) / 1e3 / args.steps, world)
+    gteps = k * 2 * L * G.nnz / t_step / 1e9 * world
+    hbm, peak_kind = measured_peaks()
+    achieved = prof["sweep_bytes"] / (prof["sweep_ms"] / 1e3) / 1e9 if prof["sweep_ms"] > 0 else 0.0
+    out = {
+        "metric": METRIC, "value": round(gteps, 3), "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(t_step * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if spec["precision"] == "fp32" else "f64",
+        "data": "synthetic (seeded generator)",
+        "config": {"workload": spec["name"], "n": G.n, "nnz": G.nnz, "d_max": G.dmax, "alpha": G.alpha_default,
+                   "epsilon": spec["eps"], "L": L, "k": k, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (CSR %.0f MB)" % ((G.nnz + G.n) * 4 / 1e6)},
+        "seconds": round(t_step, 4),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                     "frac": round(achieved / hbm, 4), "traffic": None,
+                     "peak_kind": peak_kind, "kernel": "sweep_kernel (all sweeps of the timed region)",
+                     "launches_timed": prof["sweep_launches"]},
+        "gpu_launches": prof["launches"],
+        "clocks": clk,
+        "greedy": {"evaluations": stats["evaluations"], "batches": stats["batches"],
+                   "sweeps_per_run": stats["sweeps"], "spec_misses": stats["spec_misses"],
+                   "group_head": [int(x) for x in grp[:10]], "score": score},
+        "upload_s": round(upload_s, 3),
+    }
+    if not args.no_e2e:
+        # end to end through the C ABI: host CSR -> device (upload, relabel), maximise, results back
+        import numpy as np
+
+        rp = torch.from_numpy(g.row_ptr).pin_memory().numpy()
+        ci = torch.from_numpy(g.col_idx).pin_memory().numpy()
+        n_e2e = max(1, min(args.steps, 2))
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            G2 = gedwalk.Graph(rp, ci)
+            r = G2.maximize(k, params=params)
+            G2.free()
+        t_e2e = dist_max((time.perf_counter() - t0) / n_e2e, world)
+        out["e2e"] = {"value": round(k * 2 * L * G.nnz / t_e2e / 1e9 * world, 3), "unit": "GTEPS",
+                      "seconds": round(t_e2e, 3), "h2d_bytes_per_step": int(rp.nbytes + ci.nbytes),
+                      "d2h_bytes_per_step": int(k * 12 + 16)}
+        del np
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = oracle_greedy_sample(g, spec, L)
+    return out
+
+
+# ----------------------------------------------------------------------------- reference arm (the oracle)
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return None
+    spec = workload_spec(args)
+    if spec["kind"] != "greedy":
+        return {"impl": "reference", "unavailable": "the CPU oracle arm is timed for the greedy workloads only"}
+    import oracle
+
+    g = make_graph(spec["graph"])
+    alpha = oracle.default_alpha(g)
+    L, _ = oracle.select_L(g, alpha, spec["eps"] / spec["k"])
+    samples = []
+    for _ in range(args.warmup + args.steps):
+        samples.append(oracle_greedy_sample(g, spec, L, budget_s=8.0))
+    timed = samples[args.warmup:]
+    v = statistics.mean(s["value"] for s in timed)
+    return {"impl": "reference", "metric": METRIC, "value": round(v, 6), "unit": "GTEPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator)",
+            "config": {"workload": spec["name"], "n": g.n, "nnz": g.nnz, "L": L, "k": spec["k"]},
+            "cpu_baseline": {"value": round(v, 6), "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                             "sample": timed[-1]["sample"]},
+            "e2e": {"value": round(v, 6), "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        out = run_reference(args)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    spec = workload_spec(args)
+    if spec["kind"] == "greedy":
+        out = run_greedy(args, spec, rank, world, local)
+    elif spec["kind"] == "batch":
+        from bench_extra import run_batch  # noqa
+
+        out = run_batch(args, spec, rank, world, local)
+    else:
+        from bench_extra import run_serve  # noqa
+
+        out = run_serve(args, spec, rank, world, local)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,285 @@
+/*
+ * gedwalk.h - C ABI of the GB300 GED-Walk library (libgedwalk.so).
+ *
+ * GED-Walk group centrality (Angriman, van der Grinten, Bojchevski, Zuegner,
+ * Guennemann, Meyerhenke, "Group Centrality Maximization for Large-scale
+ * Graphs", ALENEX 2020):
+ *
+ *   GED(S) = sum_{i>=1} alpha^i * phi_i(S)              (Def. ged-walk, Eq. ged_def)
+ *
+ * where phi_i(S) is the number of length-i walks that contain at least one
+ * vertex of S (Def. ed-walk). The library evaluates the truncated sum
+ * GED_{<=L}(S) (Section 3.1) and maximises it greedily (Def. ged-max,
+ * Section 3.2) on an NVIDIA GB300 (sm_103a).
+ *
+ * Conventions shared by every entry point
+ *  - Every call returns a gedwalk_status. Output buffers are caller-owned host
+ *    memory and are written only when the call returns GEDWALK_OK.
+ *  - Host inputs are copied; the caller keeps ownership of them. Device memory
+ *    belongs to the library (see gedwalk_set_allocator).
+ *  - Graphs are undirected and unweighted (Section 2): a CSR with int32
+ *    row_ptr[n+1] and col_idx[nnz], every row strictly increasing, no
+ *    self-loops, and (u,v) present iff (v,u) is. Each undirected edge is two
+ *    entries, so it yields two 1-walks.
+ *  - Vertex ids in S, groups and results are the caller's ids in [0, n).
+ *    Groups have set semantics: repeated ids count once. An id outside
+ *    [0, n) returns GEDWALK_ERR_INVALID.
+ *  - Ties in the greedy argmax go to the lowest vertex id.
+ *  - gedwalk_last_error() returns a message for the last failing call made by
+ *    the calling thread.
+ *  - One graph handle may be used from several threads; calls on the same
+ *    handle are serialised inside the library.
+ */
+#ifndef GEDWALK_H
+#define GEDWALK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GEDWALK_API __attribute__((visibility("default")))
+#else
+#define GEDWALK_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gedwalk_graph* gedwalk_graph_t; /* opaque, device-resident, owned by the library */
+typedef struct gedwalk_server* gedwalk_server_t;
+
+typedef enum {
+  GEDWALK_OK = 0,
+  GEDWALK_ERR_INVALID = 1,        /* bad argument or malformed graph */
+  GEDWALK_ERR_OOM = 2,            /* a device or host allocation failed; state is unchanged */
+  GEDWALK_ERR_NOT_CONVERGENT = 3, /* alpha >= 1/d_max and no forced L: the bound does not apply */
+  GEDWALK_ERR_DEVICE = 4,         /* a CUDA call failed (message in gedwalk_last_error) */
+  GEDWALK_ERR_TIMEOUT = 5,        /* a bounded wait expired */
+  GEDWALK_ERR_BUSY = 6,           /* serving: no admission slot or memory left */
+  GEDWALK_ERR_NOT_FOUND = 7       /* serving: unknown ticket */
+} gedwalk_status;
+
+/* precision of the walk vectors; sums of alpha^i-weighted counts are always FP64 */
+enum { GEDWALK_FP64 = 0, GEDWALK_FP32 = 1 };
+
+/* gedwalk_params.greedy_eps_rule: how epsilon sets L for maximisation */
+enum {
+  GEDWALK_EPS_OVER_K = 0, /* L from the bound at epsilon/k (Algorithm 2 separates at epsilon/k) */
+  GEDWALK_EPS_PLAIN = 1   /* L from the bound at epsilon */
+};
+
+/* gedwalk_params.flags */
+enum {
+  GEDWALK_GAINS_ALL = 1 /* maximize: evaluate every vertex's exact gain at every step (no pruning) */
+};
+
+/* gedwalk_graph_upload flags */
+enum {
+  GEDWALK_UPLOAD_TRUSTED = 1 /* skip the sortedness / symmetry / self-loop validation */
+};
+
+typedef struct {
+  double alpha;            /* walk damping; 0 selects 1/(1+d_max). Must be > 0. */
+  double epsilon;          /* additive error for the truncation bound; > 0 unless L > 0 */
+  int32_t L;               /* 0: smallest l with B_l < epsilon (Algorithm 1); > 0: forced length */
+  int32_t precision;       /* GEDWALK_FP64 or GEDWALK_FP32 */
+  int32_t greedy_eps_rule; /* GEDWALK_EPS_OVER_K (default) or GEDWALK_EPS_PLAIN */
+  int32_t flags;           /* GEDWALK_GAINS_ALL */
+  int64_t stream;          /* cudaStream_t to run on (e.g. torch.cuda.current_stream().cuda_stream); 0 = default */
+} gedwalk_params;
+
+/* Fills *p with the defaults: alpha 0, epsilon 1e-4, L 0, FP32, EPS_OVER_K, no flags, stream 0. */
+GEDWALK_API void gedwalk_params_default(gedwalk_params* p);
+
+/*
+ * Device memory hook. alloc(bytes, stream, ctx) returns device memory or NULL;
+ * release(ptr, bytes, stream, ctx) frees it. Passing NULL restores the
+ * built-in cudaMalloc/cudaFree. The Python binding installs PyTorch's caching
+ * allocator here. Set it before the first upload; it applies to every later
+ * allocation of the process.
+ */
+typedef void* (*gedwalk_alloc_fn)(size_t bytes, int64_t stream, void* ctx);
+typedef void (*gedwalk_free_fn)(void* ptr, size_t bytes, int64_t stream, void* ctx);
+GEDWALK_API gedwalk_status gedwalk_set_allocator(gedwalk_alloc_fn alloc, gedwalk_free_fn release, void* ctx);
+
+/*
+ * Uploads a graph to the current CUDA device.
+ *  row_ptr: host int32[n+1], row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz.
+ *  col_idx: host int32[nnz], see the conventions above.
+ *  n >= 1; nnz >= 0 and < 2^31.
+ *  flags: GEDWALK_UPLOAD_TRUSTED skips validation (a malformed graph then gives
+ *  unspecified results, never a device fault: indices are still range-checked).
+ * The library relabels vertices by decreasing degree internally (ties by id) for
+ * gather locality; results are always reported in the caller's ids.
+ * On success *out receives a handle to release with gedwalk_graph_free.
+ * Errors: INVALID (malformed input, with the first offending row named in
+ * gedwalk_last_error), OOM, DEVICE.
+ */
+GEDWALK_API gedwalk_status gedwalk_graph_upload(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int64_t nnz,
+                                    int32_t flags, gedwalk_graph_t* out);
+
+/* Releases a graph and all device memory tied to it. NULL is accepted. */
+GEDWALK_API gedwalk_status gedwalk_graph_free(gedwalk_graph_t g);
+
+/* n, nnz (directed entries), d_max and the default alpha 1/(1+d_max). Any pointer may be NULL. */
+GEDWALK_API gedwalk_status gedwalk_graph_info(gedwalk_graph_t g, int32_t* n, int64_t* nnz, int32_t* dmax, double* alpha_default);
+
+/*
+ * Truncation length for (alpha, epsilon) (Algorithm 1 with the combinatorial
+ * bound, Eq. comb-bound): the smallest l >= 1 with
+ *   B_l = alpha^{l+1} d_max / (1 - alpha d_max) * W_l < epsilon,
+ * W_l the number of l-walks of G. The walk totals come from FP64 sweeps on the
+ * device and the test B_l < epsilon runs on the device.
+ *  alpha 0 selects the default. *L receives l, *bound (may be NULL) B_l.
+ * Errors: NOT_CONVERGENT (alpha*d_max >= 1), INVALID (epsilon <= 0, or no
+ * l <= 4096 qualifies).
+ */
+GEDWALK_API gedwalk_status gedwalk_truncation(gedwalk_graph_t g, double alpha, double epsilon, int32_t* L, double* bound);
+
+/*
+ * GED_{<=L}(S) of one group (problem (i), Algorithm 1), by the two-state
+ * hit/miss recurrences of Section 3.1.1 run as a masked two-column SpMV:
+ *   h_i = alpha (A h_{i-1} + 1_S . A m_{i-1}),  m_i = alpha 1_{V\S} . A m_{i-1},
+ *   score += sum_v h_i(v)  (FP64),
+ * starting from h_0 = 1_S, m_0 = 1_{V\S}.
+ *  S: host int32[s_len] (s_len >= 0; S may be NULL when s_len is 0).
+ *  params: NULL means the defaults; params->precision picks FP64 or FP32 walk
+ *  vectors.
+ *  score: the partial sum, a lower bound with GED(S) in [score, score + bound].
+ *  L_used, tail_bound: may be NULL; receive L and B_L.
+ */
+GEDWALK_API gedwalk_status gedwalk_score(gedwalk_graph_t g, const int32_t* S, int32_t s_len, const gedwalk_params* params,
+                             double* score, int32_t* L_used, double* tail_bound);
+
+/*
+ * Scores G groups at once (problem (i) for many groups). Group j is
+ * members[offsets[j] .. offsets[j+1]). Groups become the columns of one masked
+ * FP32 SpMM over column blocks whose width an on-device autotuner picks; the
+ * per-group hit sums are FP64. The hits are counted by first visits:
+ *   GED_{<=L}(S) = sum_{s in S} sum_{p=0..L} alpha^p F_p(s) * K_{L-p}(s),
+ * F_p(s) the p-walks ending at s whose earlier vertices avoid S, and K_q(s) the
+ * alpha-weighted walks of length <= q starting at s (the p = 0 term excludes
+ * the empty walk). This equals the two-state sum of gedwalk_score.
+ *  offsets: host int32[G+1], offsets[0] = 0, non-decreasing.
+ *  members: host int32[offsets[G]].
+ *  scores: host double[G]. L_used may be NULL.
+ * params->precision is ignored (FP32 vectors, FP64 sums).
+ */
+GEDWALK_API gedwalk_status gedwalk_score_batch(gedwalk_graph_t g, const int32_t* offsets, const int32_t* members, int32_t G,
+                                   const gedwalk_params* params, double* scores, int32_t* L_used);
+
+/*
+ * Exact truncated marginal gain GED_{<=L}(S, x) = GED_{<=L}(S + x) - GED_{<=L}(S)
+ * (the lower bound L_l of Section 3.2.1) for every vertex x, counted directly as
+ * the alpha-weighted walks of length 1..L that visit x and avoid S (proof of
+ * Prop. ged_submod). Members of S get 0.
+ *  gains: host double[n] in caller ids. L_used may be NULL.
+ */
+GEDWALK_API gedwalk_status gedwalk_gains(gedwalk_graph_t g, const int32_t* S, int32_t s_len, const gedwalk_params* params,
+                             double* gains, int32_t* L_used);
+
+/*
+ * Greedy GED-Walk maximisation (problem (ii), Def. ged-max; the
+ * (1-1/e)-approximation of Prop. greedy_approx): k times, add the vertex with
+ * the largest truncated marginal gain GED_{<=L}(S, x), lowest id among equal
+ * gains, at a fixed L (params: EPS_OVER_K takes L from the bound at
+ * epsilon/k, as Algorithm 2 separates at epsilon/k; EPS_PLAIN at epsilon).
+ * Each step bounds every gain from above by the smaller of its last exact value
+ * (submodularity, Prop. ged_submod) and sum_i alpha^i P_i(S, x) (Lemma
+ * initialize), evaluates the best-bounded candidates exactly in batches, and
+ * accepts the best once no unevaluated bound can reach it.
+ *  k >= 0 and init_len + k <= n.
+ *  group: host int32[k], the added vertices in order.
+ *  gains: host double[k], the gain of each addition (may be NULL).
+ *  score: GED_{<=L} of init + group (may be NULL).
+ *  L_used: may be NULL.
+ *  init_group/init_len: resume from this prefix group (may be NULL/0).
+ * GEDWALK_GAINS_ALL in params->flags evaluates every vertex at every step.
+ */
+GEDWALK_API gedwalk_status gedwalk_maximize(gedwalk_graph_t g, int32_t k, const gedwalk_params* params, int32_t* group,
+                                double* gains, double* score, int32_t* L_used, const int32_t* init_group,
+                                int32_t init_len);
+
+/*
+ * Counters of the last gedwalk_maximize on this graph: exact-gain evaluations
+ * (candidate columns), candidate batches, sweep-kernel launches and the
+ * batches whose speculation (candidates chosen before the new S was known)
+ * failed to certify the winner. Any pointer may be NULL.
+ */
+GEDWALK_API gedwalk_status gedwalk_maximize_stats(gedwalk_graph_t g, int64_t* evaluations, int64_t* batches, int64_t* sweeps,
+                                      int64_t* spec_misses);
+
+/* ---------------------------------------------------------------------------
+ * Serving: a continuous-batching request loop over device-resident graphs.
+ * Score requests for the same graph that are pending together are packed as
+ * columns of one batched SpMM; maximise requests run on their own streams and
+ * overlap with the scoring. Admission is by memory: a request is admitted
+ * when its device working set fits in mem_budget beside the requests in
+ * flight, otherwise it waits in the queue. Results do not depend on which
+ * other requests shared a batch.
+ * ------------------------------------------------------------------------- */
+enum { GEDWALK_REQ_SCORE = 0, GEDWALK_REQ_MAXIMIZE = 1 };
+
+/*
+ * graphs: n_graphs uploaded handles, referenced by index in submit; they must
+ * outlive the server. mem_budget: bytes of device working memory the server
+ * may hold for requests in flight (0 = 1 GiB). max_batch: the most score
+ * requests packed into one SpMM (0 = 256). The server starts one scheduler
+ * thread.
+ */
+GEDWALK_API gedwalk_status gedwalk_serve_create(const gedwalk_graph_t* graphs, int32_t n_graphs, int64_t mem_budget,
+                                    int32_t max_batch, gedwalk_server_t* out);
+
+/*
+ * Queues a request. kind GEDWALK_REQ_SCORE scores S (s_len members);
+ * GEDWALK_REQ_MAXIMIZE runs gedwalk_maximize with k = s_len_or_k (S ignored).
+ * params: NULL = defaults (its stream field is ignored). *ticket identifies the
+ * request. BUSY when the queue holds 1<<20 requests already.
+ */
+GEDWALK_API gedwalk_status gedwalk_serve_submit(gedwalk_server_t srv, int32_t graph, int32_t kind, const int32_t* S,
+                                    int32_t s_len_or_k, const gedwalk_params* params, uint64_t* ticket);
+
+/*
+ * Waits up to wait_us microseconds (0 = do not wait, < 0 = wait without limit)
+ * for a request. *done = 1 and results written when finished: score, group
+ * (int32[k], maximize only), gains (double[k], maximize only; may be NULL),
+ * latency_us (submit to completion; may be NULL). The ticket is released once
+ * reported done. *done = 0 when still pending. A request that failed reports
+ * its own status as the return value with *done = 1.
+ */
+GEDWALK_API gedwalk_status gedwalk_serve_poll(gedwalk_server_t srv, uint64_t ticket, int32_t wait_us, double* score,
+                                  int32_t* group, double* gains, double* latency_us, int32_t* done);
+
+/* Counters: requests completed, batched SpMM launches, score requests packed into them, peak bytes in flight. */
+GEDWALK_API gedwalk_status gedwalk_serve_stats(gedwalk_server_t srv, int64_t* completed, int64_t* batches, int64_t* batched_requests,
+                                   int64_t* peak_bytes);
+
+/* Stops the scheduler after the requests in flight finish; pending requests are dropped. */
+GEDWALK_API gedwalk_status gedwalk_serve_destroy(gedwalk_server_t srv);
+
+/* ---------------------------------------------------------------------------
+ * Profiling: CUDA events around every sweep-kernel launch (the masked SpMV/SpMM
+ * step of every algorithm above) and a count of all kernel launches.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  int64_t launches;        /* every kernel launch of the library since the last reset */
+  int64_t sweep_launches;  /* sweep-kernel launches timed */
+  double sweep_ms;         /* summed device time of those launches (CUDA events on their stream) */
+  double sweep_bytes;      /* summed algorithmic bytes of those launches (see the design notes) */
+} gedwalk_profile_stats;
+
+/* enable != 0 starts timing sweep launches; every call resets the counters. */
+GEDWALK_API gedwalk_status gedwalk_profile(int32_t enable);
+
+/* Waits for the timed launches to finish and reports the counters. */
+GEDWALK_API gedwalk_status gedwalk_profile_read(gedwalk_profile_stats* out);
+
+/* Message for the calling thread's last failing call ("" if none). */
+GEDWALK_API const char* gedwalk_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GEDWALK_H */

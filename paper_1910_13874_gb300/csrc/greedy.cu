@@ -1,0 +1,535 @@
+// Greedy GED-Walk maximisation (problem (ii), Def. ged-max; Prop. greedy_approx) and
+// all-vertex exact marginal gains.
+//
+// A step with current group S:
+//  1. L fused sweeps compute phi^miss_1..L under S (column 0, stored in a table) and,
+//     in the same pass, the exact gains of up to kSpec "speculative" candidates
+//     (columns 1..), chosen before S was known from bounds that stay valid when S
+//     grows: the last exact gain (submodularity, Prop. ged_submod) and the previous
+//     step's Lemma-initialize bound (P_i is non-increasing in S).
+//  2. One pass over all vertices forms the Lemma-initialize bound
+//       ub(x) = sum_{i=1..L} alpha^i P_i(S, x) = sum_{1 <= a+b <= L} y_a(x) y_b(x),
+//     y_a = alpha^a phi^miss_a (psi^miss = phi^miss on an undirected graph), takes
+//     min(ub, last exact gain), and selects the best-bounded unevaluated vertices.
+//  3. The best evaluated candidate wins once no unevaluated bound (inflated by the
+//     rounding tolerance) reaches its gain; otherwise the next batch of candidates
+//     is evaluated exactly and step 2 repeats. A vertex whose bound is exactly 0
+//     has gain exactly 0. Among equal gains the lowest caller id wins.
+// The gain of candidate c counts walks of length 1..L in G[V\S] through c
+// (proof of Prop. ged_submod): h_0 = e_c, h_t = alpha 1_{V\S} . A h_{t-1} except
+// h_t(c) = phi^miss_t(c); gain = sum_t sum_v h_t(v) in FP64.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+
+#include "internal.h"
+
+namespace gw {
+namespace {
+
+constexpr int kTopK = 16;
+constexpr int kSelBlocks = 152 * 4;
+
+struct Stale {
+  float ub;      // last exact gain rounded up (an upper bound for every later step)
+  int32_t step;  // step in which it was evaluated, -1 if never
+};
+
+struct SelOut {  // device -> host after each selection pass
+  float val[kTopK];
+  int32_t id[kTopK];
+  int32_t zero_min_caller;  // smallest caller id among unevaluated vertices with bound exactly 0
+  int32_t pad[3];
+  double gains[16];          // exact gains of the last candidate batch
+};
+
+__device__ __forceinline__ bool better(float a, int ia, float b, int ib) { return a > b || (a == b && ia < ib); }
+
+__device__ __forceinline__ void topk_push(float (&v)[kTopK], int (&id)[kTopK], float x, int ix) {
+  if (!better(x, ix, v[kTopK - 1], id[kTopK - 1])) return;
+  v[kTopK - 1] = x;
+  id[kTopK - 1] = ix;
+#pragma unroll
+  for (int i = kTopK - 1; i > 0; --i) {
+    if (better(v[i], id[i], v[i - 1], id[i - 1])) {
+      const float tv = v[i];
+      v[i] = v[i - 1];
+      v[i - 1] = tv;
+      const int ti = id[i];
+      id[i] = id[i - 1];
+      id[i - 1] = ti;
+    }
+  }
+}
+
+// Block-wide top-K of the threads' sorted lists; thread 0 writes out[0..K).
+__device__ void block_topk(float (&v)[kTopK], int (&id)[kTopK], float* out_v, int* out_id) {
+  __shared__ float sv[kThreads / 32];
+  __shared__ int sid[kThreads / 32];
+  __shared__ float bv_s;
+  __shared__ int bi_s;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int round = 0; round < kTopK; ++round) {
+    float bv = v[0];
+    int bi = id[0];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (better(ov, oi, bv, bi)) {
+        bv = ov;
+        bi = oi;
+      }
+    }
+    if (lane == 0) {
+      sv[warp] = bv;
+      sid[warp] = bi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float b = sv[0];
+      int i0 = sid[0];
+      for (int w = 1; w < kThreads / 32; ++w)
+        if (better(sv[w], sid[w], b, i0)) {
+          b = sv[w];
+          i0 = sid[w];
+        }
+      bv_s = b;
+      bi_s = i0;
+      out_v[round] = b;
+      out_id[round] = i0;
+    }
+    __syncthreads();
+    if (bi_s != INT_MAX && id[0] == bi_s && v[0] == bv_s) {
+#pragma unroll
+      for (int i = 0; i < kTopK - 1; ++i) {
+        v[i] = v[i + 1];
+        id[i] = id[i + 1];
+      }
+      v[kTopK - 1] = -1.0f;
+      id[kTopK - 1] = INT_MAX;
+    }
+    __syncthreads();
+  }
+}
+
+// mtab row 0 = phi^miss_0 = 1_{V\S}; X column 0 (fused) = the same; candidate columns = e_c.
+template <typename T>
+__global__ void greedy_init(T* __restrict__ m0, T* __restrict__ X, int cols, int first_cand_col,
+                            const int32_t* __restrict__ cand, const uint32_t* __restrict__ mask, int32_t n) {
+  __shared__ int sc[16];
+  if (threadIdx.x < 16) sc[threadIdx.x] = threadIdx.x < cols - first_cand_col ? cand[threadIdx.x] : -1;
+  __syncthreads();
+  for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const bool inS = (mask[v >> 5] >> (v & 31)) & 1u;
+    const T m = inS ? T(0) : T(1);
+    if (m0) m0[v] = m;
+    T* row = X + static_cast<size_t>(v) * cols;
+    if (first_cand_col == 1) row[0] = m;
+    for (int j = first_cand_col; j < cols; ++j) row[j] = (sc[j - first_cand_col] == v) ? T(1) : T(0);
+  }
+}
+
+__global__ void update_stale(Stale* __restrict__ stale, const int32_t* __restrict__ cand,
+                             const double* __restrict__ gains, int count, int32_t step, double* __restrict__ out) {
+  const int j = threadIdx.x;
+  if (j >= count) return;
+  const int c = cand[j];
+  if (out) out[j] = gains[j];
+  if (c < 0) return;
+  Stale st;
+  st.ub = __double2float_ru(gains[j]);
+  st.step = step;
+  stale[c] = st;
+}
+
+// Lemma-initialize bound + selection over all vertices.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) ub_select(const T* __restrict__ mtab, int32_t L, int32_t n,
+                                                     const uint32_t* __restrict__ mask,
+                                                     const Stale* __restrict__ stale, int32_t step,
+                                                     const int32_t* __restrict__ perm, float* __restrict__ sel_v,
+                                                     int* __restrict__ sel_id, int32_t* __restrict__ zero_min) {
+  float v[kTopK];
+  int id[kTopK];
+#pragma unroll
+  for (int i = 0; i < kTopK; ++i) {
+    v[i] = -1.0f;
+    id[i] = INT_MAX;
+  }
+  for (int32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
+    if ((__ldg(mask + (x >> 5)) >> (x & 31)) & 1u) continue;
+    const Stale st = stale[x];
+    if (st.step == step) continue;  // evaluated with the current S: its exact gain is known
+    // sum over ordered pairs 1 <= a + b <= L of y_a y_b
+    //   = y_0 (Q_L - y_0) + sum_{a=1..L} y_a Q_{L-a},   Q_q = sum_{b<=q} y_b,
+    // streamed from the table; every term is non-negative, so nothing cancels
+    const T* col = mtab + x;
+    const double y0 = static_cast<double>(__ldg(col));
+    double tail = 0.0;
+    for (int a = 1; a <= L; ++a) tail += static_cast<double>(__ldg(col + static_cast<size_t>(a) * n));
+    double ub = y0 * tail;
+    double Q = y0 + tail;
+    for (int a = 1; a <= L; ++a) {
+      Q -= static_cast<double>(__ldg(col + static_cast<size_t>(L - a + 1) * n));
+      ub += static_cast<double>(__ldg(col + static_cast<size_t>(a) * n)) * Q;
+    }
+    float b = __double2float_ru(ub);
+    if (st.step >= 0 && st.ub < b) b = st.ub;
+    if (b == 0.0f) {
+      atomicMin(zero_min, __ldg(perm + x));
+      continue;
+    }
+    topk_push(v, id, b, x);
+  }
+  __shared__ float ov[kTopK];
+  __shared__ int oi[kTopK];
+  block_topk(v, id, ov, oi);
+  if (threadIdx.x < kTopK) {
+    sel_v[blockIdx.x * kTopK + threadIdx.x] = ov[threadIdx.x];
+    sel_id[blockIdx.x * kTopK + threadIdx.x] = oi[threadIdx.x];
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) select_merge(const float* __restrict__ sel_v,
+                                                        const int* __restrict__ sel_id, int count,
+                                                        SelOut* __restrict__ out) {
+  float v[kTopK];
+  int id[kTopK];
+#pragma unroll
+  for (int i = 0; i < kTopK; ++i) {
+    v[i] = -1.0f;
+    id[i] = INT_MAX;
+  }
+  for (int i = threadIdx.x; i < count; i += kThreads)
+    if (sel_id[i] != INT_MAX) topk_push(v, id, sel_v[i], sel_id[i]);
+  __shared__ float ov[kTopK];
+  __shared__ int oi[kTopK];
+  block_topk(v, id, ov, oi);
+  if (threadIdx.x < kTopK) {
+    out->val[threadIdx.x] = ov[threadIdx.x];
+    out->id[threadIdx.x] = oi[threadIdx.x];
+  }
+}
+
+__global__ void set_int(int32_t* p, int32_t v) { *p = v; }
+
+int blocks_for(int64_t n) { return static_cast<int>(std::min<int64_t>((n + 255) / 256, 152 * 16)); }
+
+struct Cand {
+  double g;
+  int32_t v;       // internal id
+  int32_t caller;  // caller id
+};
+// exact-gain order: larger gain first, then the lower caller id
+bool cand_before(const Cand& a, const Cand& b) { return a.g > b.g || (a.g == b.g && a.caller < b.caller); }
+
+struct GreedyCtx {
+  Graph& g;
+  Workspace& ws;
+  const Resolved& r;
+  cudaStream_t s;
+  int32_t L;
+  size_t es;
+  SelOut* d_out;
+  int32_t* d_cand;
+  double* d_gains;
+  SelOut* h_out;
+  int64_t sweeps = 0;
+};
+
+// Runs L sweeps. mode MODE_FUSED (column 0 = phi^miss, table rows written) or MODE_CAND.
+gedwalk_status run_sweeps(GreedyCtx& c, int mode, int cols, const std::vector<int32_t>& cand) {
+  Graph& g = c.g;
+  Workspace& ws = c.ws;
+  const bool fp64 = c.r.fp64;
+  int32_t hc[16];
+  for (int j = 0; j < 16; ++j) hc[j] = j < static_cast<int>(cand.size()) ? cand[j] : -1;
+  GW_CUDA(cudaMemcpyAsync(c.d_cand, hc, sizeof hc, cudaMemcpyHostToDevice, c.s));
+  const size_t vbytes = static_cast<size_t>(g.n) * cols * c.es;
+  GW_TRY(ws.x0.ensure(vbytes, c.s));
+  GW_TRY(ws.x1.ensure(vbytes, c.s));
+  GW_TRY(ensure_sweep_scratch(g, ws, cols, fp64, c.s));
+  const int first = mode == MODE_FUSED ? 1 : 0;
+  void* m0 = mode == MODE_FUSED ? ws.mtab.p : nullptr;
+  if (fp64)
+    greedy_init<double><<<blocks_for(g.n), 256, 0, c.s>>>(static_cast<double*>(m0), ws.x0.as<double>(), cols, first,
+                                                           c.d_cand, ws.mask.as<uint32_t>(), g.n);
+  else
+    greedy_init<float><<<blocks_for(g.n), 256, 0, c.s>>>(static_cast<float*>(m0), ws.x0.as<float>(), cols, first,
+                                                          c.d_cand, ws.mask.as<uint32_t>(), g.n);
+  GW_KCHECK();
+  SweepArgs a = base_args(g, ws);
+  a.alpha = c.r.alpha;
+  a.cand = c.d_cand;
+  void* cur = ws.x0.p;
+  void* nxt = ws.x1.p;
+  for (int32_t t = 1; t <= c.L; ++t) {
+    a.X = cur;
+    a.Y = nxt;
+    a.accumulate = t > 1;
+    char* row = ws.mtab.as<char>() + static_cast<size_t>(t) * g.n * c.es;
+    if (mode == MODE_FUSED) a.Mout = row;
+    else a.Min = row;
+    GW_TRY(launch_sweep(mode, fp64, cols, a, c.s));
+    ++c.sweeps;
+    std::swap(cur, nxt);
+  }
+  const int nsum = sweep_sums(mode, cols);
+  if (nsum > 0) GW_TRY(launch_reduce_slots(ws.slots.as<double>(), g.plan.num_slots, nsum, c.d_gains, c.s));
+  return GEDWALK_OK;
+}
+
+}  // namespace
+
+gedwalk_status maximize_impl(Graph& g, Workspace& ws, int32_t k, const Resolved& r, int32_t flags,
+                             const std::vector<int32_t>& init_int, int32_t* group, double* gains, double* score) {
+  cudaStream_t s = r.stream;
+  const size_t es = r.fp64 ? 8 : 4;
+  const int cols_fused = r.fp64 ? 4 : 8;  // phi^miss + speculative candidates
+  const int n_spec = cols_fused - 1;
+  const int cols_cand = r.fp64 ? 4 : 8;
+  const int cols_all = r.fp64 ? 8 : 16;
+  const double tol = r.fp64 ? 1e-11 : 1e-5;  // relative inflation of bounds against rounding
+  const bool gains_all = (flags & GEDWALK_GAINS_ALL) != 0;
+  const int32_t L = r.L;
+  ws.st_evals = ws.st_batches = ws.st_sweeps = ws.st_spec_miss = 0;
+
+  GW_TRY(ws.mtab.ensure(static_cast<size_t>(L + 1) * g.n * es, s));
+  GW_TRY(ws.stale.ensure(static_cast<size_t>(g.n) * sizeof(Stale), s));
+  GW_TRY(ws.sel.ensure(static_cast<size_t>(kSelBlocks) * kTopK * 8, s));
+  GW_TRY(ws.small.ensure(sizeof(SelOut) + 16 * sizeof(int32_t) + 16 * sizeof(double) + 256, s));
+  GW_TRY(ws.ensure_pinned(sizeof(SelOut) + 64));
+  GW_TRY(upload_mask(g, ws, init_int, s));
+  GW_CUDA(cudaMemsetAsync(ws.stale.p, 0xff, static_cast<size_t>(g.n) * sizeof(Stale), s));  // step -1, ub NaN
+
+  GreedyCtx c{g, ws, r, s, L, es};
+  c.d_out = ws.small.as<SelOut>();
+  c.d_cand = reinterpret_cast<int32_t*>(c.d_out + 1);
+  c.d_gains = reinterpret_cast<double*>(c.d_cand + 16);
+  c.h_out = static_cast<SelOut*>(ws.pinned);
+  float* sel_v = ws.sel.as<float>();
+  int* sel_id = reinterpret_cast<int*>(sel_v + kSelBlocks * kTopK);
+  Stale* stale = ws.stale.as<Stale>();
+
+  std::vector<uint32_t> hmask((static_cast<size_t>(g.n) + 31) / 32, 0u);
+  std::vector<char> inS(g.n, 0);
+  for (int32_t v : init_int) {
+    hmask[v >> 5] |= 1u << (v & 31);
+    inS[v] = 1;
+  }
+  std::vector<int32_t> S_all = init_int;
+  std::vector<Cand> spec;  // next step's speculative candidates (internal ids)
+
+  for (int32_t step = 0; step < k; ++step) {
+    std::vector<Cand> E;  // evaluated with the current S
+    Cand best{-1.0, -1, INT_MAX};
+    if (gains_all) {
+      GW_TRY(run_sweeps(c, MODE_FUSED, 1, {}));
+      std::vector<int32_t> batch;
+      for (int32_t v = 0; v <= g.n; ++v) {
+        if (v < g.n && !inS[v]) batch.push_back(v);
+        if (static_cast<int>(batch.size()) == cols_all || (v == g.n && !batch.empty())) {
+          GW_TRY(run_sweeps(c, MODE_CAND, cols_all, batch));
+          double hg[16];
+          GW_CUDA(cudaMemcpyAsync(hg, c.d_gains, sizeof(double) * cols_all, cudaMemcpyDeviceToHost, s));
+          GW_CUDA(cudaStreamSynchronize(s));
+          for (size_t j = 0; j < batch.size(); ++j) {
+            Cand e{hg[j], batch[j], g.perm[batch[j]]};
+            if (best.v < 0 || cand_before(e, best)) best = e;
+          }
+          ws.st_evals += static_cast<int64_t>(batch.size());
+          ++ws.st_batches;
+          batch.clear();
+        }
+      }
+    } else {
+      // 1. fused sweeps: phi^miss under S plus the speculative candidates
+      std::vector<int32_t> sc;
+      for (const Cand& e : spec) sc.push_back(e.v);
+      const int cf = sc.empty() ? 1 : cols_fused;
+      GW_TRY(run_sweeps(c, MODE_FUSED, cf, sc));
+      std::vector<int32_t> last = sc;
+      bool first_batch = true;
+      for (;;) {
+        if (!last.empty()) {
+          update_stale<<<1, 32, 0, s>>>(stale, c.d_cand, c.d_gains, static_cast<int>(last.size()), step,
+                                        c.d_out->gains);
+          GW_KCHECK();
+        }
+        // 2. bound + selection pass
+        set_int<<<1, 1, 0, s>>>(&c.d_out->zero_min_caller, INT_MAX);
+        const int nb = std::max(1, std::min(kSelBlocks, blocks_for(g.n)));
+        if (r.fp64)
+          ub_select<double><<<nb, kThreads, 0, s>>>(ws.mtab.as<double>(), L, g.n, ws.mask.as<uint32_t>(), stale, step,
+                                                    g.perm_d.as<int32_t>(), sel_v, sel_id,
+                                                    &c.d_out->zero_min_caller);
+        else
+          ub_select<float><<<nb, kThreads, 0, s>>>(ws.mtab.as<float>(), L, g.n, ws.mask.as<uint32_t>(), stale, step,
+                                                   g.perm_d.as<int32_t>(), sel_v, sel_id,
+                                                   &c.d_out->zero_min_caller);
+        GW_KCHECK();
+        select_merge<<<1, kThreads, 0, s>>>(sel_v, sel_id, nb * kTopK, c.d_out);
+        GW_KCHECK();
+        GW_CUDA(cudaMemcpyAsync(c.h_out, c.d_out, sizeof(SelOut), cudaMemcpyDeviceToHost, s));
+        GW_CUDA(cudaStreamSynchronize(s));
+        for (size_t j = 0; j < last.size(); ++j) {
+          Cand e{c.h_out->gains[j], last[j], g.perm[last[j]]};
+          E.push_back(e);
+          if (best.v < 0 || cand_before(e, best)) best = e;
+        }
+        ws.st_evals += static_cast<int64_t>(last.size());
+        if (!last.empty()) ++ws.st_batches;
+        // 3. certify
+        std::vector<int32_t> top;
+        for (int j = 0; j < kTopK; ++j)
+          if (c.h_out->id[j] != INT_MAX) top.push_back(c.h_out->id[j]);
+        const int32_t zmin = c.h_out->zero_min_caller;
+        if (zmin != INT_MAX && (best.v < 0 || best.g < 0.0 || (best.g == 0.0 && zmin < best.caller)))
+          best = Cand{0.0, g.inv[zmin], zmin};
+        const bool certified =
+            top.empty() || (best.v >= 0 && static_cast<double>(c.h_out->val[0]) * (1.0 + tol) < best.g);
+        if (certified) {
+          // speculative candidates for the next step: best remaining bounds, exact or not
+          std::vector<Cand> pool;
+          for (const Cand& e : E)
+            if (e.v != best.v) pool.push_back(e);
+          for (size_t j = 0; j < top.size(); ++j)
+            pool.push_back(Cand{static_cast<double>(c.h_out->val[j]), top[j], g.perm[top[j]]});
+          std::sort(pool.begin(), pool.end(), cand_before);
+          spec.clear();
+          for (const Cand& e : pool) {
+            if (static_cast<int>(spec.size()) == n_spec) break;
+            if (e.g > 0.0) spec.push_back(e);
+          }
+          break;
+        }
+        if (first_batch && !sc.empty()) ++ws.st_spec_miss;
+        first_batch = false;
+        last.assign(top.begin(), top.begin() + std::min<size_t>(top.size(), cols_cand));
+        GW_TRY(run_sweeps(c, MODE_CAND, cols_cand, last));
+      }
+    }
+    if (best.v < 0) return fail(GEDWALK_ERR_INVALID, "no vertex left to add");
+    group[step] = best.caller;
+    if (gains) gains[step] = best.g;
+    const int32_t w = best.v;
+    inS[w] = 1;
+    S_all.push_back(w);
+    hmask[w >> 5] |= 1u << (w & 31);
+    GW_CUDA(cudaMemcpyAsync(ws.mask.as<uint32_t>() + (w >> 5), &hmask[w >> 5], 4, cudaMemcpyHostToDevice, s));
+    spec.erase(std::remove_if(spec.begin(), spec.end(), [&](const Cand& e) { return e.v == w; }), spec.end());
+  }
+  ws.st_sweeps = c.sweeps;
+  if (score) {
+    double v = 0;
+    GW_TRY(score_one(g, ws, S_all, r, &v));
+    *score = v;
+  }
+  GW_CUDA(cudaStreamSynchronize(s));
+  return GEDWALK_OK;
+}
+
+gedwalk_status gains_impl(Graph& g, Workspace& ws, const std::vector<int32_t>& S_int, const Resolved& r,
+                          double* gains_caller) {
+  cudaStream_t s = r.stream;
+  const size_t es = r.fp64 ? 8 : 4;
+  const int cols_all = r.fp64 ? 8 : 16;
+  GW_TRY(ws.mtab.ensure(static_cast<size_t>(r.L + 1) * g.n * es, s));
+  GW_TRY(ws.small.ensure(sizeof(SelOut) + 16 * sizeof(int32_t) + 16 * sizeof(double) + 256, s));
+  GW_TRY(upload_mask(g, ws, S_int, s));
+  GreedyCtx c{g, ws, r, s, r.L, es};
+  c.d_out = ws.small.as<SelOut>();
+  c.d_cand = reinterpret_cast<int32_t*>(c.d_out + 1);
+  c.d_gains = reinterpret_cast<double*>(c.d_cand + 16);
+  std::vector<char> inS(g.n, 0);
+  for (int32_t v : S_int) inS[v] = 1;
+  for (int32_t v = 0; v < g.n; ++v) gains_caller[v] = 0.0;
+  GW_TRY(run_sweeps(c, MODE_FUSED, 1, {}));
+  std::vector<int32_t> batch;
+  for (int32_t v = 0; v <= g.n; ++v) {
+    if (v < g.n && !inS[v]) batch.push_back(v);
+    if (static_cast<int>(batch.size()) == cols_all || (v == g.n && !batch.empty())) {
+      GW_TRY(run_sweeps(c, MODE_CAND, cols_all, batch));
+      double hg[16];
+      GW_CUDA(cudaMemcpyAsync(hg, c.d_gains, sizeof(double) * cols_all, cudaMemcpyDeviceToHost, s));
+      GW_CUDA(cudaStreamSynchronize(s));
+      for (size_t j = 0; j < batch.size(); ++j) gains_caller[g.perm[batch[j]]] = hg[j];
+      batch.clear();
+    }
+  }
+  return GEDWALK_OK;
+}
+
+}  // namespace gw
+
+using namespace gw;
+
+extern "C" {
+
+gedwalk_status gedwalk_maximize(gedwalk_graph_t h, int32_t k, const gedwalk_params* params, int32_t* group,
+                                double* gains, double* score, int32_t* L_used, const int32_t* init_group,
+                                int32_t init_len) {
+  if (!h) return fail(GEDWALK_ERR_INVALID, "graph is NULL");
+  if (k < 0) return fail(GEDWALK_ERR_INVALID, "k must be >= 0");
+  if (k > 0 && !group) return fail(GEDWALK_ERR_INVALID, "group is NULL");
+  Graph* g = G(h);
+  std::lock_guard<std::mutex> lk(g->mu);
+  GW_CUDA(cudaSetDevice(g->device));
+  std::vector<int32_t> init;
+  GW_TRY(map_group(*g, init_group, init_len, &init));
+  if (static_cast<int64_t>(init.size()) + k > g->n)
+    return fail(GEDWALK_ERR_INVALID, "init group (%zu) + k (%d) exceeds n (%d)", init.size(), k, g->n);
+  gedwalk_params d;
+  gedwalk_params_default(&d);
+  const gedwalk_params* p = params ? params : &d;
+  const double eps = (p->greedy_eps_rule == GEDWALK_EPS_OVER_K && k > 0) ? p->epsilon / k : p->epsilon;
+  Resolved r;
+  GW_TRY(resolve(*g, p, eps, &r));
+  std::vector<int32_t> grp(std::max(k, 1));
+  std::vector<double> gn(std::max(k, 1));
+  double sc = 0;
+  GW_TRY(maximize_impl(*g, g->ws, k, r, p->flags, init, grp.data(), gn.data(), score ? &sc : nullptr));
+  g->st_evals = g->ws.st_evals;
+  g->st_batches = g->ws.st_batches;
+  g->st_sweeps = g->ws.st_sweeps;
+  g->st_spec_miss = g->ws.st_spec_miss;
+  for (int32_t j = 0; j < k; ++j) {
+    group[j] = grp[j];
+    if (gains) gains[j] = gn[j];
+  }
+  if (score) *score = sc;
+  if (L_used) *L_used = r.L;
+  return GEDWALK_OK;
+}
+
+gedwalk_status gedwalk_maximize_stats(gedwalk_graph_t h, int64_t* evaluations, int64_t* batches, int64_t* sweeps,
+                                      int64_t* spec_misses) {
+  if (!h) return fail(GEDWALK_ERR_INVALID, "graph is NULL");
+  Graph* g = G(h);
+  std::lock_guard<std::mutex> lk(g->mu);
+  if (evaluations) *evaluations = g->st_evals;
+  if (batches) *batches = g->st_batches;
+  if (sweeps) *sweeps = g->st_sweeps;
+  if (spec_misses) *spec_misses = g->st_spec_miss;
+  return GEDWALK_OK;
+}
+
+gedwalk_status gedwalk_gains(gedwalk_graph_t h, const int32_t* S, int32_t s_len, const gedwalk_params* params,
+                             double* gains, int32_t* L_used) {
+  if (!h || !gains) return fail(GEDWALK_ERR_INVALID, "graph or gains is NULL");
+  Graph* g = G(h);
+  std::lock_guard<std::mutex> lk(g->mu);
+  GW_CUDA(cudaSetDevice(g->device));
+  std::vector<int32_t> S_int;
+  GW_TRY(map_group(*g, S, s_len, &S_int));
+  Resolved r;
+  GW_TRY(resolve(*g, params, 0.0, &r));
+  GW_TRY(gains_impl(*g, g->ws, S_int, r, gains));
+  if (L_used) *L_used = r.L;
+  return GEDWALK_OK;
+}
+
+}  // extern "C"

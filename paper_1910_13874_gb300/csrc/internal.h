@@ -1,0 +1,230 @@
+// Internal declarations shared by the library's translation units (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <shared_mutex>
+#include <string>
+#include <vector>
+
+#include "gedwalk.h"
+
+namespace gw {
+
+// ---------------------------------------------------------------- errors
+void set_error(const char* fmt, ...);
+gedwalk_status fail(gedwalk_status st, const char* fmt, ...);
+
+#define GW_CUDA(call)                                                                                 \
+  do {                                                                                                \
+    cudaError_t e_ = (call);                                                                          \
+    if (e_ != cudaSuccess)                                                                            \
+      return ::gw::fail(GEDWALK_ERR_DEVICE, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                                          \
+  } while (0)
+
+#define GW_TRY(expr)                 \
+  do {                               \
+    gedwalk_status s_ = (expr);      \
+    if (s_ != GEDWALK_OK) return s_; \
+  } while (0)
+
+// Counts a kernel launch and checks that it was accepted.
+void count_launch();
+#define GW_KCHECK()               \
+  do {                            \
+    GW_CUDA(cudaGetLastError());  \
+    ::gw::count_launch();         \
+  } while (0)
+
+// ---------------------------------------------------------------- device memory
+void* dalloc(size_t bytes, cudaStream_t s);
+void dfree(void* p, size_t bytes, cudaStream_t s);
+
+// A device buffer that grows on demand and is released with its owner.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) dfree(p, bytes, 0);
+    p = nullptr;
+    bytes = 0;
+  }
+  // Ensures capacity >= need bytes; contents are not preserved. zero: memset new storage to 0.
+  gedwalk_status ensure(size_t need, cudaStream_t s, bool zero = false);
+  template <typename T>
+  T* as() const {
+    return static_cast<T*>(p);
+  }
+};
+
+// ---------------------------------------------------------------- sweep plan
+// The masked SpMV/SpMM "sweep" y = alpha * A x runs one CTA per work unit:
+//  - a heavy slice: part of one row of degree > kHeavyDeg; slices of a row are
+//    combined by the last CTA to finish, in slice order;
+//  - a light unit: consecutive rows of one degree class, 2^lw lanes per row.
+// Units are int4: heavy {h, e0, e1, slice_id >= 0}; light {r0, r1, lw, -1}.
+constexpr int kThreads = 256;
+constexpr int kHeavyDeg = 1024;
+constexpr int kSliceEdges = 2048;
+constexpr int kUnitEdges = 4096;
+constexpr int kRowsPerGroup = 8;
+
+struct Plan {
+  int32_t num_units = 0;   // grid size: heavy slices first, then light units
+  int32_t num_slices = 0;  // heavy slices (units [0, num_slices))
+  int32_t num_heavy = 0;   // heavy rows (new ids [0, num_heavy))
+  int32_t num_slots = 0;   // num_units + num_heavy column-sum slots
+  DevBuf units;            // int4[num_units]
+  DevBuf heavy;            // int4[num_heavy]: {row, first slice, slice count, 0}
+};
+
+// ---------------------------------------------------------------- workspaces
+// Per-request scratch. The graph owns one for the synchronous API; the server
+// creates one per concurrent request slot.
+struct Workspace {
+  DevBuf x0, x1;     // walk vectors, [n][C]
+  DevBuf mtab;       // phi^miss table, [(L+1)][n]
+  DevBuf partial;    // heavy-slice partial sums, [num_slices][C]
+  DevBuf counters;   // heavy-row arrival counters, [num_heavy] (kept at 0 between launches)
+  DevBuf slots;      // column-sum slots, [num_slots][C] doubles
+  DevBuf mask;       // S bitmask, [ceil(n/32)]
+  DevBuf stale;      // greedy: {float upper bound, int step} per vertex
+  DevBuf sel;        // greedy: per-block candidate lists
+  DevBuf small;      // small device-side results
+  DevBuf members;    // batched scoring: member ids / group ids / accumulators
+  DevBuf pinned_dummy;
+  int64_t st_evals = 0, st_batches = 0, st_sweeps = 0, st_spec_miss = 0;  // last maximize
+  std::vector<uint8_t> host_small;  // staging
+  void* pinned = nullptr;           // pinned host staging buffer
+  size_t pinned_bytes = 0;
+  ~Workspace();
+  gedwalk_status ensure_pinned(size_t bytes);
+};
+
+// ---------------------------------------------------------------- graph
+struct Graph {
+  int device = 0;
+  int32_t n = 0;
+  int64_t nnz = 0;
+  int32_t dmax = 0;
+  double alpha_default = 0;
+  DevBuf rp, ci;            // relabelled CSR (new ids), ci padded by 4 entries
+  DevBuf perm_d;            // int32[n]: new -> caller id
+  std::vector<int32_t> perm;  // new -> caller id
+  std::vector<int32_t> inv;   // caller id -> new
+  std::vector<int32_t> deg;   // degree by new id
+  Plan plan;
+
+  // alpha-scaled walk totals t_r = alpha A t_{r-1}, t_0 = 1 (FP64, [rows][n]) and sums Wa[r]
+  double tt_alpha = -1.0;
+  int32_t tt_rows = 0;
+  DevBuf ttab;
+  std::vector<double> Wa;
+  // readers of ttab hold it shared; growing or replacing the table holds it exclusively
+  std::shared_mutex tt_lock;
+
+  // batched-scoring autotuner result: column-block width per graph (0 = not tuned)
+  int32_t batch_cols = 0;
+  std::vector<std::pair<int32_t, double>> tune_log;
+
+  // statistics of the last maximize
+  int64_t st_evals = 0, st_batches = 0, st_sweeps = 0, st_spec_miss = 0;
+
+  Workspace ws;    // workspace of the synchronous API
+  std::mutex mu;   // serialises calls on this handle
+};
+
+// ---------------------------------------------------------------- launchers
+enum SweepMode : int {
+  MODE_TOTALS = 0,  // y = alpha A x, FP64, stores the column sum
+  MODE_SCORE = 1,   // two-state hit/miss step, sums h
+  MODE_FUSED = 2,   // greedy: column 0 = phi^miss under S, columns 1.. candidate columns
+  MODE_CAND = 3,    // greedy: candidate columns only; candidate rows read phi^miss from a table
+  MODE_PLAIN = 4    // batched scoring: y = alpha A x, no mask
+};
+
+struct SweepArgs {
+  const int32_t* rp;
+  const int32_t* ci;
+  const int4* units;
+  const int4* heavy;
+  int32_t num_units;
+  int32_t n;
+  int64_t nnz;
+  const void* X;
+  void* Y;
+  double alpha;
+  const uint32_t* mask;
+  void* partial;
+  unsigned* counters;
+  double* slots;
+  int32_t accumulate;
+  void* Mout;
+  const void* Min;
+  const int32_t* cand;
+};
+
+// Profiling hooks around sweep launches (no-ops unless gedwalk_profile(1) was called).
+bool profiling();
+void profile_begin(cudaStream_t s, cudaEvent_t* a);
+void profile_end(cudaStream_t s, cudaEvent_t a, double bytes);
+// Algorithmic bytes of one sweep launch: CSR once, x read once, y written once, plus the mask
+// and the phi^miss row where the mode reads or writes them.
+double sweep_bytes(int mode, bool fp64, int cols, int32_t n, int64_t nnz);
+
+// Launches one sweep (instantiated for the supported (type, columns, mode) triples).
+gedwalk_status launch_sweep(int mode, bool fp64, int cols, const SweepArgs& a, cudaStream_t s);
+// Column-sum count of a mode at width cols.
+int sweep_sums(int mode, int cols);
+// out[c] = sum over slots of slots[slot][c], c < nsum, deterministic order.
+gedwalk_status launch_reduce_slots(const double* slots, int32_t num_slots, int32_t nsum, double* out,
+                                   cudaStream_t s);
+
+// Ensures workspace scratch for sweeps of width cols (partials, counters, slots).
+gedwalk_status ensure_sweep_scratch(Graph& g, Workspace& ws, int cols, bool fp64, cudaStream_t s);
+// Fills a SweepArgs with the graph/plan/scratch fields.
+SweepArgs base_args(Graph& g, Workspace& ws);
+
+// ---------------------------------------------------------------- shared algorithm helpers
+struct Resolved {
+  double alpha;
+  int32_t L;
+  double bound;  // B_L, NaN when L was forced without a valid bound
+  bool fp64;
+  cudaStream_t stream;
+};
+// Resolves alpha (0 -> default), L (from epsilon unless forced) for a given epsilon.
+gedwalk_status resolve(Graph& g, const gedwalk_params* p, double eps_override, Resolved* r);
+// Ensures the FP64 walk-total table holds rows 0..rows-1 for alpha.
+gedwalk_status ensure_totals(Graph& g, double alpha, int32_t rows, cudaStream_t s);
+// Truncation length from the combinatorial bound (device-side test); L=-1 if none <= Lcap.
+gedwalk_status truncation_length(Graph& g, double alpha, double eps, int32_t* L, double* bound, cudaStream_t s);
+// Maps caller ids to internal ids with set semantics; INVALID on out-of-range ids.
+gedwalk_status map_group(const Graph& g, const int32_t* S, int32_t s_len, std::vector<int32_t>* out);
+// Uploads the S bitmask (internal ids) into ws.mask.
+gedwalk_status upload_mask(Graph& g, Workspace& ws, const std::vector<int32_t>& S_int, cudaStream_t s);
+
+gedwalk_status score_one(Graph& g, Workspace& ws, const std::vector<int32_t>& S_int, const Resolved& r,
+                         double* score);
+// Picks the batched-scoring column width for this graph (timed once, then cached).
+gedwalk_status autotune_batch(Graph& g, Workspace& ws, const Resolved& r);
+gedwalk_status score_batch_impl(Graph& g, Workspace& ws, const int32_t* offsets, const int32_t* members_int,
+                                int32_t G, const Resolved& r, double* scores);
+gedwalk_status maximize_impl(Graph& g, Workspace& ws, int32_t k, const Resolved& r, int32_t flags,
+                             const std::vector<int32_t>& init_int, int32_t* group, double* gains, double* score);
+gedwalk_status gains_impl(Graph& g, Workspace& ws, const std::vector<int32_t>& S_int, const Resolved& r,
+                          double* gains_caller);
+
+inline Graph* G(gedwalk_graph_t h) { return reinterpret_cast<Graph*>(h); }
+
+}  // namespace gw

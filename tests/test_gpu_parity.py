@@ -1,0 +1,290 @@
+"""CUDA library vs the CPU oracle, element by element, through the C ABI.
+
+Tolerances (stated by the specification this library follows): FP64 walk vectors match the
+FP64 oracle to relative error 1e-12 per score and gain; FP32 walk vectors (FP64 sums) to 1e-5.
+The selected greedy sequence must be identical wherever the top two oracle gains differ by
+more than the tolerance; elsewhere the chosen vertex's oracle gain must be within the
+tolerance of the best one. Gains that are exactly zero (members of S, isolated vertices) must
+be exactly zero.
+
+Graphs: the 1000-vertex Erdos-Renyi graph of the small configuration (average degree 10),
+Barabasi-Albert and R-MAT graphs large enough to have rows split across several CTAs
+(degree > 1024) and many light units, plus the special graphs with closed forms.
+"""
+import functools
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 1e-5}
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return np.abs(a - b) / np.maximum(np.abs(b), 1e-300)
+
+
+@functools.lru_cache(maxsize=None)
+def host_graph(name):
+    if name == "er1000":
+        return gg.erdos_renyi(1000, 10, 1)
+    if name == "ba5000":
+        return gg.barabasi_albert(5000, 4, 2)
+    if name == "rmat14":
+        return gg.rmat(14, 16, seed=3)
+    if name == "rmat15":
+        return gg.rmat(15, 16, seed=4)
+    if name == "k8":
+        return gg.complete(8)
+    if name == "star":
+        return gg.star(40)
+    if name == "path":
+        return gg.path(50)
+    if name == "isolated":
+        return gg.from_edges(30, [(0, 1), (1, 2), (2, 0), (5, 6), (6, 7), (7, 8), (8, 5), (5, 7)])
+    raise KeyError(name)
+
+
+_dev = {}
+
+
+def dev_graph(name):
+    from paper_1910_13874_gb300 import gedwalk
+
+    if name not in _dev:
+        _dev[name] = gedwalk.Graph.from_host(host_graph(name))
+    return _dev[name]
+
+
+def groups(n, count, lo, hi, seed):
+    off, mem = gg.random_groups(n, count, lo, hi, seed)
+    return [mem[off[j]:off[j + 1]] for j in range(count)]
+
+
+# ------------------------------------------------------------------ truncation length
+@pytest.mark.parametrize("name,eps", [("er1000", 1e-6), ("er1000", 1e-3), ("ba5000", 1e-4), ("rmat14", 1e-4)])
+def test_truncation_length_matches_oracle(cuda_device, name, eps):
+    g = host_graph(name)
+    G = dev_graph(name)
+    alpha = oracle.default_alpha(g)
+    assert G.alpha_default == alpha
+    L, B = G.truncation(0.0, eps)
+    Lo, Bo = oracle.select_L(g, alpha, eps)
+    assert L == Lo
+    assert rel(B, Bo) < 1e-12
+
+
+# ------------------------------------------------------------------ scoring one group
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_score_small_config_16_groups(cuda_device, prec):
+    # the small configuration: 16 random groups of 5 vertices, epsilon 1e-6
+    g = host_graph("er1000")
+    G = dev_graph("er1000")
+    alpha = oracle.default_alpha(g)
+    for S in groups(g.n, 16, 5, 5, 42):
+        s, L, B = G.score(S, precision=prec, epsilon=1e-6)
+        Lo, Bo = oracle.select_L(g, alpha, 1e-6)
+        assert L == Lo
+        want = oracle.score(g, S, alpha, L)
+        assert rel(s, want) < TOL[prec], (S, s, want)
+        assert rel(B, Bo) < 1e-12
+
+
+@pytest.mark.parametrize("name", ["ba5000", "rmat14", "rmat15", "star", "path", "isolated"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_score_graphs(cuda_device, name, prec):
+    g = host_graph(name)
+    G = dev_graph(name)
+    alpha = oracle.default_alpha(g)
+    rng = np.random.default_rng(7)
+    for size in (1, 2, 17, 60):
+        size = min(size, g.n)
+        S = rng.choice(g.n, size=size, replace=False)
+        L = 6
+        s, Lu, _ = G.score(S, precision=prec, L=L)
+        assert Lu == L
+        want = oracle.score(g, S, alpha, L)
+        assert rel(s, want) < TOL[prec], (name, size, s, want)
+    # the highest-degree vertex (a row split over several CTAs in the R-MAT graphs)
+    hub = int(np.argmax(g.degrees))
+    s, _, _ = G.score([hub], precision=prec, L=5)
+    assert rel(s, oracle.score(g, [hub], alpha, 5)) < TOL[prec]
+
+
+def test_score_closed_forms_and_edge_cases(cuda_device):
+    from paper_1910_13874_gb300 import gedwalk
+
+    G = dev_graph("k8")
+    # K_n: phi_i = n(n-1)^i - (n-s)(n-s-1)^i; alpha = 1/8 keeps the arithmetic exact
+    n, s_, L = 8, 3, 5
+    want = sum(0.125 ** i * (n * (n - 1) ** i - (n - s_) * (n - s_ - 1) ** i) for i in range(1, L + 1))
+    for prec in ("fp64", "fp32"):
+        got, _, _ = G.score([0, 1, 2], precision=prec, alpha=0.125, L=L)
+        assert got == want
+        # duplicates are a set
+        assert G.score([2, 1, 0, 1, 2], precision=prec, alpha=0.125, L=L)[0] == want
+        assert G.score([], precision=prec, alpha=0.125, L=L)[0] == 0.0
+    # S = V gives GED_{<=L}(V) = sum_x Katz_{<=L}(x) (Prop. katz-relation)
+    gi = host_graph("isolated")
+    Gi = dev_graph("isolated")
+    alpha = oracle.default_alpha(gi)
+    _, Wa = oracle.walk_totals(gi, alpha, 6)
+    assert rel(Gi.score(np.arange(gi.n), precision="fp64", L=6)[0], Wa[1:].sum()) < 1e-12
+    # isolated vertices score exactly 0
+    assert Gi.score([20, 25], precision="fp32", L=6)[0] == 0.0
+    with pytest.raises(gedwalk.GedWalkError) as e:
+        Gi.score([0, 30], L=3)
+    assert e.value.status == gedwalk.ERR_INVALID
+    with pytest.raises(gedwalk.GedWalkError) as e:
+        Gi.score([0], alpha=0.5, epsilon=1e-4)  # alpha * d_max >= 1
+    assert e.value.status == gedwalk.ERR_NOT_CONVERGENT
+    assert Gi.score([0], alpha=0.5, L=3)[0] == pytest.approx(oracle.score(gi, [0], 0.5, 3), rel=1e-12)
+
+
+def test_upload_rejects_malformed_graphs(cuda_device):
+    from paper_1910_13874_gb300 import gedwalk
+
+    g = gg.from_edges(4, [(0, 1), (1, 2)])
+    bad_sym = g.col_idx.copy()
+    bad_sym[0] = 3  # row 0 now lists 3, row 3 does not list 0
+    for rp, ci in [(g.row_ptr, bad_sym), (g.row_ptr, np.array([1, 0, 2, 1], np.int32) * 9),
+                   (np.array([0, 1, 1, 3, 3], np.int32), np.array([0, 1, 2], np.int32))]:
+        with pytest.raises(gedwalk.GedWalkError) as e:
+            gedwalk.Graph(rp, ci)
+        assert e.value.status == gedwalk.ERR_INVALID
+
+
+# ------------------------------------------------------------------ exact gains of every vertex
+@pytest.mark.parametrize("name", ["er1000", "rmat14", "isolated"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_all_vertex_gains(cuda_device, name, prec):
+    g = host_graph(name)
+    G = dev_graph(name)
+    alpha = oracle.default_alpha(g)
+    L = 5
+    S = [int(np.argmax(g.degrees)), 3, 7]
+    gains, Lu = G.gains(S, precision=prec, L=L)
+    assert Lu == L
+    xs = range(g.n) if g.n <= 1000 else np.random.default_rng(1).choice(g.n, 300, replace=False)
+    for x in xs:
+        want = oracle.gain(g, S, int(x), alpha, L)
+        if want == 0.0:
+            assert gains[x] == 0.0, x
+        else:
+            assert rel(gains[x], want) < TOL[prec], (x, gains[x], want)
+
+
+# ------------------------------------------------------------------ greedy maximisation
+def check_greedy(g, grp, gains, alpha, L, tol, init=()):
+    """Each pick is the oracle's best next vertex for the GPU's own prefix, or within tol of it.
+
+    With a tie inside the tolerance the sequences may part; from then on every GPU pick is
+    still compared with the oracle's best continuation of the GPU's prefix.
+    """
+    S = list(init)
+    for step, v in enumerate(grp):
+        v = int(v)
+        ob, obg, _ = oracle.greedy(g, 1, alpha, L, "lazy", init=S or None)
+        gv = oracle.gain(g, S, v, alpha, L)
+        if gv == 0.0:
+            assert gains[step] == 0.0, step
+        else:
+            assert rel(gains[step], gv) < tol, (step, gains[step], gv)
+        if v != int(ob[0]):
+            assert gv >= obg[0] * (1 - tol), (step, v, gv, int(ob[0]), obg[0])
+        S.append(v)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_maximize_small_config_all_gains(cuda_device, prec):
+    # the small configuration: greedy k=5 with every vertex's exact gain compared at every step
+    g = host_graph("er1000")
+    G = dev_graph("er1000")
+    alpha = oracle.default_alpha(g)
+    grp, gains, score, L = G.maximize(5, precision=prec, epsilon=1e-6, gains_all=True)
+    L_o, _ = oracle.select_L(g, alpha, 1e-6 / 5)
+    assert L == L_o
+    ogrp, ogains, _ = oracle.greedy(g, 5, alpha, L, "all")
+    assert list(grp) == list(ogrp)
+    assert np.all(rel(gains, ogains) < TOL[prec])
+    assert rel(score, oracle.score(g, grp, alpha, L)) < TOL[prec]
+    # the pruned path chooses the same group
+    grp2, gains2, _, _ = G.maximize(5, precision=prec, epsilon=1e-6)
+    assert list(grp2) == list(grp)
+    assert np.all(rel(gains2, ogains) < TOL[prec])
+
+
+@pytest.mark.parametrize("name,k", [("ba5000", 25), ("rmat14", 25), ("rmat15", 12), ("er1000", 12)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_maximize_graphs(cuda_device, name, k, prec):
+    g = host_graph(name)
+    G = dev_graph(name)
+    alpha = oracle.default_alpha(g)
+    grp, gains, score, L = G.maximize(k, precision=prec, epsilon=1e-4)
+    assert len(set(grp.tolist())) == k
+    check_greedy(g, grp, gains, alpha, L, TOL[prec])
+    assert rel(score, oracle.score(g, grp, alpha, L)) < TOL[prec]
+
+
+def test_maximize_ties_go_to_lowest_id(cuda_device):
+    G = dev_graph("k8")
+    for prec in ("fp64", "fp32"):
+        grp, gains, _, _ = G.maximize(5, precision=prec, alpha=0.125, L=4)
+        assert list(grp) == [0, 1, 2, 3, 4]
+    # star: the centre first, then every gain is 0 and the lowest leaf follows
+    Gs = dev_graph("star")
+    grp, gains, _, _ = Gs.maximize(3, precision="fp32", L=5)
+    assert list(grp) == [0, 1, 2] and gains[1] == 0.0 and gains[2] == 0.0
+
+
+def test_maximize_isolated_and_resume(cuda_device):
+    g = host_graph("isolated")
+    G = dev_graph("isolated")
+    alpha = oracle.default_alpha(g)
+    # more picks than vertices with positive gain: zeros go to the lowest ids
+    grp, gains, _, L = G.maximize(12, precision="fp64", L=6)
+    ogrp, ogains, _ = oracle.greedy(g, 12, alpha, 6, "all")
+    assert list(grp) == list(ogrp)
+    assert np.all(rel(gains, ogains) < 1e-12)
+    # resuming from a prefix reproduces the rest
+    g2 = host_graph("rmat14")
+    G2 = dev_graph("rmat14")
+    full, fg, _, L = G2.maximize(10, precision="fp32", L=6)
+    rest, rg, _, _ = G2.maximize(6, precision="fp32", L=6, init=full[:4])
+    assert list(rest) == list(full[4:])
+    assert np.all(rel(rg, fg[4:]) < 1e-5)
+
+
+def test_determinism(cuda_device):
+    G = dev_graph("rmat15")
+    a = G.maximize(8, precision="fp32", epsilon=1e-4)
+    b = G.maximize(8, precision="fp32", epsilon=1e-4)
+    assert list(a[0]) == list(b[0]) and np.array_equal(a[1], b[1]) and a[2] == b[2]
+    S = list(range(0, 3000, 37))
+    assert G.score(S, precision="fp32", L=7)[0] == G.score(S, precision="fp32", L=7)[0]
+
+
+# ------------------------------------------------------------------ batched scoring
+@pytest.mark.parametrize("name", ["er1000", "ba5000", "rmat15"])
+def test_score_batch(cuda_device, name):
+    g = host_graph(name)
+    G = dev_graph(name)
+    alpha = oracle.default_alpha(g)
+    off, mem = gg.random_groups(g.n, 70, 1, 100, 11)
+    scores, L = G.score_batch(off, mem, epsilon=1e-4)
+    for j in range(70):
+        S = mem[off[j]:off[j + 1]]
+        assert rel(scores[j], oracle.score(g, S, alpha, L)) < 1e-5, j
+    # batch invariance: each column alone gives bitwise the same value
+    for j in (0, 33, 69):
+        one, _ = G.score_batch([0, off[j + 1] - off[j]], mem[off[j]:off[j + 1]], epsilon=1e-4)
+        assert one[0] == scores[j]
+    # empty groups and duplicate members
+    s2, _ = G.score_batch([0, 0, 4], [5, 5, 6, 5], epsilon=1e-4)
+    assert s2[0] == 0.0 and rel(s2[1], oracle.score(g, [5, 6], alpha, L)) < 1e-5
