@@ -223,13 +223,12 @@ static int64_t validate_csr(const int32_t* rp, const int32_t* ci, int32_t n, int
   return -1;
 }
 
-static int light_lanes_log2(int32_t d) {
-  if (d <= 3) return 0;
-  if (d <= 7) return 1;
-  if (d <= 15) return 2;
-  if (d <= 31) return 3;
-  if (d <= 63) return 4;
-  return 5;
+// Degree class of a light row: 2^cls lanes with at most two entries each (cls <= 5), or a
+// whole warp looping over the row (cls 6).
+static int row_class(int32_t d) {
+  int cls = 0;
+  while (cls < 6 && d > (2 << cls)) ++cls;
+  return cls;
 }
 
 static gedwalk_status build_plan(Graph& g, const std::vector<int32_t>& rp) {
@@ -250,20 +249,23 @@ static gedwalk_status build_plan(Graph& g, const std::vector<int32_t>& rp) {
   }
   g.plan.num_slices = slice;
   g.plan.num_heavy = nh;
+  // isolated rows (degree 0, sorted last) get no units: their sums are 0, nothing gathers
+  // their x, and the few outputs read back at such rows are zeroed by the callers
+  g.n_active = g.n;
+  while (g.n_active > 0 && g.deg[g.n_active - 1] == 0) --g.n_active;
   int32_t r = nh;
-  while (r < g.n) {
-    const int lw = light_lanes_log2(g.deg[r]);
-    const int ngrp = kThreads >> lw;
+  while (r < g.n_active) {
+    const int cls = row_class(g.deg[r]);
+    const int32_t max_rows = cls == 6 ? 32 : kUnitRowsMax;
+    const int64_t max_edges = cls == 6 ? kLongUnitEdges : kUnitEdges;
     int32_t r1 = r;
     int64_t edges = 0;
-    while (r1 < g.n && light_lanes_log2(g.deg[r1]) == lw) {
-      const int32_t rows = r1 - r;
-      if (rows >= ngrp * kRowsPerGroup) break;
-      if (edges >= kUnitEdges && rows >= ngrp) break;
+    while (r1 < g.n_active && row_class(g.deg[r1]) == cls && r1 - r < max_rows &&
+           (r1 == r || edges + g.deg[r1] <= max_edges)) {
       edges += g.deg[r1];
       ++r1;
     }
-    units.push_back(make_int4(r, r1, lw, -1));
+    units.push_back(make_int4(r, r1, cls, -1));
     r = r1;
   }
   g.plan.num_units = static_cast<int32_t>(units.size());
@@ -324,7 +326,12 @@ gedwalk_status ensure_sweep_scratch(Graph& g, Workspace& ws, int cols, bool fp64
   const size_t cbytes = static_cast<size_t>(std::max(g.plan.num_heavy, 1)) * sizeof(unsigned);
   if (ws.counters.bytes < cbytes || !ws.counters.p) GW_TRY(ws.counters.ensure(cbytes, s, /*zero=*/true));
   GW_TRY(ws.slots.ensure(static_cast<size_t>(std::max(g.plan.num_slots, 1)) * cols * sizeof(double), s));
+  GW_TRY(ws.parts.ensure(static_cast<size_t>(cols) * kReduceParts * sizeof(double), s));
   return GEDWALK_OK;
+}
+
+gedwalk_status reduce_slots(Graph& g, Workspace& ws, int nsum, double* out, cudaStream_t s) {
+  return launch_reduce_slots(ws.slots.as<double>(), g.plan.num_slots, nsum, out, ws.parts.as<double>(), s);
 }
 
 // ---------------------------------------------------------------- walk totals
@@ -369,8 +376,11 @@ gedwalk_status ensure_totals(Graph& g, double alpha, int32_t rows, cudaStream_t 
   for (int32_t r = r0; r < rows; ++r) {
     a.X = T + static_cast<size_t>(r - 1) * n;
     a.Y = T + static_cast<size_t>(r) * n;
+    if (g.n_active < g.n)  // isolated vertices start no walk of length >= 1
+      GW_CUDA(cudaMemsetAsync(T + static_cast<size_t>(r) * n + g.n_active, 0,
+                              sizeof(double) * (n - static_cast<size_t>(g.n_active)), s));
     GW_TRY(launch_sweep(MODE_TOTALS, true, 1, a, s));
-    GW_TRY(launch_reduce_slots(ws.slots.as<double>(), g.plan.num_slots, 1, dWa + r, s));
+    GW_TRY(reduce_slots(g, ws, 1, dWa + r, s));
   }
   std::vector<double> tmp(rows);
   GW_CUDA(cudaMemcpyAsync(tmp.data() + r0, dWa + r0, sizeof(double) * (rows - r0), cudaMemcpyDeviceToHost, s));

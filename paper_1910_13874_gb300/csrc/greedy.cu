@@ -23,6 +23,7 @@
 #include <algorithm>
 #include <climits>
 #include <cmath>
+#include <cstdlib>
 
 #include "internal.h"
 
@@ -30,7 +31,7 @@ namespace gw {
 namespace {
 
 constexpr int kTopK = 16;
-constexpr int kSelBlocks = 152 * 4;
+constexpr int kSelBlocks = 152 * 3;
 
 struct Stale {
   float ub;      // last exact gain rounded up (an upper bound for every later step)
@@ -145,8 +146,45 @@ __global__ void update_stale(Stale* __restrict__ stale, const int32_t* __restric
   stale[c] = st;
 }
 
-// Lemma-initialize bound + selection over all vertices.
+__device__ __forceinline__ float to_f32_up(float v) { return v; }
+__device__ __forceinline__ float to_f32_up(double v) { return __double2float_ru(v); }
+
+// Lemma-initialize bound of vertex x:
+//   ub(x) = sum_{i=1..L} alpha^i P_i(S, x) = sum over ordered pairs 1 <= a+b <= L of y_a(x) y_b(x)
+//         = y_0 (Q_L - y_0) + sum_{a=1..L} y_a Q_{L-a},   Q_q = sum_{b <= q} y_b,
+// y_a = alpha^a phi^miss_a(x) (psi^miss = phi^miss on an undirected graph). Evaluated in FP32
+// with every operation rounded toward +infinity on non-negative inputs (FP64 inputs are
+// first rounded up), so the result never falls below the bound of the stored vectors.
+template <typename T, int L>
+__device__ __forceinline__ float ub_fixed(const T* __restrict__ col, int32_t n) {
+  float y[L + 1];
+#pragma unroll
+  for (int a = 0; a <= L; ++a) y[a] = to_f32_up(__ldcs(col + static_cast<size_t>(a) * n));
+  float Q[L + 1];
+  Q[0] = y[0];
+  float R = 0.0f;
+#pragma unroll
+  for (int q = 1; q <= L; ++q) {
+    Q[q] = __fadd_ru(Q[q - 1], y[q]);
+    R = __fadd_ru(R, y[q]);
+  }
+  float ub = __fmul_ru(y[0], R);
+#pragma unroll
+  for (int a = 1; a <= L; ++a) ub = __fmaf_ru(y[a], Q[L - a], ub);
+  return ub;
+}
+
 template <typename T>
+__device__ float ub_any(const T* __restrict__ col, int32_t n, int32_t L) {
+  float ub = 0.0f;
+  for (int i = 1; i <= L; ++i)
+    for (int j = 0; j <= i; ++j)
+      ub = __fmaf_ru(to_f32_up(col[static_cast<size_t>(i - j) * n]), to_f32_up(col[static_cast<size_t>(j) * n]), ub);
+  return ub;
+}
+
+// Lemma-initialize bound + selection over all vertices. LF = L when L <= 16, else 0 (any L).
+template <typename T, int LF>
 __global__ void __launch_bounds__(kThreads) ub_select(const T* __restrict__ mtab, int32_t L, int32_t n,
                                                      const uint32_t* __restrict__ mask,
                                                      const Stale* __restrict__ stale, int32_t step,
@@ -163,20 +201,7 @@ __global__ void __launch_bounds__(kThreads) ub_select(const T* __restrict__ mtab
     if ((__ldg(mask + (x >> 5)) >> (x & 31)) & 1u) continue;
     const Stale st = stale[x];
     if (st.step == step) continue;  // evaluated with the current S: its exact gain is known
-    // sum over ordered pairs 1 <= a + b <= L of y_a y_b
-    //   = y_0 (Q_L - y_0) + sum_{a=1..L} y_a Q_{L-a},   Q_q = sum_{b<=q} y_b,
-    // streamed from the table; every term is non-negative, so nothing cancels
-    const T* col = mtab + x;
-    const double y0 = static_cast<double>(__ldg(col));
-    double tail = 0.0;
-    for (int a = 1; a <= L; ++a) tail += static_cast<double>(__ldg(col + static_cast<size_t>(a) * n));
-    double ub = y0 * tail;
-    double Q = y0 + tail;
-    for (int a = 1; a <= L; ++a) {
-      Q -= static_cast<double>(__ldg(col + static_cast<size_t>(L - a + 1) * n));
-      ub += static_cast<double>(__ldg(col + static_cast<size_t>(a) * n)) * Q;
-    }
-    float b = __double2float_ru(ub);
+    float b = LF > 0 ? ub_fixed<T, (LF > 0 ? LF : 1)>(mtab + x, n) : ub_any<T>(mtab + x, n, L);
     if (st.step >= 0 && st.ub < b) b = st.ub;
     if (b == 0.0f) {
       atomicMin(zero_min, __ldg(perm + x));
@@ -191,6 +216,21 @@ __global__ void __launch_bounds__(kThreads) ub_select(const T* __restrict__ mtab
     sel_v[blockIdx.x * kTopK + threadIdx.x] = ov[threadIdx.x];
     sel_id[blockIdx.x * kTopK + threadIdx.x] = oi[threadIdx.x];
   }
+}
+
+template <typename T>
+cudaError_t launch_ub_select(int nb, cudaStream_t s, const T* mtab, int32_t L, int32_t n, const uint32_t* mask,
+                             const Stale* stale, int32_t step, const int32_t* perm, float* sel_v, int* sel_id,
+                             int32_t* zero_min) {
+#define GW_UB(LL) \
+  case LL: ub_select<T, LL><<<nb, kThreads, 0, s>>>(mtab, L, n, mask, stale, step, perm, sel_v, sel_id, zero_min); break;
+  switch (L) {
+    GW_UB(1) GW_UB(2) GW_UB(3) GW_UB(4) GW_UB(5) GW_UB(6) GW_UB(7) GW_UB(8)
+    GW_UB(9) GW_UB(10) GW_UB(11) GW_UB(12) GW_UB(13) GW_UB(14) GW_UB(15) GW_UB(16)
+    default: ub_select<T, 0><<<nb, kThreads, 0, s>>>(mtab, L, n, mask, stale, step, perm, sel_v, sel_id, zero_min);
+  }
+#undef GW_UB
+  return cudaGetLastError();
 }
 
 __global__ void __launch_bounds__(kThreads) select_merge(const float* __restrict__ sel_v,
@@ -217,6 +257,15 @@ __global__ void __launch_bounds__(kThreads) select_merge(const float* __restrict
 __global__ void set_int(int32_t* p, int32_t v) { *p = v; }
 
 int blocks_for(int64_t n) { return static_cast<int>(std::min<int64_t>((n + 255) / 256, 152 * 16)); }
+
+// Rows 1..L of the phi^miss table at isolated vertices: the sweeps never write them (no walk
+// of length >= 1 ends there), so they are set to 0 once.
+gedwalk_status zero_isolated_tail(Graph& g, void* tab, size_t es, int32_t L, cudaStream_t s) {
+  if (g.n_active >= g.n || L < 1) return GEDWALK_OK;
+  char* base = static_cast<char*>(tab) + static_cast<size_t>(g.n) * es + static_cast<size_t>(g.n_active) * es;
+  GW_CUDA(cudaMemset2DAsync(base, static_cast<size_t>(g.n) * es, 0, static_cast<size_t>(g.n - g.n_active) * es, L, s));
+  return GEDWALK_OK;
+}
 
 struct Cand {
   double g;
@@ -278,7 +327,7 @@ gedwalk_status run_sweeps(GreedyCtx& c, int mode, int cols, const std::vector<in
     std::swap(cur, nxt);
   }
   const int nsum = sweep_sums(mode, cols);
-  if (nsum > 0) GW_TRY(launch_reduce_slots(ws.slots.as<double>(), g.plan.num_slots, nsum, c.d_gains, c.s));
+  if (nsum > 0) GW_TRY(reduce_slots(g, ws, nsum, c.d_gains, c.s));
   return GEDWALK_OK;
 }
 
@@ -288,7 +337,14 @@ gedwalk_status maximize_impl(Graph& g, Workspace& ws, int32_t k, const Resolved&
                              const std::vector<int32_t>& init_int, int32_t* group, double* gains, double* score) {
   cudaStream_t s = r.stream;
   const size_t es = r.fp64 ? 8 : 4;
-  const int cols_fused = r.fp64 ? 4 : 8;  // phi^miss + speculative candidates
+  // phi^miss + speculative candidates. Every gather costs one L2 sector whatever the row
+  // width, so narrow rows are cheapest; one speculative candidate certifies most steps (a
+  // miss costs one extra candidate batch). GEDWALK_SPEC_COLS (2, 4 or 8) overrides.
+  int cols_fused = 2;
+  if (const char* e = getenv("GEDWALK_SPEC_COLS")) {
+    const int v = atoi(e);
+    if (v == 2 || v == 4 || (v == 8 && !r.fp64)) cols_fused = v;
+  }
   const int n_spec = cols_fused - 1;
   const int cols_cand = r.fp64 ? 4 : 8;
   const int cols_all = r.fp64 ? 8 : 16;
@@ -298,6 +354,7 @@ gedwalk_status maximize_impl(Graph& g, Workspace& ws, int32_t k, const Resolved&
   ws.st_evals = ws.st_batches = ws.st_sweeps = ws.st_spec_miss = 0;
 
   GW_TRY(ws.mtab.ensure(static_cast<size_t>(L + 1) * g.n * es, s));
+  GW_TRY(zero_isolated_tail(g, ws.mtab.p, es, L, s));
   GW_TRY(ws.stale.ensure(static_cast<size_t>(g.n) * sizeof(Stale), s));
   GW_TRY(ws.sel.ensure(static_cast<size_t>(kSelBlocks) * kTopK * 8, s));
   GW_TRY(ws.small.ensure(sizeof(SelOut) + 16 * sizeof(int32_t) + 16 * sizeof(double) + 256, s));
@@ -363,14 +420,12 @@ gedwalk_status maximize_impl(Graph& g, Workspace& ws, int32_t k, const Resolved&
         set_int<<<1, 1, 0, s>>>(&c.d_out->zero_min_caller, INT_MAX);
         const int nb = std::max(1, std::min(kSelBlocks, blocks_for(g.n)));
         if (r.fp64)
-          ub_select<double><<<nb, kThreads, 0, s>>>(ws.mtab.as<double>(), L, g.n, ws.mask.as<uint32_t>(), stale, step,
-                                                    g.perm_d.as<int32_t>(), sel_v, sel_id,
-                                                    &c.d_out->zero_min_caller);
+          GW_CUDA(launch_ub_select<double>(nb, s, ws.mtab.as<double>(), L, g.n, ws.mask.as<uint32_t>(), stale, step,
+                                           g.perm_d.as<int32_t>(), sel_v, sel_id, &c.d_out->zero_min_caller));
         else
-          ub_select<float><<<nb, kThreads, 0, s>>>(ws.mtab.as<float>(), L, g.n, ws.mask.as<uint32_t>(), stale, step,
-                                                   g.perm_d.as<int32_t>(), sel_v, sel_id,
-                                                   &c.d_out->zero_min_caller);
-        GW_KCHECK();
+          GW_CUDA(launch_ub_select<float>(nb, s, ws.mtab.as<float>(), L, g.n, ws.mask.as<uint32_t>(), stale, step,
+                                          g.perm_d.as<int32_t>(), sel_v, sel_id, &c.d_out->zero_min_caller));
+        count_launch();
         select_merge<<<1, kThreads, 0, s>>>(sel_v, sel_id, nb * kTopK, c.d_out);
         GW_KCHECK();
         GW_CUDA(cudaMemcpyAsync(c.h_out, c.d_out, sizeof(SelOut), cudaMemcpyDeviceToHost, s));
@@ -438,6 +493,7 @@ gedwalk_status gains_impl(Graph& g, Workspace& ws, const std::vector<int32_t>& S
   const size_t es = r.fp64 ? 8 : 4;
   const int cols_all = r.fp64 ? 8 : 16;
   GW_TRY(ws.mtab.ensure(static_cast<size_t>(r.L + 1) * g.n * es, s));
+  GW_TRY(zero_isolated_tail(g, ws.mtab.p, es, r.L, s));
   GW_TRY(ws.small.ensure(sizeof(SelOut) + 16 * sizeof(int32_t) + 16 * sizeof(double) + 256, s));
   GW_TRY(upload_mask(g, ws, S_int, s));
   GreedyCtx c{g, ws, r, s, r.L, es};

@@ -68,16 +68,20 @@ struct DevBuf {
 };
 
 // ---------------------------------------------------------------- sweep plan
-// The masked SpMV/SpMM "sweep" y = alpha * A x runs one CTA per work unit:
-//  - a heavy slice: part of one row of degree > kHeavyDeg; slices of a row are
-//    combined by the last CTA to finish, in slice order;
-//  - a light unit: consecutive rows of one degree class, 2^lw lanes per row.
-// Units are int4: heavy {h, e0, e1, slice_id >= 0}; light {r0, r1, lw, -1}.
+// The masked SpMV/SpMM "sweep" y = alpha * A x runs one warp per work unit (int4):
+//  - light unit {r0, r1, cls, -1}: rows [r0, r1) of one degree class; classes 0..5 give
+//    2^cls lanes to a row of degree <= 2^(cls+1), class 6 a whole warp to a row of degree
+//    <= kHeavyDeg;
+//  - heavy slice {h, e0, e1, slice >= 0}: entries [e0, e1) of heavy row h (degree >
+//    kHeavyDeg); the slices of a row are combined by the last warp to finish, in order.
 constexpr int kThreads = 256;
 constexpr int kHeavyDeg = 1024;
-constexpr int kSliceEdges = 2048;
-constexpr int kUnitEdges = 4096;
-constexpr int kRowsPerGroup = 8;
+constexpr int kSliceEdges = 1024;
+constexpr int kUnitEdges = 1024;      // entries per short-row unit (at least one row)
+constexpr int kLongUnitEdges = 2048;  // entries per long-row unit (at least one row)
+constexpr int kUnitRowsMax = 128;     // rows per unit (short classes); long units take <= 32
+constexpr int kReduceParts = 64;      // first-stage parts of the deterministic slot reduction
+constexpr int64_t kL1HubBytes = 160 * 1024;  // x rows per SM kept in L1 with high priority
 
 struct Plan {
   int32_t num_units = 0;   // grid size: heavy slices first, then light units
@@ -97,6 +101,7 @@ struct Workspace {
   DevBuf partial;    // heavy-slice partial sums, [num_slices][C]
   DevBuf counters;   // heavy-row arrival counters, [num_heavy] (kept at 0 between launches)
   DevBuf slots;      // column-sum slots, [num_slots][C] doubles
+  DevBuf parts;      // slot-reduction partials, [C][kReduceParts] doubles
   DevBuf mask;       // S bitmask, [ceil(n/32)]
   DevBuf stale;      // greedy: {float upper bound, int step} per vertex
   DevBuf sel;        // greedy: per-block candidate lists
@@ -117,6 +122,7 @@ struct Graph {
   int32_t n = 0;
   int64_t nnz = 0;
   int32_t dmax = 0;
+  int32_t n_active = 0;     // rows with at least one entry; isolated rows are [n_active, n)
   double alpha_default = 0;
   DevBuf rp, ci;            // relabelled CSR (new ids), ci padded by 4 entries
   DevBuf perm_d;            // int32[n]: new -> caller id
@@ -172,6 +178,7 @@ struct SweepArgs {
   void* Mout;
   const void* Min;
   const int32_t* cand;
+  int32_t hub;  // rows [0, hub) of x are gathered with L1 retention priority (set by the launcher)
 };
 
 // Profiling hooks around sweep launches (no-ops unless gedwalk_profile(1) was called).
@@ -186,9 +193,11 @@ double sweep_bytes(int mode, bool fp64, int cols, int32_t n, int64_t nnz);
 gedwalk_status launch_sweep(int mode, bool fp64, int cols, const SweepArgs& a, cudaStream_t s);
 // Column-sum count of a mode at width cols.
 int sweep_sums(int mode, int cols);
-// out[c] = sum over slots of slots[slot][c], c < nsum, deterministic order.
+// out[c] = sum over slots of slots[slot][c], c < nsum, in a fixed order (parts: nsum*kReduceParts).
 gedwalk_status launch_reduce_slots(const double* slots, int32_t num_slots, int32_t nsum, double* out,
-                                   cudaStream_t s);
+                                   double* parts, cudaStream_t s);
+// The same over a workspace's slots after sweeps of width cols.
+gedwalk_status reduce_slots(Graph& g, Workspace& ws, int nsum, double* out, cudaStream_t s);
 
 // Ensures workspace scratch for sweeps of width cols (partials, counters, slots).
 gedwalk_status ensure_sweep_scratch(Graph& g, Workspace& ws, int cols, bool fp64, cudaStream_t s);

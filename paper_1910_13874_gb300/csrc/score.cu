@@ -21,10 +21,13 @@ __global__ void init_two_state(T* __restrict__ X, const uint32_t* __restrict__ m
 }
 
 // Batched scoring, first-visit form. Column j of a block is m_0 = 1_{V \ S_j}.
-__global__ void init_batch(float* __restrict__ X, int32_t n, int32_t cols, int32_t active) {
+// Isolated rows (r >= n_active) hold 0: the sweeps never write them and nothing gathers them,
+// so they read as the (zero) first-visit counts of such vertices.
+__global__ void init_batch(float* __restrict__ X, int32_t n, int32_t n_active, int32_t cols, int32_t active) {
   const size_t total = static_cast<size_t>(n) * cols;
+  const size_t live = static_cast<size_t>(n_active) * cols;
   for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < total; i += size_t(gridDim.x) * blockDim.x)
-    X[i] = (static_cast<int32_t>(i % cols) < active) ? 1.0f : 0.0f;
+    X[i] = (i < live && static_cast<int32_t>(i % cols) < active) ? 1.0f : 0.0f;
 }
 
 __global__ void zero_members(float* __restrict__ X, int32_t cols, const int32_t* __restrict__ mrow,
@@ -105,7 +108,7 @@ gedwalk_status score_one(Graph& g, Workspace& ws, const std::vector<int32_t>& S_
     GW_TRY(launch_sweep(MODE_SCORE, r.fp64, 2, a, s));
     std::swap(cur, nxt);
   }
-  GW_TRY(launch_reduce_slots(ws.slots.as<double>(), g.plan.num_slots, 1, ws.small.as<double>(), s));
+  GW_TRY(reduce_slots(g, ws, 1, ws.small.as<double>(), s));
   double h = 0;
   GW_CUDA(cudaMemcpyAsync(&h, ws.small.p, sizeof h, cudaMemcpyDeviceToHost, s));
   GW_CUDA(cudaStreamSynchronize(s));
@@ -128,7 +131,7 @@ gedwalk_status autotune_batch(Graph& g, Workspace& ws, const Resolved& r) {
     const size_t vbytes = static_cast<size_t>(g.n) * c * 4;
     if (ws.x0.ensure(vbytes, s) != GEDWALK_OK || ws.x1.ensure(vbytes, s) != GEDWALK_OK) break;
     GW_TRY(ensure_sweep_scratch(g, ws, c, false, s));
-    init_batch<<<blocks_for(static_cast<int64_t>(g.n) * c), 256, 0, s>>>(ws.x0.as<float>(), g.n, c, c);
+    init_batch<<<blocks_for(static_cast<int64_t>(g.n) * c), 256, 0, s>>>(ws.x0.as<float>(), g.n, g.n, c, c);
     GW_KCHECK();
     SweepArgs a = base_args(g, ws);
     a.alpha = r.alpha;
@@ -189,6 +192,9 @@ gedwalk_status score_batch_impl(Graph& g, Workspace& ws, const int32_t* offsets,
   const double* T = g.ttab.as<double>();
   SweepArgs a = base_args(g, ws);
   a.alpha = r.alpha;
+  if (g.n_active < g.n)
+    GW_CUDA(cudaMemsetAsync(ws.x1.as<float>() + static_cast<size_t>(g.n_active) * C, 0,
+                            sizeof(float) * C * (static_cast<size_t>(g.n) - g.n_active), s));
   if (total > 0) {
     batch_member_init<<<blocks_for(total), 256, 0, s>>>(mrow, acc, static_cast<int32_t>(total), T, g.n, r.L);
     GW_KCHECK();
@@ -197,7 +203,8 @@ gedwalk_status score_batch_impl(Graph& g, Workspace& ws, const int32_t* offsets,
     const int32_t g1 = std::min(G, g0 + C);
     const int32_t m0 = offsets[g0], m1 = offsets[g1];
     const int32_t cnt = m1 - m0;
-    init_batch<<<blocks_for(static_cast<int64_t>(g.n) * C), 256, 0, s>>>(ws.x0.as<float>(), g.n, C, g1 - g0);
+    init_batch<<<blocks_for(static_cast<int64_t>(g.n) * C), 256, 0, s>>>(ws.x0.as<float>(), g.n, g.n_active, C,
+                                                                          g1 - g0);
     GW_KCHECK();
     if (cnt > 0) {
       zero_members<<<blocks_for(cnt), 256, 0, s>>>(ws.x0.as<float>(), C, mrow + m0, mcol + m0, cnt);

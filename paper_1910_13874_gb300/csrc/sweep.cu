@@ -7,19 +7,27 @@
 // feed the Lemma-initialize bound, and the candidate columns that count the
 // walks through a vertex (proof of Prop. ged_submod).
 //
-// Work distribution (the graph is relabelled by decreasing degree, so rows of
-// similar degree are contiguous):
-//  - light units: a CTA takes consecutive rows of one degree class and gives
-//    each row 2^lw lanes; lanes stride over the row's entries, gather the C-wide
-//    rows of x (16-byte vector loads) and reduce with xor shuffles;
-//  - heavy slices: rows of degree > kHeavyDeg are cut into slices of about
-//    kSliceEdges entries, one CTA per slice; each CTA writes its partial sum,
-//    and the last CTA to arrive (atomic counter) adds the partials in slice
-//    order and runs the epilogue. No CTA ever waits for another.
-// Column sums (sum_v y(v) per column, FP64) are reduced per CTA in a fixed order
-// into per-CTA slots, so every result is bitwise reproducible.
+// Work distribution. The graph is relabelled by decreasing degree, so rows of
+// similar degree are contiguous, and the host cuts the rows into warp-sized
+// units (no CTA-wide barrier anywhere after the prologue):
+//  - short rows (degree <= 64): W lanes per row with 2W >= degree, so every lane
+//    gathers at most two entries; a warp handles two rows per group per
+//    iteration and issues all of their loads before reducing (4 gathers in
+//    flight per lane);
+//  - long rows (64 < degree <= kHeavyDeg): one warp per row, entries strided
+//    over the lanes in groups of four loads;
+//  - heavy rows (degree > kHeavyDeg): cut into slices of about kSliceEdges
+//    entries, one warp per slice; each writes its partial sum and the last warp
+//    to arrive (atomic counter) adds the partials in slice order and finishes
+//    the row. No warp ever waits for another.
+// A row's C-wide sum is reduce-scattered across its lanes (halving the columns
+// at every shuffle step), so each lane ends with its own columns and the
+// epilogue runs column-parallel. Column sums (sum_v y(v), FP64) are reduced per
+// warp in a fixed order into per-unit slots: every result is bitwise
+// reproducible.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "internal.h"
@@ -28,273 +36,481 @@ namespace gw {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kWarps = kThreads / 32;
 
-template <typename T>
-__device__ __forceinline__ T ldx(const T* p) {
-  return __ldg(p);
-}
+template <int X>
+struct Log2 {
+  static constexpr int v = 1 + Log2<X / 2>::v;
+};
+template <>
+struct Log2<1> {
+  static constexpr int v = 0;
+};
 
-// acc[c] += X[v][c] for c < C with the widest aligned vector loads.
-template <typename T, int C>
-__device__ __forceinline__ void add_row(T (&acc)[C], const T* __restrict__ X, int v) {
-  constexpr int kBytes = int(sizeof(T)) * C;
-  const T* p = X + static_cast<size_t>(v) * C;
+// p[0..N) -> out with the widest aligned vector loads (through the read-only path).
+template <typename T, int N>
+__device__ __forceinline__ void load_vec(const T* __restrict__ p, T (&out)[N]) {
+  constexpr int kBytes = int(sizeof(T)) * N;
   if constexpr (kBytes % 16 == 0) {
     constexpr int kPer = 16 / int(sizeof(T));
-    const float4* q = reinterpret_cast<const float4*>(p);
 #pragma unroll
     for (int k = 0; k < kBytes / 16; ++k) {
-      float4 t = __ldg(q + k);
-      T vals[kPer];
-      memcpy(vals, &t, 16);
-#pragma unroll
-      for (int e = 0; e < kPer; ++e) acc[k * kPer + e] += vals[e];
+      const float4 t = __ldg(reinterpret_cast<const float4*>(p) + k);
+      memcpy(&out[k * kPer], &t, 16);
     }
   } else if constexpr (kBytes == 8) {
-    float2 t = __ldg(reinterpret_cast<const float2*>(p));
-    T vals[8 / sizeof(T)];
-    memcpy(vals, &t, 8);
-#pragma unroll
-    for (int e = 0; e < C; ++e) acc[e] += vals[e];
+    const float2 t = __ldg(reinterpret_cast<const float2*>(p));
+    memcpy(out, &t, 8);
   } else {
 #pragma unroll
-    for (int e = 0; e < C; ++e) acc[e] += ldx(p + e);
+    for (int e = 0; e < N; ++e) out[e] = __ldg(p + e);
   }
 }
 
-// Y[r][0..C) = vals with vector stores.
-template <typename T, int C>
-__device__ __forceinline__ void store_row(T* __restrict__ Y, int r, const T (&vals)[C]) {
-  constexpr int kBytes = int(sizeof(T)) * C;
-  T* p = Y + static_cast<size_t>(r) * C;
+template <typename T, int N>
+__device__ __forceinline__ void store_vec(T* __restrict__ p, const T (&v)[N]) {
+  constexpr int kBytes = int(sizeof(T)) * N;
   if constexpr (kBytes % 16 == 0) {
-    float4* q = reinterpret_cast<float4*>(p);
+    constexpr int kPer = 16 / int(sizeof(T));
 #pragma unroll
     for (int k = 0; k < kBytes / 16; ++k) {
       float4 t;
-      memcpy(&t, &vals[k * (16 / int(sizeof(T)))], 16);
-      q[k] = t;
+      memcpy(&t, &v[k * kPer], 16);
+      reinterpret_cast<float4*>(p)[k] = t;
     }
   } else if constexpr (kBytes == 8) {
     float2 t;
-    memcpy(&t, vals, 8);
+    memcpy(&t, v, 8);
     *reinterpret_cast<float2*>(p) = t;
   } else {
 #pragma unroll
-    for (int e = 0; e < C; ++e) p[e] = vals[e];
+    for (int e = 0; e < N; ++e) p[e] = v[e];
   }
+}
+
+// Gathers of x rows. Vertices are numbered by decreasing degree, so the rows with the
+// lowest ids are gathered most often: rows below the hub limit are loaded with high L1
+// retention priority, all others without allocating in L1, so the stream of cold rows
+// cannot flush the hot ones. 32-byte rows take a single 256-bit load.
+#define GW_LD1(Q, TY, R, x, p) asm volatile("ld.global.nc." Q "." TY " %0, [%1];" : "=" R(x[0]) : "l"(p))
+#define GW_LD2(Q, TY, R, x, p) \
+  asm volatile("ld.global.nc." Q ".v2." TY " {%0,%1}, [%2];" : "=" R(x[0]), "=" R(x[1]) : "l"(p))
+#define GW_LD4(Q, TY, R, x, p)                                                                        \
+  asm volatile("ld.global.nc." Q ".v4." TY " {%0,%1,%2,%3}, [%4];" : "=" R(x[0]), "=" R(x[1]), "=" R(x[2]), \
+               "=" R(x[3]) : "l"(p))
+#define GW_LD8(Q, x, p)                                                                                 \
+  asm volatile("ld.global.nc." Q ".v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"                              \
+               : "=f"(x[0]), "=f"(x[1]), "=f"(x[2]), "=f"(x[3]), "=f"(x[4]), "=f"(x[5]), "=f"(x[6]), \
+                 "=f"(x[7])                                                                             \
+               : "l"(p))
+
+template <typename T, int N, bool HOT>
+__device__ __forceinline__ void gather_vec(const T* __restrict__ p, T* x) {
+  if constexpr (sizeof(T) == 4) {
+    if constexpr (N == 1) {
+      if (HOT) GW_LD1("L1::evict_last", "f32", "f", x, p); else GW_LD1("L1::no_allocate", "f32", "f", x, p);
+    } else if constexpr (N == 2) {
+      if (HOT) GW_LD2("L1::evict_last", "f32", "f", x, p); else GW_LD2("L1::no_allocate", "f32", "f", x, p);
+    } else if constexpr (N == 4) {
+      if (HOT) GW_LD4("L1::evict_last", "f32", "f", x, p); else GW_LD4("L1::no_allocate", "f32", "f", x, p);
+    } else {
+#pragma unroll
+      for (int k = 0; k < N / 8; ++k) {
+        if (HOT) GW_LD8("L1::evict_last", (x + 8 * k), (p + 8 * k));
+        else GW_LD8("L1::no_allocate", (x + 8 * k), (p + 8 * k));
+      }
+    }
+  } else {
+    if constexpr (N == 1) {
+      if (HOT) GW_LD1("L1::evict_last", "f64", "d", x, p); else GW_LD1("L1::no_allocate", "f64", "d", x, p);
+    } else if constexpr (N == 2) {
+      if (HOT) GW_LD2("L1::evict_last", "f64", "d", x, p); else GW_LD2("L1::no_allocate", "f64", "d", x, p);
+    } else {
+#pragma unroll
+      for (int k = 0; k < N / 4; ++k) {
+        if (HOT) GW_LD4("L1::evict_last", "f64", "d", (x + 4 * k), (p + 4 * k));
+        else GW_LD4("L1::no_allocate", "f64", "d", (x + 4 * k), (p + 4 * k));
+      }
+    }
+  }
+}
+
+template <typename T, int C>
+__device__ __forceinline__ void add_row(T (&acc)[C], const T* __restrict__ X, int v, int hub) {
+  T x[C];
+  const T* p = X + static_cast<size_t>(v) * C;
+  if (v < hub) gather_vec<T, C, true>(p, x);
+  else gather_vec<T, C, false>(p, x);
+#pragma unroll
+  for (int c = 0; c < C; ++c) acc[c] += x[c];
+}
+
+// Column indices are streamed once per sweep: keep them out of L1 (which holds the gathered
+// rows of x) and first in line for eviction from L2.
+__device__ __forceinline__ uint64_t stream_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+
+__device__ __forceinline__ int ld_idx(const int32_t* p, uint64_t pol) {
+  int v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+  return v;
 }
 
 __device__ __forceinline__ bool in_mask(const uint32_t* __restrict__ mask, int r) {
   return (__ldg(mask + (r >> 5)) >> (r & 31)) & 1u;
 }
 
-// Number of FP64 column sums a mode keeps.
+// Reduce-scatter of the C-wide partial sums held by the W = 2^LW lanes of a group.
+// On return acc[0..CPL) holds the group totals of columns [blk*CPL, (blk+1)*CPL) with
+// blk = lane & (2^HS - 1), HS = min(log2 C, LW), CPL = C >> HS: each halving step keeps
+// the upper or lower half of the held columns by one lane bit, highest bit first, so
+// the blocks come out in natural order. Every lane of the warp must take part.
+template <typename T, int C, int LW>
+struct Scatter {
+  static constexpr int LC = Log2<C>::v;
+  static constexpr int HS = LC < LW ? LC : LW;
+  static constexpr int CPL = C >> HS;
+  __device__ __forceinline__ static void run(T (&acc)[C], int lane) {
+#pragma unroll
+    for (int st = HS - 1; st >= 0; --st) {
+      const int o = 1 << st;
+      const bool up = (lane & o) != 0;
+      const int half = (C >> (HS - 1 - st)) / 2;
+#pragma unroll
+      for (int i = 0; i < C / 2; ++i) {
+        if (i < half) {
+          const T send = up ? acc[i] : acc[i + half];
+          const T keep = up ? acc[i + half] : acc[i];
+          acc[i] = keep + __shfl_xor_sync(kFull, send, o);
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 1 << HS; o < (1 << LW); o <<= 1)
+#pragma unroll
+      for (int i = 0; i < CPL; ++i) acc[i] += __shfl_xor_sync(kFull, acc[i], o);
+  }
+};
+
+// Number of FP64 column sums a mode keeps; column c feeds sum (c - first).
 template <int MODE, int C>
 struct Sums {
   static constexpr int N = MODE == MODE_TOTALS ? 1 : MODE == MODE_SCORE ? 1 : MODE == MODE_FUSED ? C - 1
                            : MODE == MODE_CAND ? C : 0;
-  static constexpr int A = N > 0 ? N : 1;  // storage
+  static constexpr int first = MODE == MODE_FUSED ? 1 : 0;
 };
 
-// The per-row epilogue. acc holds sum_{u ~ r} x(u) for each column.
-template <typename T, int C, int MODE>
-__device__ __forceinline__ void epilogue(const SweepArgs& a, const int* __restrict__ s_cand, int r,
-                                         const T (&acc)[C], double (&cs)[Sums<MODE, C>::A]) {
+// Column-parallel epilogue for row r. The calling lane holds the totals s[0..CPL) of
+// columns c0 .. c0+CPL-1; base is the first lane of the row's group. Every lane of the
+// warp calls it (shuffles inside); `store` marks the lanes that own distinct columns of a
+// valid row. cs accumulates this lane's column sums (FP64).
+template <typename T, int C, int MODE, int CPL>
+__device__ __forceinline__ void epilogue(const SweepArgs& a, const int* __restrict__ s_cand, int r, bool valid,
+                                         bool store, int c0, int base, T (&s)[CPL], double (&cs)[CPL]) {
   const T alpha = static_cast<T>(a.alpha);
   T* Y = static_cast<T*>(a.Y);
-  if constexpr (MODE == MODE_TOTALS) {
-    T out[C];
-    out[0] = alpha * acc[0];
-    store_row<T, C>(Y, r, out);
-    cs[0] += static_cast<double>(out[0]);
-  } else if constexpr (MODE == MODE_SCORE) {
+  constexpr bool kMasked = MODE == MODE_SCORE || MODE == MODE_FUSED || MODE == MODE_CAND;
+  const bool inS = kMasked && valid ? in_mask(a.mask, r) : false;
+  if constexpr (MODE == MODE_SCORE) {
     // Section 3.1.1: hit_i(v) = sum hit_{i-1}(u) + [v in S] sum miss_{i-1}(u);
-    //                miss_i(v) = [v not in S] sum miss_{i-1}(u)
-    const bool inS = in_mask(a.mask, r);
-    T out[C];
-    out[0] = alpha * (inS ? acc[0] + acc[1] : acc[0]);
-    out[1] = inS ? T(0) : alpha * acc[1];
-    store_row<T, C>(Y, r, out);
-    cs[0] += static_cast<double>(out[0]);
-  } else if constexpr (MODE == MODE_FUSED) {
-    // column 0: phi^miss under S; columns j >= 1: walks through candidate c_j that avoid S,
-    // whose row c_j takes the phi^miss value (every S-avoiding walk ending at c_j visits it)
-    const bool inS = in_mask(a.mask, r);
-    T out[C];
-    out[0] = inS ? T(0) : alpha * acc[0];
-#pragma unroll
-    for (int j = 1; j < C; ++j) {
-      T y = inS ? T(0) : alpha * acc[j];
-      if (s_cand[j - 1] == r) y = out[0];
-      out[j] = y;
-      cs[j - 1] += static_cast<double>(y);
+    //                miss_i(v) = [v not in S] sum miss_{i-1}(u).  Columns: 0 = hit, 1 = miss.
+    T sh, sm;
+    if constexpr (CPL == 2) {
+      sh = s[0];
+      sm = s[1];
+    } else {
+      sh = s[0];
+      sm = __shfl_sync(kFull, s[0], base + 1);
     }
-    store_row<T, C>(Y, r, out);
-    static_cast<T*>(a.Mout)[r] = out[0];
-  } else if constexpr (MODE == MODE_CAND) {
-    const bool inS = in_mask(a.mask, r);
-    T out[C];
-#pragma unroll
-    for (int j = 0; j < C; ++j) {
-      T y = inS ? T(0) : alpha * acc[j];
-      if (s_cand[j] == r) y = __ldg(static_cast<const T*>(a.Min) + r);
-      out[j] = y;
-      cs[j] += static_cast<double>(y);
+    if (store && c0 == 0) {
+      T out[2];
+      out[0] = alpha * (inS ? sh + sm : sh);
+      out[1] = inS ? T(0) : alpha * sm;
+      store_vec<T, 2>(Y + static_cast<size_t>(r) * C, out);
+      cs[0] += static_cast<double>(out[0]);
     }
-    store_row<T, C>(Y, r, out);
-  } else {  // MODE_PLAIN
-    T out[C];
+  } else {
+    T y[CPL];
 #pragma unroll
-    for (int j = 0; j < C; ++j) out[j] = alpha * acc[j];
-    store_row<T, C>(Y, r, out);
+    for (int k = 0; k < CPL; ++k) y[k] = inS ? T(0) : alpha * s[k];
+    if constexpr (MODE == MODE_FUSED) {
+      // column 0 is phi^miss under S; candidate column j >= 1 takes it at the candidate's row
+      // (every S-avoiding walk ending at c_j visits c_j)
+      const T m = __shfl_sync(kFull, y[0], base);
+#pragma unroll
+      for (int k = 0; k < CPL; ++k) {
+        const int c = c0 + k;
+        if (c >= 1 && s_cand[c - 1] == r) y[k] = m;
+      }
+      if (store && c0 == 0) static_cast<T*>(a.Mout)[r] = y[0];
+    } else if constexpr (MODE == MODE_CAND) {
+#pragma unroll
+      for (int k = 0; k < CPL; ++k)
+        if (valid && s_cand[c0 + k] == r) y[k] = __ldg(static_cast<const T*>(a.Min) + r);
+    }
+    if (store) {
+      store_vec<T, CPL>(Y + static_cast<size_t>(r) * C + c0, y);
+      if constexpr (Sums<MODE, C>::N > 0) {
+#pragma unroll
+        for (int k = 0; k < CPL; ++k) cs[k] += static_cast<double>(y[k]);
+      }
+    }
   }
 }
 
-// Deterministic block sum: thread 0 receives the totals.
-template <typename V, int N>
-__device__ __forceinline__ void block_sum(V (&v)[N], V (*sm)[N]) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// Writes this lane's column sums (already reduced over the warp) to slot `slot`.
+template <int MODE, int C, int CPL>
+__device__ __forceinline__ void write_slot(const SweepArgs& a, size_t slot, int c0, const double (&cs)[CPL]) {
+  constexpr int NS = Sums<MODE, C>::N;
+  constexpr int F = Sums<MODE, C>::first;
+  if constexpr (NS > 0) {
+    double* dst = a.slots + slot * NS;
 #pragma unroll
-  for (int c = 0; c < N; ++c)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_down_sync(kFull, v[c], o);
-  if (lane == 0)
-#pragma unroll
-    for (int c = 0; c < N; ++c) sm[warp][c] = v[c];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int c = 0; c < N; ++c) {
-      V s = sm[0][c];
-      for (int w = 1; w < kThreads / 32; ++w) s += sm[w][c];
-      v[c] = s;
+    for (int k = 0; k < CPL; ++k) {
+      const int c = c0 + k;
+      if (c >= F && c - F < NS) dst[c - F] = a.accumulate ? dst[c - F] + cs[k] : cs[k];
     }
   }
-  __syncthreads();
+}
+
+// Short rows (degree <= 2W): W lanes per row, at most two entries per lane, two rows per group.
+template <typename T, int C, int MODE, int LW>
+__device__ __forceinline__ void short_rows(const SweepArgs& a, const int4 u, int uidx, int lane, int* s_rp,
+                                          const int* s_cand) {
+  constexpr int W = 1 << LW;
+  constexpr int NG = 32 / W;
+  using SC = Scatter<T, C, LW>;
+  constexpr int CPL = SC::CPL;
+  const int r0 = u.x, nrows = u.y - u.x;
+  for (int i = lane; i <= nrows; i += 32) s_rp[i] = __ldcs(a.rp + r0 + i);
+  __syncwarp();
+  const int g = lane >> LW, gl = lane & (W - 1);
+  const int base = lane & ~(W - 1);
+  const int blk = gl & ((1 << SC::HS) - 1);
+  const bool owner = (gl >> SC::HS) == 0;
+  const int c0 = blk * CPL;
+  const T* __restrict__ X = static_cast<const T*>(a.X);
+  const int32_t* __restrict__ ci = a.ci;
+  const uint64_t pol = stream_policy();
+  double cs[CPL];
+#pragma unroll
+  for (int k = 0; k < CPL; ++k) cs[k] = 0.0;
+  for (int it = 0; it < nrows; it += 2 * NG) {
+    const int ra = it + g, rb = it + NG + g;
+    const bool va = ra < nrows, vb = rb < nrows;
+    int ea0 = 0, ea1 = 0, eb0 = 0, eb1 = 0;
+    if (va) {
+      ea0 = s_rp[ra];
+      ea1 = s_rp[ra + 1];
+    }
+    if (vb) {
+      eb0 = s_rp[rb];
+      eb1 = s_rp[rb + 1];
+    }
+    // all index loads first, then all gathers
+    const int ja0 = ea0 + gl, ja1 = ea0 + gl + W, jb0 = eb0 + gl, jb1 = eb0 + gl + W;
+    const int va0 = ja0 < ea1 ? ld_idx(ci + ja0, pol) : -1;
+    const int va1 = ja1 < ea1 ? ld_idx(ci + ja1, pol) : -1;
+    const int vb0 = jb0 < eb1 ? ld_idx(ci + jb0, pol) : -1;
+    const int vb1 = jb1 < eb1 ? ld_idx(ci + jb1, pol) : -1;
+    T acca[C], accb[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      acca[c] = T(0);
+      accb[c] = T(0);
+    }
+    if (va0 >= 0) add_row<T, C>(acca, X, va0, a.hub);
+    if (va1 >= 0) add_row<T, C>(acca, X, va1, a.hub);
+    if (vb0 >= 0) add_row<T, C>(accb, X, vb0, a.hub);
+    if (vb1 >= 0) add_row<T, C>(accb, X, vb1, a.hub);
+    SC::run(acca, lane);
+    SC::run(accb, lane);
+    T sa[CPL], sb[CPL];
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) {
+      sa[k] = acca[k];
+      sb[k] = accb[k];
+    }
+    epilogue<T, C, MODE, CPL>(a, s_cand, r0 + ra, va, va && owner, c0, base, sa, cs);
+    epilogue<T, C, MODE, CPL>(a, s_cand, r0 + rb, vb, vb && owner, c0, base, sb, cs);
+  }
+  // sum the groups' copies of each column (non-owners hold zeros)
+#pragma unroll
+  for (int o = W; o < 32; o <<= 1)
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) cs[k] += __shfl_xor_sync(kFull, cs[k], o);
+  if (lane < W && owner) write_slot<MODE, C, CPL>(a, static_cast<size_t>(uidx), c0, cs);
+}
+
+// Long rows: one warp per row, entries strided over the lanes in groups of four loads.
+template <typename T, int C, int MODE>
+__device__ __forceinline__ void long_rows(const SweepArgs& a, const int4 u, int uidx, int lane, int* s_rp,
+                                         const int* s_cand) {
+  using SC = Scatter<T, C, 5>;
+  constexpr int CPL = SC::CPL;
+  const int r0 = u.x, nrows = u.y - u.x;
+  for (int i = lane; i <= nrows; i += 32) s_rp[i] = __ldcs(a.rp + r0 + i);
+  __syncwarp();
+  const int blk = lane & ((1 << SC::HS) - 1);
+  const bool owner = (lane >> SC::HS) == 0;
+  const int c0 = blk * CPL;
+  const T* __restrict__ X = static_cast<const T*>(a.X);
+  const int32_t* __restrict__ ci = a.ci;
+  const uint64_t pol = stream_policy();
+  double cs[CPL];
+#pragma unroll
+  for (int k = 0; k < CPL; ++k) cs[k] = 0.0;
+  for (int rr = 0; rr < nrows; ++rr) {
+    const int e0 = s_rp[rr], e1 = s_rp[rr + 1];
+    T acc[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) acc[c] = T(0);
+    int j = e0 + lane;
+    for (; j + 96 < e1; j += 128) {
+      const int v0 = ld_idx(ci + j, pol), v1 = ld_idx(ci + j + 32, pol), v2 = ld_idx(ci + j + 64, pol),
+                v3 = ld_idx(ci + j + 96, pol);
+      add_row<T, C>(acc, X, v0, a.hub);
+      add_row<T, C>(acc, X, v1, a.hub);
+      add_row<T, C>(acc, X, v2, a.hub);
+      add_row<T, C>(acc, X, v3, a.hub);
+    }
+    for (; j < e1; j += 32) add_row<T, C>(acc, X, ld_idx(ci + j, pol), a.hub);
+    SC::run(acc, lane);
+    T s[CPL];
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) s[k] = acc[k];
+    epilogue<T, C, MODE, CPL>(a, s_cand, r0 + rr, true, owner, c0, 0, s, cs);
+  }
+  if (owner) write_slot<MODE, C, CPL>(a, static_cast<size_t>(uidx), c0, cs);
+}
+
+// Heavy slice: entries [u.y, u.z) of heavy row u.x, slice u.w.
+template <typename T, int C, int MODE>
+__device__ __forceinline__ void heavy_slice(const SweepArgs& a, const int4 u, int uidx, int lane,
+                                           const int* s_cand) {
+  using SC = Scatter<T, C, 5>;
+  constexpr int CPL = SC::CPL;
+  constexpr int NS = Sums<MODE, C>::N;
+  const int blk = lane & ((1 << SC::HS) - 1);
+  const bool owner = (lane >> SC::HS) == 0;
+  const int c0 = blk * CPL;
+  const T* __restrict__ X = static_cast<const T*>(a.X);
+  const int32_t* __restrict__ ci = a.ci;
+  const uint64_t pol = stream_policy();
+  T acc[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c) acc[c] = T(0);
+  int j = u.y + lane;
+  for (; j + 96 < u.z; j += 128) {
+    const int v0 = ld_idx(ci + j, pol), v1 = ld_idx(ci + j + 32, pol), v2 = ld_idx(ci + j + 64, pol),
+              v3 = ld_idx(ci + j + 96, pol);
+    add_row<T, C>(acc, X, v0, a.hub);
+    add_row<T, C>(acc, X, v1, a.hub);
+    add_row<T, C>(acc, X, v2, a.hub);
+    add_row<T, C>(acc, X, v3, a.hub);
+  }
+  for (; j < u.z; j += 32) add_row<T, C>(acc, X, ld_idx(ci + j, pol), a.hub);
+  SC::run(acc, lane);
+  // this unit's own slot carries nothing: the row's sums go to the heavy row's slot
+  if constexpr (NS > 0) {
+    if (lane < NS) a.slots[static_cast<size_t>(uidx) * NS + lane] = 0.0;
+  }
+  const int4 hr = a.heavy[u.x];  // {row, first slice, slice count, 0}
+  T* part = static_cast<T*>(a.partial);
+  if (owner) {
+    T s[CPL];
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) s[k] = acc[k];
+    store_vec<T, CPL>(part + static_cast<size_t>(u.w) * C + c0, s);
+  }
+  __threadfence();
+  __syncwarp();
+  unsigned prev = 0;
+  if (lane == 0) prev = atomicAdd(a.counters + u.x, 1u);
+  prev = __shfl_sync(kFull, prev, 0);
+  if (prev != static_cast<unsigned>(hr.z - 1)) return;  // warp-uniform
+  __threadfence();
+  T tot[CPL];
+#pragma unroll
+  for (int k = 0; k < CPL; ++k) tot[k] = T(0);
+  for (int s = hr.y; s < hr.y + hr.z; ++s)
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) tot[k] += __ldcg(part + static_cast<size_t>(s) * C + c0 + k);
+  double cs[CPL];
+#pragma unroll
+  for (int k = 0; k < CPL; ++k) cs[k] = 0.0;
+  epilogue<T, C, MODE, CPL>(a, s_cand, hr.x, true, owner, c0, 0, tot, cs);
+  if (owner) write_slot<MODE, C, CPL>(a, static_cast<size_t>(a.num_units + u.x), c0, cs);
+  if (lane == 0) a.counters[u.x] = 0u;  // ready for the next launch
 }
 
 template <typename T, int C, int MODE>
 __global__ void __launch_bounds__(kThreads) sweep_kernel(const SweepArgs a) {
-  constexpr int NS = Sums<MODE, C>::N;
-  constexpr int NA = Sums<MODE, C>::A;
-  __shared__ int s_cand[C];
-  __shared__ double s_cs[kThreads / 32][NA];
-  __shared__ T s_acc[kThreads / 32][C];
-  __shared__ int s_last;
-  if (threadIdx.x < C)
+  constexpr int kCand = 16;
+  __shared__ int s_cand[kCand];
+  __shared__ int s_rp[kWarps][kUnitRowsMax + 1];
+  if (threadIdx.x < kCand)
     s_cand[threadIdx.x] = (MODE == MODE_FUSED || MODE == MODE_CAND) && a.cand ? a.cand[threadIdx.x] : -1;
   __syncthreads();
-
-  const int4 u = a.units[blockIdx.x];
-  const int32_t* __restrict__ ci = a.ci;
-  const T* __restrict__ X = static_cast<const T*>(a.X);
-  double cs[NA];
-#pragma unroll
-  for (int c = 0; c < NA; ++c) cs[c] = 0.0;
-
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int uidx = blockIdx.x * kWarps + warp;
+  if (uidx >= a.num_units) return;
+  const int4 u = a.units[uidx];
   if (u.w >= 0) {
-    // ---- heavy slice: entries [u.y, u.z) of heavy row u.x
-    T acc[C];
-#pragma unroll
-    for (int c = 0; c < C; ++c) acc[c] = T(0);
-    int j = u.y + threadIdx.x;
-    for (; j + 3 * kThreads < u.z; j += 4 * kThreads) {
-      const int v0 = __ldcs(ci + j), v1 = __ldcs(ci + j + kThreads), v2 = __ldcs(ci + j + 2 * kThreads),
-                v3 = __ldcs(ci + j + 3 * kThreads);
-      add_row<T, C>(acc, X, v0);
-      add_row<T, C>(acc, X, v1);
-      add_row<T, C>(acc, X, v2);
-      add_row<T, C>(acc, X, v3);
-    }
-    for (; j < u.z; j += kThreads) add_row<T, C>(acc, X, __ldcs(ci + j));
-    block_sum<T, C>(acc, s_acc);
-    const int4 hr = a.heavy[u.x];  // {row, first slice, slice count, 0}
-    if constexpr (NS > 0) {
-      // this CTA's own slot carries nothing: the row's sums go to the heavy row's slot
-      if (threadIdx.x < NS) a.slots[static_cast<size_t>(blockIdx.x) * NS + threadIdx.x] = 0.0;
-    }
-    if (threadIdx.x == 0) {
-      T* part = static_cast<T*>(a.partial) + static_cast<size_t>(u.w) * C;
-#pragma unroll
-      for (int c = 0; c < C; ++c) part[c] = acc[c];
-      __threadfence();
-      const unsigned prev = atomicAdd(a.counters + u.x, 1u);
-      s_last = (prev == static_cast<unsigned>(hr.z - 1));
-    }
-    __syncthreads();
-    if (s_last && threadIdx.x == 0) {
-      __threadfence();
-      T tot[C];
-#pragma unroll
-      for (int c = 0; c < C; ++c) tot[c] = T(0);
-      const T* part = static_cast<const T*>(a.partial);
-      for (int s = hr.y; s < hr.y + hr.z; ++s)
-#pragma unroll
-        for (int c = 0; c < C; ++c) tot[c] += __ldcg(part + static_cast<size_t>(s) * C + c);
-      epilogue<T, C, MODE>(a, s_cand, hr.x, tot, cs);
-      if constexpr (NS > 0) {
-        double* slot = a.slots + static_cast<size_t>(a.num_units + u.x) * NS;
-#pragma unroll
-        for (int c = 0; c < NS; ++c) slot[c] = a.accumulate ? slot[c] + cs[c] : cs[c];
-      }
-      a.counters[u.x] = 0u;  // ready for the next launch
-    }
+    heavy_slice<T, C, MODE>(a, u, uidx, lane, s_cand);
     return;
   }
-
-  // ---- light unit: rows [u.x, u.y), 2^u.z lanes per row
-  const int lw = u.z;
-  const int w = 1 << lw;
-  const int lane = threadIdx.x & (w - 1);
-  const int grp = threadIdx.x >> lw;
-  const int ngrp = kThreads >> lw;
-  const int rows = u.y - u.x;
-  const int iters = (rows + ngrp - 1) / ngrp;
-  for (int it = 0; it < iters; ++it) {
-    const int r = u.x + it * ngrp + grp;
-    const bool valid = r < u.y;
-    T acc[C];
-#pragma unroll
-    for (int c = 0; c < C; ++c) acc[c] = T(0);
-    if (valid) {
-      const int e0 = __ldcs(a.rp + r), e1 = __ldcs(a.rp + r + 1);
-      int j = e0 + lane;
-      for (; j + 3 * w < e1; j += 4 * w) {
-        const int v0 = __ldcs(ci + j), v1 = __ldcs(ci + j + w), v2 = __ldcs(ci + j + 2 * w),
-                  v3 = __ldcs(ci + j + 3 * w);
-        add_row<T, C>(acc, X, v0);
-        add_row<T, C>(acc, X, v1);
-        add_row<T, C>(acc, X, v2);
-        add_row<T, C>(acc, X, v3);
-      }
-      for (; j < e1; j += w) add_row<T, C>(acc, X, __ldcs(ci + j));
-    }
-    // butterfly over the row's lanes; every lane of the warp takes part
-    for (int o = w >> 1; o > 0; o >>= 1)
-#pragma unroll
-      for (int c = 0; c < C; ++c) acc[c] += __shfl_xor_sync(kFull, acc[c], o);
-    if (valid && lane == 0) epilogue<T, C, MODE>(a, s_cand, r, acc, cs);
-  }
-  if constexpr (NS > 0) {
-    block_sum<double, NA>(cs, s_cs);
-    if (threadIdx.x == 0) {
-      double* slot = a.slots + static_cast<size_t>(blockIdx.x) * NS;
-#pragma unroll
-      for (int c = 0; c < NS; ++c) slot[c] = a.accumulate ? slot[c] + cs[c] : cs[c];
-    }
+  int* rp = s_rp[warp];
+  switch (u.z) {
+    case 0: short_rows<T, C, MODE, 0>(a, u, uidx, lane, rp, s_cand); break;
+    case 1: short_rows<T, C, MODE, 1>(a, u, uidx, lane, rp, s_cand); break;
+    case 2: short_rows<T, C, MODE, 2>(a, u, uidx, lane, rp, s_cand); break;
+    case 3: short_rows<T, C, MODE, 3>(a, u, uidx, lane, rp, s_cand); break;
+    case 4: short_rows<T, C, MODE, 4>(a, u, uidx, lane, rp, s_cand); break;
+    case 5: short_rows<T, C, MODE, 5>(a, u, uidx, lane, rp, s_cand); break;
+    default: long_rows<T, C, MODE>(a, u, uidx, lane, rp, s_cand); break;
   }
 }
 
-// Sum of slots[i][c] over i, one CTA per column, fixed order.
-__global__ void __launch_bounds__(kThreads) reduce_slots_kernel(const double* __restrict__ slots, int32_t num_slots,
-                                                               int32_t nsum, double* __restrict__ out) {
-  __shared__ double sm[kThreads / 32][1];
-  const int c = blockIdx.x;
-  double v[1] = {0.0};
-  for (int i = threadIdx.x; i < num_slots; i += kThreads) v[0] += slots[static_cast<size_t>(i) * nsum + c];
-  block_sum<double, 1>(v, sm);
-  if (threadIdx.x == 0) out[c] = v[0];
+// Deterministic block sum: thread 0 receives the total.
+__device__ __forceinline__ double block_sum1(double v, double* sm) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+  if (lane == 0) sm[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = sm[0];
+    for (int w = 1; w < kWarps; ++w) s += sm[w];
+    v = s;
+  }
+  __syncthreads();
+  return v;
+}
+
+// Stage 1: CTA (part, c) sums a fixed stretch of slots for column c; stage 2 adds the
+// stretches in order.
+__global__ void __launch_bounds__(kThreads) reduce_slots_part(const double* __restrict__ slots, int32_t num_slots,
+                                                             int32_t nsum, double* __restrict__ parts) {
+  __shared__ double sm[kWarps];
+  const int c = blockIdx.y, part = blockIdx.x;
+  const int per = (num_slots + kReduceParts - 1) / kReduceParts;
+  const int lo = part * per, hi = min(num_slots, lo + per);
+  double v = 0.0;
+  for (int i = lo + threadIdx.x; i < hi; i += kThreads) v += slots[static_cast<size_t>(i) * nsum + c];
+  v = block_sum1(v, sm);
+  if (threadIdx.x == 0) parts[c * kReduceParts + part] = v;
+}
+
+__global__ void reduce_slots_final(const double* __restrict__ parts, int32_t nsum, double* __restrict__ out) {
+  const int c = threadIdx.x;
+  if (c >= nsum) return;
+  double s = 0.0;
+  for (int p = 0; p < kReduceParts; ++p) s += parts[c * kReduceParts + p];
+  out[c] = s;
 }
 
 template <typename T, int C, int MODE>
@@ -303,7 +519,16 @@ gedwalk_status run(const SweepArgs& a, cudaStream_t s) {
   cudaEvent_t ev = nullptr;
   const bool prof = profiling();
   if (prof) profile_begin(s, &ev);
-  sweep_kernel<T, C, MODE><<<a.num_units, kThreads, 0, s>>>(a);
+  static bool configured = false;  // small shared-memory carveout: the rest of the unified
+  if (!configured) {                 // L1/shared array caches the gathered rows of x
+    cudaFuncSetAttribute(sweep_kernel<T, C, MODE>, cudaFuncAttributePreferredSharedMemoryCarveout, 16);
+    cudaGetLastError();
+    configured = true;
+  }
+  const int grid = (a.num_units + kWarps - 1) / kWarps;
+  SweepArgs b = a;  // rows gathered with L1 priority: about kL1HubBytes of them
+  b.hub = static_cast<int32_t>(std::min<int64_t>(a.n, kL1HubBytes / (sizeof(T) * C)));
+  sweep_kernel<T, C, MODE><<<grid, kThreads, 0, s>>>(b);
   GW_KCHECK();
   if (prof) profile_end(s, ev, sweep_bytes(MODE, sizeof(T) == 8, C, a.n, a.nnz));
   return GEDWALK_OK;
@@ -332,8 +557,11 @@ gedwalk_status launch_sweep(int mode, bool fp64, int cols, const SweepArgs& a, c
   GW_CASE(MODE_SCORE, double, 2)
   GW_CASE(MODE_SCORE, float, 2)
   GW_CASE(MODE_FUSED, float, 1)
+  GW_CASE(MODE_FUSED, float, 2)
+  GW_CASE(MODE_FUSED, float, 4)
   GW_CASE(MODE_FUSED, float, 8)
   GW_CASE(MODE_FUSED, double, 1)
+  GW_CASE(MODE_FUSED, double, 2)
   GW_CASE(MODE_FUSED, double, 4)
   GW_CASE(MODE_CAND, float, 8)
   GW_CASE(MODE_CAND, float, 16)
@@ -348,9 +576,11 @@ gedwalk_status launch_sweep(int mode, bool fp64, int cols, const SweepArgs& a, c
 }
 
 gedwalk_status launch_reduce_slots(const double* slots, int32_t num_slots, int32_t nsum, double* out,
-                                   cudaStream_t s) {
+                                   double* parts, cudaStream_t s) {
   if (nsum <= 0) return GEDWALK_OK;
-  reduce_slots_kernel<<<nsum, kThreads, 0, s>>>(slots, num_slots, nsum, out);
+  reduce_slots_part<<<dim3(kReduceParts, nsum), kThreads, 0, s>>>(slots, num_slots, nsum, parts);
+  GW_KCHECK();
+  reduce_slots_final<<<1, 32, 0, s>>>(parts, nsum, out);
   GW_KCHECK();
   return GEDWALK_OK;
 }
