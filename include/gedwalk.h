@@ -258,6 +258,37 @@ GEDWALK_API gedwalk_status gedwalk_serve_stats(gedwalk_server_t srv, int64_t* co
 /* Stops the scheduler after the requests in flight finish; pending requests are dropped. */
 GEDWALK_API gedwalk_status gedwalk_serve_destroy(gedwalk_server_t srv);
 
+/*
+ * One step of the two-state hit/miss recurrence on caller-owned device memory,
+ * allocating nothing. The paper has no counterpart: this exists for callers that
+ * cannot allocate device memory, such as code running after its framework has
+ * given the whole GPU to its own memory pool, or services that forbid device
+ * allocation (its latency and its failure modes) once they are serving. Every
+ * other entry point allocates workspaces; this one calls no cudaMalloc, cudaFree
+ * or other allocating routine.
+ *  d_row_ptr, d_col_idx: device int32[n+1] / int32[nnz], an undirected CSR as in
+ *    gedwalk_graph_upload (not validated here; caller ids, no relabelling).
+ *  d_mask: device uint32[ceil(n/32)], bit v set iff v is in S.
+ *  d_x: device float[n][2], (hit, miss) of the previous length; d_y receives the
+ *    next length. Both 8-byte aligned; they must not overlap. A score starts from
+ *    x = (1_S, 1_{V\S}) and applies the step L times, swapping x and y.
+ *  alpha: the damping factor (> 0).
+ *  d_hit_sum: device double[1], receives sum_v hit'(v), i.e. alpha^i phi_i(S) of
+ *    this step (Eq. phisum); the score is the sum over the L steps.
+ *  stream: cudaStream_t (0 = default). The call is asynchronous.
+ * Scratch: a fixed 512 KiB device array inside the library (per GPU, held until
+ * the process exits) limits n to 16,777,216; larger n returns
+ * GEDWALK_ERR_INVALID. The first call on each device looks up that array's
+ * address, so make the first call on a device before any stream capture. All
+ * calls share the array, so calls that overlap on the GPU (different streams,
+ * no ordering between them) race and give wrong sums.
+ * Errors: INVALID (NULL pointer, n out of range, alpha <= 0, misalignment),
+ * DEVICE (launch failure).
+ */
+GEDWALK_API gedwalk_status gedwalk_score_step_noalloc(const int32_t* d_row_ptr, const int32_t* d_col_idx, int32_t n,
+                                                      const uint32_t* d_mask, const float* d_x, float* d_y,
+                                                      double alpha, double* d_hit_sum, int64_t stream);
+
 /* ---------------------------------------------------------------------------
  * Profiling: CUDA events around every sweep-kernel launch (the masked SpMV/SpMM
  * step of every algorithm above) and a count of all kernel launches.

@@ -31,8 +31,8 @@ EXPORTS = [
     "gedwalk_params_default", "gedwalk_set_allocator", "gedwalk_graph_upload", "gedwalk_graph_free",
     "gedwalk_graph_info", "gedwalk_truncation", "gedwalk_score", "gedwalk_score_batch", "gedwalk_gains",
     "gedwalk_maximize", "gedwalk_maximize_stats", "gedwalk_serve_create", "gedwalk_serve_submit",
-    "gedwalk_serve_poll", "gedwalk_serve_stats", "gedwalk_serve_destroy", "gedwalk_profile",
-    "gedwalk_profile_read", "gedwalk_last_error",
+    "gedwalk_serve_poll", "gedwalk_serve_stats", "gedwalk_serve_destroy", "gedwalk_score_step_noalloc",
+    "gedwalk_profile", "gedwalk_profile_read", "gedwalk_last_error",
 ]
 
 
@@ -110,6 +110,8 @@ def load(path: Optional[str] = None):
                                                   _i32p]),
             "gedwalk_serve_stats": (ctypes.c_int, [vp, _i64p, _i64p, _i64p, _i64p]),
             "gedwalk_serve_destroy": (ctypes.c_int, [vp]),
+            "gedwalk_score_step_noalloc": (ctypes.c_int, [vp, vp, ctypes.c_int32, vp, vp, vp, ctypes.c_double, vp,
+                                                          ctypes.c_int64]),
             "gedwalk_profile": (ctypes.c_int, [ctypes.c_int32]),
             "gedwalk_profile_read": (ctypes.c_int, [ctypes.POINTER(ProfileStats)]),
             "gedwalk_last_error": (ctypes.c_char_p, []),
@@ -173,6 +175,12 @@ def use_torch_allocator():
     hooks = (_ALLOC_FN(_alloc), _FREE_FN(_free))
     _check(load().gedwalk_set_allocator(hooks[0], hooks[1], None))
     _torch_hooks = hooks
+
+
+def score_step_noalloc(d_row_ptr: int, d_col_idx: int, n: int, d_mask: int, d_x: int, d_y: int, alpha: float,
+                       d_hit_sum: int, stream: int = 0):
+    """One two-state step on caller-owned device buffers (raw device addresses); allocates nothing."""
+    _check(load().gedwalk_score_step_noalloc(d_row_ptr, d_col_idx, n, d_mask, d_x, d_y, alpha, d_hit_sum, stream))
 
 
 def profile(enable: bool = True):
