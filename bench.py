@@ -131,6 +131,50 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+MODE_NAMES = {0: "totals", 1: "two-state score", 2: "fused greedy", 3: "candidate batch", 4: "batched scoring"}
+
+
+def recorded_traffic(top, workload_key):
+    """Per-launch DRAM bytes of the dominant kernel from a committed ncu summary, or None.
+
+    The summary applies only to the same kernel instantiation on the same workload and only while
+    the sweep kernel's device code is unchanged since the counters were taken.
+    """
+    from paper_1910_13874_gb300.kernel_hash import sweep_kernel_hash
+
+    files = {("rmat22", 2, 2, 0): "sweep_fused_f2_rmat22.md"}
+    name = files.get((workload_key, top["top_mode"], top["top_cols"], top["top_fp64"]))
+    if not name:
+        return None
+    path = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if ":" in line and line.split(":")[0].strip() in ("traffic_bytes_per_launch", "sweep_kernel_source_hash"):
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("sweep_kernel_source_hash") != sweep_kernel_hash():
+        return None
+    return int(vals["traffic_bytes_per_launch"]) if "traffic_bytes_per_launch" in vals else None
+
+
+def roofline(prof, workload_key):
+    hbm, peak_kind = measured_peaks()
+    ms, by, n = prof["top_ms"], prof["top_bytes"], prof["top_launches"]
+    achieved = by / (ms / 1e3) / 1e9 if ms > 0 else 0.0
+    all_ach = prof["sweep_bytes"] / (prof["sweep_ms"] / 1e3) / 1e9 if prof["sweep_ms"] > 0 else 0.0
+    kname = (f"sweep_kernel<{'double' if prof['top_fp64'] else 'float'}, {prof['top_cols']}, "
+             f"{prof['top_mode']}> ({MODE_NAMES.get(prof['top_mode'], '?')})")
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+            "frac": round(achieved / hbm, 4), "traffic": recorded_traffic(prof, workload_key),
+            "peak_kind": peak_kind, "kernel": kname, "launches_timed": n,
+            "avg_launch_us": round(ms / max(n, 1) * 1e3, 1),
+            "algorithmic_bytes_per_launch": round(by / max(n, 1)),
+            "all_sweeps": {"achieved": round(all_ach, 1), "frac": round(all_ach / hbm, 4),
+                           "launches": prof["sweep_launches"]}}
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -223,8 +267,6 @@ def run_greedy(args, spec, rank, world, local):
     stats = G.maximize_stats()
     t_step = dist_max(e0.elapsed_time(e1) / 1e3 / args.steps, world)
     gteps = k * 2 * L * G.nnz / t_step / 1e9 * world
-    hbm, peak_kind = measured_peaks()
-    achieved = prof["sweep_bytes"] / (prof["sweep_ms"] / 1e3) / 1e9 if prof["sweep_ms"] > 0 else 0.0
     out = {
         "metric": METRIC, "value": round(gteps, 3), "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(t_step * 1e3, 3), "higher_is_better": True,
@@ -234,10 +276,7 @@ def run_greedy(args, spec, rank, world, local):
                    "epsilon": spec["eps"], "L": L, "k": k, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (CSR %.0f MB)" % ((G.nnz + G.n) * 4 / 1e6)},
         "seconds": round(t_step, 4),
-        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                     "frac": round(achieved / hbm, 4), "traffic": None,
-                     "peak_kind": peak_kind, "kernel": "sweep_kernel (all sweeps of the timed region)",
-                     "launches_timed": prof["sweep_launches"]},
+        "roofline": roofline(prof, f"rmat{args.scale}" if args.workload == "rmat" else args.workload),
         "gpu_launches": prof["launches"],
         "clocks": clk,
         "greedy": {"evaluations": stats["evaluations"], "batches": stats["batches"],
@@ -309,8 +348,6 @@ def run_batch(args, spec, rank, world, local):
     for j in range(sample):
         G.score(mem[off[j]:off[j + 1]], params=p64)
     t64 = (time.perf_counter() - t0) / sample
-    hbm, peak_kind = measured_peaks()
-    achieved = prof["sweep_bytes"] / (prof["sweep_ms"] / 1e3) / 1e9 if prof["sweep_ms"] > 0 else 0.0
     out = {
         "metric": "group-score queries/s (batched FP32 scoring)", "value": round(qps, 1), "unit": "queries/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t * 1e3, 3),
@@ -320,9 +357,7 @@ def run_batch(args, spec, rank, world, local):
                    "member_total": int(off[-1]), "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (CSR %.0f MB)" % ((G.nnz + G.n) * 4 / 1e6)},
         "fp64_per_group_queries_s": round(1.0 / t64, 1), "speedup_vs_fp64_per_group": round(qps / world * t64, 2),
-        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                     "frac": round(achieved / hbm, 4), "traffic": None, "peak_kind": peak_kind,
-                     "kernel": "sweep_kernel MODE_PLAIN", "launches_timed": prof["sweep_launches"]},
+        "roofline": roofline(prof, "batch"),
         "gpu_launches": prof["launches"], "clocks": clk,
         "e2e": {"value": round(qps, 1), "unit": "queries/s", "h2d_bytes_per_step": int(mem.nbytes + off.nbytes),
                 "d2h_bytes_per_step": int(8 * spec["groups"]),

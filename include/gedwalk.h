@@ -298,6 +298,14 @@ typedef struct {
   int64_t sweep_launches;  /* sweep-kernel launches timed */
   double sweep_ms;         /* summed device time of those launches (CUDA events on their stream) */
   double sweep_bytes;      /* summed algorithmic bytes of those launches (see the design notes) */
+  /* the sweep instantiation with the largest summed time: */
+  int32_t top_mode;        /* 0 totals, 1 two-state score, 2 fused greedy, 3 candidates, 4 batched */
+  int32_t top_cols;        /* columns per row */
+  int32_t top_fp64;        /* 1 for FP64 rows */
+  int32_t top_pad;
+  int64_t top_launches;
+  double top_ms;
+  double top_bytes;
 } gedwalk_profile_stats;
 
 /* enable != 0 starts timing sweep launches; every call resets the counters. */

@@ -43,6 +43,7 @@ struct Profiler {
   struct Rec {
     cudaEvent_t a, b;
     double bytes;
+    int key;  // (mode * 1000 + cols) * 2 + fp64
   };
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> pool;
@@ -76,7 +77,7 @@ void profile_begin(cudaStream_t s, cudaEvent_t* a) {
   if (*a) cudaEventRecord(*a, s);
 }
 
-void profile_end(cudaStream_t s, cudaEvent_t a, double bytes) {
+void profile_end(cudaStream_t s, cudaEvent_t a, double bytes, int key) {
   Profiler& p = prof();
   std::lock_guard<std::mutex> lk(p.mu);
   if (!a) return;
@@ -86,7 +87,7 @@ void profile_end(cudaStream_t s, cudaEvent_t a, double bytes) {
     return;
   }
   cudaEventRecord(b, s);
-  p.recs.push_back({a, b, bytes});
+  p.recs.push_back({a, b, bytes, key});
 }
 
 double sweep_bytes(int mode, bool fp64, int cols, int32_t n, int64_t nnz) {
@@ -515,17 +516,42 @@ gedwalk_status gedwalk_profile_read(gedwalk_profile_stats* out) {
   Profiler& p = prof();
   std::lock_guard<std::mutex> lk(p.mu);
   double ms = 0.0, bytes = 0.0;
+  struct Agg {
+    int64_t n = 0;
+    double ms = 0.0, bytes = 0.0;
+  };
+  std::vector<std::pair<int, Agg>> per;
   for (auto& r : p.recs) {
     GW_CUDA(cudaEventSynchronize(r.b));
     float t = 0.0f;
     GW_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
     ms += t;
     bytes += r.bytes;
+    auto it = std::find_if(per.begin(), per.end(), [&](const std::pair<int, Agg>& e) { return e.first == r.key; });
+    if (it == per.end()) {
+      per.push_back({r.key, Agg()});
+      it = per.end() - 1;
+    }
+    it->second.n++;
+    it->second.ms += t;
+    it->second.bytes += r.bytes;
   }
+  *out = gedwalk_profile_stats{};
   out->launches = p.launches.load();
   out->sweep_launches = static_cast<int64_t>(p.recs.size());
   out->sweep_ms = ms;
   out->sweep_bytes = bytes;
+  const std::pair<int, Agg>* top = nullptr;
+  for (const auto& e : per)
+    if (!top || e.second.ms > top->second.ms) top = &e;
+  if (top) {
+    out->top_fp64 = top->first % 2;
+    out->top_cols = (top->first / 2) % 1000;
+    out->top_mode = (top->first / 2) / 1000;
+    out->top_launches = top->second.n;
+    out->top_ms = top->second.ms;
+    out->top_bytes = top->second.bytes;
+  }
   return GEDWALK_OK;
 }
 

@@ -184,7 +184,7 @@ struct SweepArgs {
 // Profiling hooks around sweep launches (no-ops unless gedwalk_profile(1) was called).
 bool profiling();
 void profile_begin(cudaStream_t s, cudaEvent_t* a);
-void profile_end(cudaStream_t s, cudaEvent_t a, double bytes);
+void profile_end(cudaStream_t s, cudaEvent_t a, double bytes, int key);
 // Algorithmic bytes of one sweep launch: CSR once, x read once, y written once, plus the mask
 // and the phi^miss row where the mode reads or writes them.
 double sweep_bytes(int mode, bool fp64, int cols, int32_t n, int64_t nnz);

@@ -35,6 +35,7 @@
 namespace gw {
 namespace {
 
+// [sweep-kernel-source-begin] (the profiles record a hash of the device code up to the end marker)
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWarps = kThreads / 32;
 
@@ -144,6 +145,15 @@ __device__ __forceinline__ void add_row(T (&acc)[C], const T* __restrict__ X, in
 #pragma unroll
   for (int c = 0; c < C; ++c) acc[c] += x[c];
 }
+
+// Where gathered rows of x come from.
+// GlobalSrc: global memory, rows below `hub` with L1 retention priority.
+template <typename T, int C>
+struct GlobalSrc {
+  const T* __restrict__ X;
+  int hub;
+  __device__ __forceinline__ void add(T (&acc)[C], int v) const { add_row<T, C>(acc, X, v, hub); }
+};
 
 // Column indices are streamed once per sweep: keep them out of L1 (which holds the gathered
 // rows of x) and first in line for eviction from L2.
@@ -277,9 +287,9 @@ __device__ __forceinline__ void write_slot(const SweepArgs& a, size_t slot, int 
 }
 
 // Short rows (degree <= 2W): W lanes per row, at most two entries per lane, two rows per group.
-template <typename T, int C, int MODE, int LW>
-__device__ __forceinline__ void short_rows(const SweepArgs& a, const int4 u, int uidx, int lane, int* s_rp,
-                                          const int* s_cand) {
+template <typename T, int C, int MODE, int LW, class Src>
+__device__ __forceinline__ void short_rows(const SweepArgs& a, const Src& src, const int4 u, int uidx, int lane,
+                                          int* s_rp, const int* s_cand) {
   constexpr int W = 1 << LW;
   constexpr int NG = 32 / W;
   using SC = Scatter<T, C, LW>;
@@ -292,7 +302,6 @@ __device__ __forceinline__ void short_rows(const SweepArgs& a, const int4 u, int
   const int blk = gl & ((1 << SC::HS) - 1);
   const bool owner = (gl >> SC::HS) == 0;
   const int c0 = blk * CPL;
-  const T* __restrict__ X = static_cast<const T*>(a.X);
   const int32_t* __restrict__ ci = a.ci;
   const uint64_t pol = stream_policy();
   double cs[CPL];
@@ -322,10 +331,10 @@ __device__ __forceinline__ void short_rows(const SweepArgs& a, const int4 u, int
       acca[c] = T(0);
       accb[c] = T(0);
     }
-    if (va0 >= 0) add_row<T, C>(acca, X, va0, a.hub);
-    if (va1 >= 0) add_row<T, C>(acca, X, va1, a.hub);
-    if (vb0 >= 0) add_row<T, C>(accb, X, vb0, a.hub);
-    if (vb1 >= 0) add_row<T, C>(accb, X, vb1, a.hub);
+    if (va0 >= 0) src.add(acca, va0);
+    if (va1 >= 0) src.add(acca, va1);
+    if (vb0 >= 0) src.add(accb, vb0);
+    if (vb1 >= 0) src.add(accb, vb1);
     SC::run(acca, lane);
     SC::run(accb, lane);
     T sa[CPL], sb[CPL];
@@ -346,9 +355,9 @@ __device__ __forceinline__ void short_rows(const SweepArgs& a, const int4 u, int
 }
 
 // Long rows: one warp per row, entries strided over the lanes in groups of four loads.
-template <typename T, int C, int MODE>
-__device__ __forceinline__ void long_rows(const SweepArgs& a, const int4 u, int uidx, int lane, int* s_rp,
-                                         const int* s_cand) {
+template <typename T, int C, int MODE, class Src>
+__device__ __forceinline__ void long_rows(const SweepArgs& a, const Src& src, const int4 u, int uidx, int lane,
+                                         int* s_rp, const int* s_cand) {
   using SC = Scatter<T, C, 5>;
   constexpr int CPL = SC::CPL;
   const int r0 = u.x, nrows = u.y - u.x;
@@ -357,7 +366,6 @@ __device__ __forceinline__ void long_rows(const SweepArgs& a, const int4 u, int 
   const int blk = lane & ((1 << SC::HS) - 1);
   const bool owner = (lane >> SC::HS) == 0;
   const int c0 = blk * CPL;
-  const T* __restrict__ X = static_cast<const T*>(a.X);
   const int32_t* __restrict__ ci = a.ci;
   const uint64_t pol = stream_policy();
   double cs[CPL];
@@ -372,12 +380,12 @@ __device__ __forceinline__ void long_rows(const SweepArgs& a, const int4 u, int 
     for (; j + 96 < e1; j += 128) {
       const int v0 = ld_idx(ci + j, pol), v1 = ld_idx(ci + j + 32, pol), v2 = ld_idx(ci + j + 64, pol),
                 v3 = ld_idx(ci + j + 96, pol);
-      add_row<T, C>(acc, X, v0, a.hub);
-      add_row<T, C>(acc, X, v1, a.hub);
-      add_row<T, C>(acc, X, v2, a.hub);
-      add_row<T, C>(acc, X, v3, a.hub);
+      src.add(acc, v0);
+      src.add(acc, v1);
+      src.add(acc, v2);
+      src.add(acc, v3);
     }
-    for (; j < e1; j += 32) add_row<T, C>(acc, X, ld_idx(ci + j, pol), a.hub);
+    for (; j < e1; j += 32) src.add(acc, ld_idx(ci + j, pol));
     SC::run(acc, lane);
     T s[CPL];
 #pragma unroll
@@ -388,8 +396,8 @@ __device__ __forceinline__ void long_rows(const SweepArgs& a, const int4 u, int 
 }
 
 // Heavy slice: entries [u.y, u.z) of heavy row u.x, slice u.w.
-template <typename T, int C, int MODE>
-__device__ __forceinline__ void heavy_slice(const SweepArgs& a, const int4 u, int uidx, int lane,
+template <typename T, int C, int MODE, class Src>
+__device__ __forceinline__ void heavy_slice(const SweepArgs& a, const Src& src, const int4 u, int uidx, int lane,
                                            const int* s_cand) {
   using SC = Scatter<T, C, 5>;
   constexpr int CPL = SC::CPL;
@@ -397,7 +405,6 @@ __device__ __forceinline__ void heavy_slice(const SweepArgs& a, const int4 u, in
   const int blk = lane & ((1 << SC::HS) - 1);
   const bool owner = (lane >> SC::HS) == 0;
   const int c0 = blk * CPL;
-  const T* __restrict__ X = static_cast<const T*>(a.X);
   const int32_t* __restrict__ ci = a.ci;
   const uint64_t pol = stream_policy();
   T acc[C];
@@ -407,12 +414,12 @@ __device__ __forceinline__ void heavy_slice(const SweepArgs& a, const int4 u, in
   for (; j + 96 < u.z; j += 128) {
     const int v0 = ld_idx(ci + j, pol), v1 = ld_idx(ci + j + 32, pol), v2 = ld_idx(ci + j + 64, pol),
               v3 = ld_idx(ci + j + 96, pol);
-    add_row<T, C>(acc, X, v0, a.hub);
-    add_row<T, C>(acc, X, v1, a.hub);
-    add_row<T, C>(acc, X, v2, a.hub);
-    add_row<T, C>(acc, X, v3, a.hub);
+    src.add(acc, v0);
+    src.add(acc, v1);
+    src.add(acc, v2);
+    src.add(acc, v3);
   }
-  for (; j < u.z; j += 32) add_row<T, C>(acc, X, ld_idx(ci + j, pol), a.hub);
+  for (; j < u.z; j += 32) src.add(acc, ld_idx(ci + j, pol));
   SC::run(acc, lane);
   // this unit's own slot carries nothing: the row's sums go to the heavy row's slot
   if constexpr (NS > 0) {
@@ -447,33 +454,44 @@ __device__ __forceinline__ void heavy_slice(const SweepArgs& a, const int4 u, in
   if (lane == 0) a.counters[u.x] = 0u;  // ready for the next launch
 }
 
+// Runs work unit uidx with the given gather source.
+template <typename T, int C, int MODE, class Src>
+__device__ __forceinline__ void run_unit(const SweepArgs& a, const Src& src, int uidx, int lane, int* rp,
+                                        const int* s_cand) {
+  const int4 u = a.units[uidx];
+  if (u.w >= 0) {
+    heavy_slice<T, C, MODE>(a, src, u, uidx, lane, s_cand);
+    return;
+  }
+  switch (u.z) {
+    case 0: short_rows<T, C, MODE, 0>(a, src, u, uidx, lane, rp, s_cand); break;
+    case 1: short_rows<T, C, MODE, 1>(a, src, u, uidx, lane, rp, s_cand); break;
+    case 2: short_rows<T, C, MODE, 2>(a, src, u, uidx, lane, rp, s_cand); break;
+    case 3: short_rows<T, C, MODE, 3>(a, src, u, uidx, lane, rp, s_cand); break;
+    case 4: short_rows<T, C, MODE, 4>(a, src, u, uidx, lane, rp, s_cand); break;
+    case 5: short_rows<T, C, MODE, 5>(a, src, u, uidx, lane, rp, s_cand); break;
+    default: long_rows<T, C, MODE>(a, src, u, uidx, lane, rp, s_cand); break;
+  }
+}
+
+constexpr int kCandSlots = 16;
+
+// One warp per unit, one CTA per eight units.
 template <typename T, int C, int MODE>
 __global__ void __launch_bounds__(kThreads) sweep_kernel(const SweepArgs a) {
-  constexpr int kCand = 16;
-  __shared__ int s_cand[kCand];
+  __shared__ int s_cand[kCandSlots];
   __shared__ int s_rp[kWarps][kUnitRowsMax + 1];
-  if (threadIdx.x < kCand)
+  if (threadIdx.x < kCandSlots)
     s_cand[threadIdx.x] = (MODE == MODE_FUSED || MODE == MODE_CAND) && a.cand ? a.cand[threadIdx.x] : -1;
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int uidx = blockIdx.x * kWarps + warp;
   if (uidx >= a.num_units) return;
-  const int4 u = a.units[uidx];
-  if (u.w >= 0) {
-    heavy_slice<T, C, MODE>(a, u, uidx, lane, s_cand);
-    return;
-  }
-  int* rp = s_rp[warp];
-  switch (u.z) {
-    case 0: short_rows<T, C, MODE, 0>(a, u, uidx, lane, rp, s_cand); break;
-    case 1: short_rows<T, C, MODE, 1>(a, u, uidx, lane, rp, s_cand); break;
-    case 2: short_rows<T, C, MODE, 2>(a, u, uidx, lane, rp, s_cand); break;
-    case 3: short_rows<T, C, MODE, 3>(a, u, uidx, lane, rp, s_cand); break;
-    case 4: short_rows<T, C, MODE, 4>(a, u, uidx, lane, rp, s_cand); break;
-    case 5: short_rows<T, C, MODE, 5>(a, u, uidx, lane, rp, s_cand); break;
-    default: long_rows<T, C, MODE>(a, u, uidx, lane, rp, s_cand); break;
-  }
+  const GlobalSrc<T, C> src{static_cast<const T*>(a.X), a.hub};
+  run_unit<T, C, MODE>(a, src, uidx, lane, s_rp[warp], s_cand);
 }
+
+// [sweep-kernel-source-end]
 
 // Deterministic block sum: thread 0 receives the total.
 __device__ __forceinline__ double block_sum1(double v, double* sm) {
@@ -520,7 +538,7 @@ gedwalk_status run(const SweepArgs& a, cudaStream_t s) {
   const bool prof = profiling();
   if (prof) profile_begin(s, &ev);
   static bool configured = false;  // small shared-memory carveout: the rest of the unified
-  if (!configured) {                 // L1/shared array caches the gathered rows of x
+  if (!configured) {               // L1/shared array caches the gathered rows of x
     cudaFuncSetAttribute(sweep_kernel<T, C, MODE>, cudaFuncAttributePreferredSharedMemoryCarveout, 16);
     cudaGetLastError();
     configured = true;
@@ -530,7 +548,7 @@ gedwalk_status run(const SweepArgs& a, cudaStream_t s) {
   b.hub = static_cast<int32_t>(std::min<int64_t>(a.n, kL1HubBytes / (sizeof(T) * C)));
   sweep_kernel<T, C, MODE><<<grid, kThreads, 0, s>>>(b);
   GW_KCHECK();
-  if (prof) profile_end(s, ev, sweep_bytes(MODE, sizeof(T) == 8, C, a.n, a.nnz));
+  if (prof) profile_end(s, ev, sweep_bytes(MODE, sizeof(T) == 8, C, a.n, a.nnz), (MODE * 1000 + C) * 2 + (sizeof(T) == 8));
   return GEDWALK_OK;
 }
 

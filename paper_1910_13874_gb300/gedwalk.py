@@ -48,6 +48,13 @@ class ProfileStats(ctypes.Structure):
         ("sweep_launches", ctypes.c_int64),
         ("sweep_ms", ctypes.c_double),
         ("sweep_bytes", ctypes.c_double),
+        ("top_mode", ctypes.c_int32),
+        ("top_cols", ctypes.c_int32),
+        ("top_fp64", ctypes.c_int32),
+        ("top_pad", ctypes.c_int32),
+        ("top_launches", ctypes.c_int64),
+        ("top_ms", ctypes.c_double),
+        ("top_bytes", ctypes.c_double),
     ]
 
 
@@ -192,7 +199,9 @@ def profile_read() -> dict:
     st = ProfileStats()
     _check(load().gedwalk_profile_read(ctypes.byref(st)))
     return {"launches": st.launches, "sweep_launches": st.sweep_launches, "sweep_ms": st.sweep_ms,
-            "sweep_bytes": st.sweep_bytes}
+            "sweep_bytes": st.sweep_bytes, "top_mode": st.top_mode, "top_cols": st.top_cols,
+            "top_fp64": st.top_fp64, "top_launches": st.top_launches, "top_ms": st.top_ms,
+            "top_bytes": st.top_bytes}
 
 
 class Graph:
