@@ -432,6 +432,7 @@ gedwalk_status resolve(Graph& g, const gedwalk_params* p, double eps_override, R
   gedwalk_params d;
   gedwalk_params_default(&d);
   if (!p) p = &d;
+  if (p->alpha < 0.0 || std::isnan(p->alpha)) return fail(GEDWALK_ERR_INVALID, "alpha must be positive (0 = default)");
   r->alpha = p->alpha > 0.0 ? p->alpha : g.alpha_default;
   if (!(r->alpha > 0.0) || !std::isfinite(r->alpha)) return fail(GEDWALK_ERR_INVALID, "alpha must be positive");
   if (p->precision != GEDWALK_FP64 && p->precision != GEDWALK_FP32)
@@ -653,6 +654,7 @@ gedwalk_status gedwalk_truncation(gedwalk_graph_t h, double alpha, double epsilo
   if (!h || !L) return fail(GEDWALK_ERR_INVALID, "graph or L is NULL");
   Graph* g = G(h);
   std::lock_guard<std::mutex> lk(g->mu);
+  if (alpha < 0.0 || std::isnan(alpha)) return fail(GEDWALK_ERR_INVALID, "alpha must be positive (0 = default)");
   if (alpha == 0.0) alpha = g->alpha_default;
   double b = 0;
   int32_t l = 0;
