@@ -395,13 +395,14 @@ def run_serve(args, spec, rank, world, local):
     devs = [gedwalk.Graph.from_host(h) for h in hosts]
     srv = gedwalk.Server(devs, mem_budget=8 << 30, max_batch=256)
     rng = np.random.default_rng(42)
-    rates = [1000, 5000, 20000]
+    # the configured mix (90% score, 10% maximise) and score-only traffic, Poisson arrivals
+    plan = [(1000, 0.9), (5000, 0.9), (20000, 0.9), (5000, 1.0), (20000, 1.0), (50000, 1.0)]
     per_rate = max(1.0, min(3.0, args.steps))
     results = []
-    for rate in rates:
+    for rate, score_frac in plan:
         n_req = int(rate * per_rate)
         gaps = rng.exponential(1.0 / rate, size=n_req)
-        kinds = rng.random(n_req) < 0.9
+        kinds = rng.random(n_req) < score_frac
         gis = rng.integers(0, len(hosts), size=n_req)
         tickets = []
         t0 = time.perf_counter()
@@ -420,17 +421,26 @@ def run_serve(args, spec, rank, world, local):
         lat = [srv.poll(t, -1)["latency_us"] for t in tickets]
         wall = time.perf_counter() - t0
         lat = np.array(lat) / 1e3
-        results.append({"offered_req_s": rate, "achieved_req_s": round(n_req / wall, 1),
-                        "p50_ms": round(float(np.percentile(lat, 50)), 3),
-                        "p99_ms": round(float(np.percentile(lat, 99)), 3), "requests": n_req})
+        res = {"offered_req_s": rate, "score_fraction": score_frac, "achieved_req_s": round(n_req / wall, 1),
+               "p50_ms": round(float(np.percentile(lat, 50)), 3),
+               "p99_ms": round(float(np.percentile(lat, 99)), 3), "requests": n_req}
+        for flag, name in ((True, "score"), (False, "maximize")):
+            sel = lat[kinds == flag]
+            if sel.size:
+                res[name] = {"p50_ms": round(float(np.percentile(sel, 50)), 3),
+                             "p99_ms": round(float(np.percentile(sel, 99)), 3), "count": int(sel.size)}
+        results.append(res)
     st = srv.stats()
+    st["mean_batch"] = round(st["batched_requests"] / max(st["batches"], 1), 2)
     srv.close()
-    best = max(results, key=lambda r: r["achieved_req_s"])
+    mixed = [r for r in results if r["score_fraction"] < 1.0]
+    best = max(mixed, key=lambda r: r["achieved_req_s"])
     return {"metric": "serving queries/s with p50/p99 latency", "value": best["achieved_req_s"], "unit": "queries/s",
             "n_gpus": world, "steps": args.steps, "warmup": 0, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded generator)",
             "config": {"workload": spec["name"], "graphs": [f"n={d.n} nnz={d.nnz}" for d in devs],
-                       "mix": "90% score |S|~U{1..200}, 10% maximize k~U{5..50}", "epsilon": spec["eps"]},
+                       "mix": "90% score |S|~U{1..200}, 10% maximize k~U{5..50}; plus score-only rates",
+                       "epsilon": spec["eps"], "value_is": "best achieved rate of the configured mix"},
             "rates": results, "server": st,
             "e2e": {"value": best["achieved_req_s"], "unit": "queries/s", "h2d_bytes_per_step": None,
                     "d2h_bytes_per_step": None, "note": "requests submitted from host memory through the C ABI"}}

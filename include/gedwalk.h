@@ -216,8 +216,10 @@ GEDWALK_API gedwalk_status gedwalk_maximize_stats(gedwalk_graph_t g, int64_t* ev
  * columns of one batched SpMM; maximise requests run on their own streams and
  * overlap with the scoring. Admission is by memory: a request is admitted
  * when its device working set fits in mem_budget beside the requests in
- * flight, otherwise it waits in the queue. Results do not depend on which
- * other requests shared a batch.
+ * flight, otherwise it waits in its queue. Score requests are admitted before
+ * maximise requests, and a maximise request only when one of the server's 8
+ * maximise workers is free. Results do not depend on which other requests
+ * shared a batch.
  * ------------------------------------------------------------------------- */
 enum { GEDWALK_REQ_SCORE = 0, GEDWALK_REQ_MAXIMIZE = 1 };
 

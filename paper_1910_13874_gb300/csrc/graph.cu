@@ -399,6 +399,12 @@ gedwalk_status truncation_length(Graph& g, double alpha, double eps, int32_t* L,
     return fail(GEDWALK_ERR_NOT_CONVERGENT,
                 "alpha * d_max = %g >= 1: the combinatorial bound needs alpha < 1/d_max (force L instead)",
                 alpha * g.dmax);
+  for (const Graph::Trunc& t : g.trunc_cache)  // L depends only on (graph, alpha, epsilon)
+    if (t.alpha == alpha && t.eps == eps) {
+      *L = t.L;
+      if (bound) *bound = t.bound;
+      return GEDWALK_OK;
+    }
   const double coef = alpha * g.dmax / (1.0 - alpha * g.dmax);
   const int32_t kCap = 4096;
   int32_t rows = std::max(g.tt_alpha == alpha ? g.tt_rows : 0, 4);
@@ -421,6 +427,8 @@ gedwalk_status truncation_length(Graph& g, double alpha, double eps, int32_t* L,
     if (hl > 0) {
       *L = hl;
       if (bound) *bound = hb;
+      if (g.trunc_cache.size() >= 64) g.trunc_cache.erase(g.trunc_cache.begin());
+      g.trunc_cache.push_back({alpha, eps, hl, hb});
       return GEDWALK_OK;
     }
     if (rows >= kCap) return fail(GEDWALK_ERR_INVALID, "no truncation length <= %d reaches epsilon %g", kCap, eps);

@@ -138,6 +138,13 @@ struct Graph {
   std::vector<double> Wa;
   // readers of ttab hold it shared; growing or replacing the table holds it exclusively
   std::shared_mutex tt_lock;
+  // truncation lengths already found: {alpha, epsilon, L, B_L}
+  struct Trunc {
+    double alpha, eps;
+    int32_t L;
+    double bound;
+  };
+  std::vector<Trunc> trunc_cache;
 
   // batched-scoring autotuner result: column-block width per graph (0 = not tuned)
   int32_t batch_cols = 0;

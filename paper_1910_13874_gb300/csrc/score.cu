@@ -176,14 +176,15 @@ gedwalk_status score_batch_impl(Graph& g, Workspace& ws, const int32_t* offsets,
   int32_t* mrow = reinterpret_cast<int32_t*>(acc + total);
   int32_t* mcol = mrow + total;
   int32_t* goff = mcol + total;
-  std::vector<int32_t> hcol(total);
+  // members, their columns and the group offsets go up in one copy from pinned staging
+  const size_t up = sizeof(int32_t) * (2 * static_cast<size_t>(total) + G + 1);
+  GW_TRY(ws.ensure_pinned(std::max(up, sizeof(double) * static_cast<size_t>(G)) + 64));
+  int32_t* hst = static_cast<int32_t*>(ws.pinned);
+  if (total > 0) memcpy(hst, members_int, sizeof(int32_t) * total);
   for (int32_t j = 0; j < G; ++j)
-    for (int32_t i = offsets[j]; i < offsets[j + 1]; ++i) hcol[i] = j % C;
-  if (total > 0) {
-    GW_CUDA(cudaMemcpyAsync(mrow, members_int, sizeof(int32_t) * total, cudaMemcpyHostToDevice, s));
-    GW_CUDA(cudaMemcpyAsync(mcol, hcol.data(), sizeof(int32_t) * total, cudaMemcpyHostToDevice, s));
-  }
-  GW_CUDA(cudaMemcpyAsync(goff, offsets, sizeof(int32_t) * (G + 1), cudaMemcpyHostToDevice, s));
+    for (int32_t i = offsets[j]; i < offsets[j + 1]; ++i) hst[total + i] = j % C;
+  memcpy(hst + 2 * total, offsets, sizeof(int32_t) * (G + 1));
+  GW_CUDA(cudaMemcpyAsync(mrow, hst, up, cudaMemcpyHostToDevice, s));
   const size_t vbytes = static_cast<size_t>(g.n) * C * 4;
   GW_TRY(ws.x0.ensure(vbytes, s));
   GW_TRY(ws.x1.ensure(vbytes, s));
@@ -226,8 +227,9 @@ gedwalk_status score_batch_impl(Graph& g, Workspace& ws, const int32_t* offsets,
   }
   batch_group_sum<<<blocks_for(G), 256, 0, s>>>(acc, goff, G, ws.small.as<double>());
   GW_KCHECK();
-  GW_CUDA(cudaMemcpyAsync(scores, ws.small.p, sizeof(double) * G, cudaMemcpyDeviceToHost, s));
+  GW_CUDA(cudaMemcpyAsync(ws.pinned, ws.small.p, sizeof(double) * G, cudaMemcpyDeviceToHost, s));
   GW_CUDA(cudaStreamSynchronize(s));
+  memcpy(scores, ws.pinned, sizeof(double) * G);
   return GEDWALK_OK;
 }
 

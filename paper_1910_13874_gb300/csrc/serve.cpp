@@ -1,7 +1,10 @@
 // Serving: a continuous-batching request loop over device-resident graphs.
 //
-// Requests enter a FIFO queue and are admitted while their estimated device
-// working set fits in the memory budget beside the requests in flight.
+// Requests enter per-kind FIFO queues and are admitted while their estimated
+// device working set fits in the memory budget beside the requests in flight.
+// Score requests (cheap, batched) are admitted first; a maximise request is
+// admitted only when a worker is free to run it, so queued maximisations never
+// hold memory that waiting score requests could use.
 // Admitted score requests wait in their graph's lane; whenever the lane is
 // free it takes every waiting request with the same (alpha, L) (up to
 // max_batch) and scores them as the columns of one batched SpMM on the lane's
@@ -24,7 +27,7 @@ namespace gw {
 namespace {
 
 using Clock = std::chrono::steady_clock;
-constexpr int kMaxWorkers = 4;
+constexpr int kMaxWorkers = 8;
 constexpr size_t kMaxQueue = size_t(1) << 20;
 
 struct Request {
@@ -70,8 +73,10 @@ struct Server {
   std::mutex mu;
   std::condition_variable cv_work;  // lanes / workers wait here
   std::condition_variable cv_done;  // pollers wait here
-  std::deque<ReqPtr> pending;       // not yet admitted
+  std::deque<ReqPtr> pending;       // score requests not yet admitted
+  std::deque<ReqPtr> pending_max;   // maximise requests not yet admitted
   std::deque<ReqPtr> max_queue;     // admitted maximize requests
+  int32_t max_running = 0;          // admitted maximise requests (queued or running)
   std::unordered_map<uint64_t, ReqPtr> table;
   std::vector<std::unique_ptr<Lane>> lanes;
   std::vector<std::unique_ptr<Worker>> workers;
@@ -89,19 +94,28 @@ struct Server {
   }
 
   void admit_locked() {
-    while (!pending.empty()) {
+    while (!pending.empty()) {  // score requests first (FIFO)
       ReqPtr q = pending.front();
-      if (in_flight > 0 && in_flight + q->mem > budget) break;  // FIFO: wait for memory to free up
+      if (in_flight > 0 && in_flight + q->mem > budget) break;
       pending.pop_front();
       in_flight += q->mem;
       peak = std::max(peak, in_flight);
-      if (q->kind == GEDWALK_REQ_SCORE) lanes[q->graph]->queue.push_back(q);
-      else max_queue.push_back(q);
+      lanes[q->graph]->queue.push_back(q);
+    }
+    while (!pending_max.empty() && max_running < kMaxWorkers) {  // then maximise requests, one per free worker
+      ReqPtr q = pending_max.front();
+      if (in_flight > 0 && in_flight + q->mem > budget) break;
+      pending_max.pop_front();
+      in_flight += q->mem;
+      peak = std::max(peak, in_flight);
+      ++max_running;
+      max_queue.push_back(q);
     }
     cv_work.notify_all();
   }
 
   void finish_locked(const ReqPtr& q) {
+    if (q->kind == GEDWALK_REQ_MAXIMIZE) --max_running;
     q->done = true;
     q->t_done = Clock::now();
     in_flight -= q->mem;
@@ -267,12 +281,13 @@ gedwalk_status gedwalk_serve_submit(gedwalk_server_t h, int32_t graph, int32_t k
   }
   std::lock_guard<std::mutex> lk(srv->mu);
   if (srv->stop) return fail(GEDWALK_ERR_BUSY, "server is stopping");
-  if (srv->pending.size() >= kMaxQueue) return fail(GEDWALK_ERR_BUSY, "request queue is full");
+  if (srv->pending.size() + srv->pending_max.size() >= kMaxQueue)
+    return fail(GEDWALK_ERR_BUSY, "request queue is full");
   q->mem = srv->estimate(*q);
   q->ticket = srv->next_ticket++;
   q->t_submit = Clock::now();
   srv->table[q->ticket] = q;
-  srv->pending.push_back(q);
+  (kind == GEDWALK_REQ_SCORE ? srv->pending : srv->pending_max).push_back(q);
   srv->admit_locked();
   *ticket = q->ticket;
   return GEDWALK_OK;
@@ -332,6 +347,7 @@ gedwalk_status gedwalk_serve_destroy(gedwalk_server_t h) {
     std::lock_guard<std::mutex> lk(srv->mu);
     srv->stop = true;
     srv->pending.clear();
+    srv->pending_max.clear();
     srv->cv_work.notify_all();
   }
   for (auto& l : srv->lanes)
