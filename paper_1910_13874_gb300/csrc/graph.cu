@@ -46,6 +46,11 @@ struct Profiler {
     int key;  // (mode * 1000 + cols) * 2 + fp64
   };
   std::vector<Rec> recs;
+  struct Done {
+    double ms, bytes;
+    int key;
+  };
+  std::vector<Done> done;  // timings read directly (graph replays)
   std::vector<cudaEvent_t> pool;
   cudaEvent_t take() {
     if (!pool.empty()) {
@@ -68,6 +73,13 @@ Profiler& prof() {
 }  // namespace
 
 void count_launch() { prof().launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(int n) { prof().launches.fetch_add(n, std::memory_order_relaxed); }
+
+void profile_add(double ms, double bytes, int key) {
+  Profiler& p = prof();
+  std::lock_guard<std::mutex> lk(p.mu);
+  if (p.enabled.load()) p.done.push_back({ms, bytes, key});
+}
 bool profiling() { return prof().enabled.load(std::memory_order_relaxed); }
 
 void profile_begin(cudaStream_t s, cudaEvent_t* a) {
@@ -134,7 +146,20 @@ gedwalk_status DevBuf::ensure(size_t need, cudaStream_t s, bool zero) {
   return GEDWALK_OK;
 }
 
+void SweepGraph::reset() {
+  if (exec) cudaGraphExecDestroy(exec);
+  exec = nullptr;
+  for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  ev.clear();
+  key = 0;
+  uses = 0;
+  timing_pending = false;
+}
+
 Workspace::~Workspace() {
+  for (SweepGraph& sg : graphs) sg.reset();
+  if (order_ev) cudaEventDestroy(order_ev);
+  if (own_stream) cudaStreamDestroy(own_stream);
   if (pinned) cudaFreeHost(pinned);
 }
 
@@ -257,7 +282,11 @@ static gedwalk_status build_plan(Graph& g, const std::vector<int32_t>& rp) {
   int32_t r = nh;
   while (r < g.n_active) {
     const int cls = row_class(g.deg[r]);
-    const int32_t max_rows = cls == 6 ? 32 : kUnitRowsMax;
+    // a short-row unit takes up to kUnitRowsMax rows; on small graphs fewer, down to one
+    // iteration of its warp (2 rows per lane group), so that every SM gets work
+    const int32_t iter_rows = cls == 6 ? 1 : 2 * (32 >> cls);
+    const int32_t small_cap = std::max<int32_t>(iter_rows, g.n_active / kTargetUnits);
+    const int32_t max_rows = std::min<int32_t>(cls == 6 ? 32 : kUnitRowsMax, small_cap);
     const int64_t max_edges = cls == 6 ? kLongUnitEdges : kUnitEdges;
     int32_t r1 = r;
     int64_t edges = 0;
@@ -515,6 +544,7 @@ gedwalk_status gedwalk_profile(int32_t enable) {
     p.pool.push_back(r.b);
   }
   p.recs.clear();
+  p.done.clear();
   p.launches.store(0);
   p.enabled.store(enable != 0);
   return GEDWALK_OK;
@@ -530,24 +560,28 @@ gedwalk_status gedwalk_profile_read(gedwalk_profile_stats* out) {
     double ms = 0.0, bytes = 0.0;
   };
   std::vector<std::pair<int, Agg>> per;
-  for (auto& r : p.recs) {
-    GW_CUDA(cudaEventSynchronize(r.b));
-    float t = 0.0f;
-    GW_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
+  auto add = [&](double t, double b, int key) {
     ms += t;
-    bytes += r.bytes;
-    auto it = std::find_if(per.begin(), per.end(), [&](const std::pair<int, Agg>& e) { return e.first == r.key; });
+    bytes += b;
+    auto it = std::find_if(per.begin(), per.end(), [&](const std::pair<int, Agg>& e) { return e.first == key; });
     if (it == per.end()) {
-      per.push_back({r.key, Agg()});
+      per.push_back({key, Agg()});
       it = per.end() - 1;
     }
     it->second.n++;
     it->second.ms += t;
-    it->second.bytes += r.bytes;
+    it->second.bytes += b;
+  };
+  for (auto& r : p.recs) {
+    GW_CUDA(cudaEventSynchronize(r.b));
+    float t = 0.0f;
+    GW_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
+    add(t, r.bytes, r.key);
   }
+  for (auto& d : p.done) add(d.ms, d.bytes, d.key);
   *out = gedwalk_profile_stats{};
   out->launches = p.launches.load();
-  out->sweep_launches = static_cast<int64_t>(p.recs.size());
+  out->sweep_launches = static_cast<int64_t>(p.recs.size() + p.done.size());
   out->sweep_ms = ms;
   out->sweep_bytes = bytes;
   const std::pair<int, Agg>* top = nullptr;

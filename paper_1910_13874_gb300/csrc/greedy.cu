@@ -31,7 +31,7 @@ namespace gw {
 namespace {
 
 constexpr int kTopK = 16;
-constexpr int kSelBlocks = 152 * 3;
+constexpr int kSelBlocks = 152 * 8;
 
 struct Stale {
   float ub;      // last exact gain rounded up (an upper bound for every later step)
@@ -65,10 +65,11 @@ __device__ __forceinline__ void topk_push(float (&v)[kTopK], int (&id)[kTopK], f
   }
 }
 
-// Block-wide top-K of the threads' sorted lists; thread 0 writes out[0..K).
+// Block-wide top-K of the threads' sorted lists (NT threads); thread 0 writes out[0..K).
+template <int NT>
 __device__ void block_topk(float (&v)[kTopK], int (&id)[kTopK], float* out_v, int* out_id) {
-  __shared__ float sv[kThreads / 32];
-  __shared__ int sid[kThreads / 32];
+  __shared__ float sv[NT / 32];
+  __shared__ int sid[NT / 32];
   __shared__ float bv_s;
   __shared__ int bi_s;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -92,7 +93,7 @@ __device__ void block_topk(float (&v)[kTopK], int (&id)[kTopK], float* out_v, in
     if (threadIdx.x == 0) {
       float b = sv[0];
       int i0 = sid[0];
-      for (int w = 1; w < kThreads / 32; ++w)
+      for (int w = 1; w < NT / 32; ++w)
         if (better(sv[w], sid[w], b, i0)) {
           b = sv[w];
           i0 = sid[w];
@@ -197,21 +198,37 @@ __global__ void __launch_bounds__(kThreads) ub_select(const T* __restrict__ mtab
     v[i] = -1.0f;
     id[i] = INT_MAX;
   }
-  for (int32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
-    if ((__ldg(mask + (x >> 5)) >> (x & 31)) & 1u) continue;
-    const Stale st = stale[x];
-    if (st.step == step) continue;  // evaluated with the current S: its exact gain is known
-    float b = LF > 0 ? ub_fixed<T, (LF > 0 ? LF : 1)>(mtab + x, n) : ub_any<T>(mtab + x, n, L);
-    if (st.step >= 0 && st.ub < b) b = st.ub;
-    if (b == 0.0f) {
-      atomicMin(zero_min, __ldg(perm + x));
-      continue;
+  // four vertices per iteration, all of their loads issued before any decision
+  const int32_t stride = gridDim.x * blockDim.x;
+  for (int32_t base = blockIdx.x * blockDim.x + threadIdx.x; base < n; base += 4 * stride) {
+    float b[4];
+    bool live[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int32_t xr = base + k * stride;
+      const int32_t x = xr < n ? xr : n - 1;
+      const bool inS = (__ldg(mask + (x >> 5)) >> (x & 31)) & 1u;
+      const Stale st = stale[x];
+      float ub = LF > 0 ? ub_fixed<T, (LF > 0 ? LF : 1)>(mtab + x, n) : ub_any<T>(mtab + x, n, L);
+      if (st.step >= 0 && st.ub < ub) ub = st.ub;
+      b[k] = ub;
+      // evaluated with the current S: its exact gain is known
+      live[k] = xr < n && !inS && st.step != step;
     }
-    topk_push(v, id, b, x);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (!live[k]) continue;
+      const int32_t x = base + k * stride;
+      if (b[k] == 0.0f) {
+        atomicMin(zero_min, __ldg(perm + x));
+        continue;
+      }
+      topk_push(v, id, b[k], x);
+    }
   }
   __shared__ float ov[kTopK];
   __shared__ int oi[kTopK];
-  block_topk(v, id, ov, oi);
+  block_topk<kThreads>(v, id, ov, oi);
   if (threadIdx.x < kTopK) {
     sel_v[blockIdx.x * kTopK + threadIdx.x] = ov[threadIdx.x];
     sel_id[blockIdx.x * kTopK + threadIdx.x] = oi[threadIdx.x];
@@ -233,9 +250,11 @@ cudaError_t launch_ub_select(int nb, cudaStream_t s, const T* mtab, int32_t L, i
   return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(kThreads) select_merge(const float* __restrict__ sel_v,
-                                                        const int* __restrict__ sel_id, int count,
-                                                        SelOut* __restrict__ out) {
+constexpr int kMergeThreads = 1024;
+
+__global__ void __launch_bounds__(kMergeThreads) select_merge(const float* __restrict__ sel_v,
+                                                             const int* __restrict__ sel_id, int count,
+                                                             SelOut* __restrict__ out) {
   float v[kTopK];
   int id[kTopK];
 #pragma unroll
@@ -243,11 +262,11 @@ __global__ void __launch_bounds__(kThreads) select_merge(const float* __restrict
     v[i] = -1.0f;
     id[i] = INT_MAX;
   }
-  for (int i = threadIdx.x; i < count; i += kThreads)
+  for (int i = threadIdx.x; i < count; i += kMergeThreads)
     if (sel_id[i] != INT_MAX) topk_push(v, id, sel_v[i], sel_id[i]);
   __shared__ float ov[kTopK];
   __shared__ int oi[kTopK];
-  block_topk(v, id, ov, oi);
+  block_topk<kMergeThreads>(v, id, ov, oi);
   if (threadIdx.x < kTopK) {
     out->val[threadIdx.x] = ov[threadIdx.x];
     out->id[threadIdx.x] = oi[threadIdx.x];
@@ -289,18 +308,12 @@ struct GreedyCtx {
   int64_t sweeps = 0;
 };
 
-// Runs L sweeps. mode MODE_FUSED (column 0 = phi^miss, table rows written) or MODE_CAND.
-gedwalk_status run_sweeps(GreedyCtx& c, int mode, int cols, const std::vector<int32_t>& cand) {
+// Issues init + L sweeps + column-sum reduction on c.s. ev (optional): two external events
+// around each sweep (graph capture).
+gedwalk_status issue_sweeps(GreedyCtx& c, int mode, int cols, bool profile, const std::vector<cudaEvent_t>* ev) {
   Graph& g = c.g;
   Workspace& ws = c.ws;
   const bool fp64 = c.r.fp64;
-  int32_t hc[16];
-  for (int j = 0; j < 16; ++j) hc[j] = j < static_cast<int>(cand.size()) ? cand[j] : -1;
-  GW_CUDA(cudaMemcpyAsync(c.d_cand, hc, sizeof hc, cudaMemcpyHostToDevice, c.s));
-  const size_t vbytes = static_cast<size_t>(g.n) * cols * c.es;
-  GW_TRY(ws.x0.ensure(vbytes, c.s));
-  GW_TRY(ws.x1.ensure(vbytes, c.s));
-  GW_TRY(ensure_sweep_scratch(g, ws, cols, fp64, c.s));
   const int first = mode == MODE_FUSED ? 1 : 0;
   void* m0 = mode == MODE_FUSED ? ws.mtab.p : nullptr;
   if (fp64)
@@ -322,8 +335,11 @@ gedwalk_status run_sweeps(GreedyCtx& c, int mode, int cols, const std::vector<in
     char* row = ws.mtab.as<char>() + static_cast<size_t>(t) * g.n * c.es;
     if (mode == MODE_FUSED) a.Mout = row;
     else a.Min = row;
-    GW_TRY(launch_sweep(mode, fp64, cols, a, c.s));
-    ++c.sweeps;
+    // external events bracket the whole run of sweeps (event nodes between kernel nodes cost
+    // a few microseconds each)
+    if (ev && t == 1) GW_CUDA(cudaEventRecordWithFlags((*ev)[0], c.s, cudaEventRecordExternal));
+    GW_TRY(launch_sweep(mode, fp64, cols, a, c.s, profile));
+    if (ev && t == c.L) GW_CUDA(cudaEventRecordWithFlags((*ev)[1], c.s, cudaEventRecordExternal));
     std::swap(cur, nxt);
   }
   const int nsum = sweep_sums(mode, cols);
@@ -331,10 +347,112 @@ gedwalk_status run_sweeps(GreedyCtx& c, int mode, int cols, const std::vector<in
   return GEDWALK_OK;
 }
 
+uint64_t mix_key(uint64_t h, uint64_t v) {
+  h ^= v + 0x9e3779b97f4a7c15ULL + (h << 6) + (h >> 2);
+  return h;
+}
+
+// Runs L sweeps. mode MODE_FUSED (column 0 = phi^miss, table rows written) or MODE_CAND. On a
+// capturable stream the sequence is captured once per configuration (on its second use) and
+// replayed as a CUDA graph.
+gedwalk_status run_sweeps(GreedyCtx& c, int mode, int cols, const std::vector<int32_t>& cand) {
+  Graph& g = c.g;
+  Workspace& ws = c.ws;
+  const bool fp64 = c.r.fp64;
+  int32_t hc[16];
+  for (int j = 0; j < 16; ++j) hc[j] = j < static_cast<int>(cand.size()) ? cand[j] : -1;
+  GW_CUDA(cudaMemcpyAsync(c.d_cand, hc, sizeof hc, cudaMemcpyHostToDevice, c.s));
+  const size_t vbytes = static_cast<size_t>(g.n) * cols * c.es;
+  GW_TRY(ws.x0.ensure(vbytes, c.s));
+  GW_TRY(ws.x1.ensure(vbytes, c.s));
+  GW_TRY(ensure_sweep_scratch(g, ws, cols, fp64, c.s));
+  c.sweeps += c.L;
+  if (c.s == nullptr || g.plan.num_units == 0) return issue_sweeps(c, mode, cols, true, nullptr);
+  SweepGraph& sg = ws.graphs[mode == MODE_FUSED ? 0 : 1];
+  uint64_t key = 0;
+  for (uint64_t v : {uint64_t(mode), uint64_t(cols), uint64_t(fp64), uint64_t(c.L), uint64_t(g.n),
+                     reinterpret_cast<uint64_t>(&g), reinterpret_cast<uint64_t>(c.s),
+                     reinterpret_cast<uint64_t>(ws.x0.p), reinterpret_cast<uint64_t>(ws.x1.p),
+                     reinterpret_cast<uint64_t>(ws.mtab.p), reinterpret_cast<uint64_t>(ws.slots.p),
+                     reinterpret_cast<uint64_t>(ws.parts.p), reinterpret_cast<uint64_t>(ws.partial.p),
+                     reinterpret_cast<uint64_t>(ws.counters.p), reinterpret_cast<uint64_t>(ws.mask.p),
+                     reinterpret_cast<uint64_t>(c.d_cand), reinterpret_cast<uint64_t>(c.d_gains)}) {
+    key = mix_key(key, v);
+  }
+  uint64_t abits;
+  memcpy(&abits, &c.r.alpha, 8);
+  key = mix_key(key, abits);
+  if (sg.key != key) {
+    sg.reset();
+    sg.key = key;
+  }
+  if (!sg.exec) {
+    if (sg.uses++ < 1) return issue_sweeps(c, mode, cols, true, nullptr);  // set-up happens outside capture
+    sg.ev.assign(2, nullptr);
+    for (cudaEvent_t& e : sg.ev) GW_CUDA(cudaEventCreate(&e));
+    GW_CUDA(cudaStreamBeginCapture(c.s, cudaStreamCaptureModeThreadLocal));
+    const gedwalk_status st = issue_sweeps(c, mode, cols, false, &sg.ev);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(c.s, &graph);
+    if (st != GEDWALK_OK || ce != cudaSuccess || !graph) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      sg.reset();
+      return st != GEDWALK_OK ? st : fail(GEDWALK_ERR_DEVICE, "stream capture failed: %s", cudaGetErrorString(ce));
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&sg.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+      sg.exec = nullptr;
+      sg.reset();
+      return fail(GEDWALK_ERR_DEVICE, "graph instantiation failed: %s", cudaGetErrorString(ie));
+    }
+    sg.kernels = 1 + c.L + (sweep_sums(mode, cols) > 0 ? 2 : 0);
+    sg.sweeps = c.L;
+    sg.bytes = sweep_bytes(mode, fp64, cols, g.n, g.nnz);
+    sg.prof_key = (mode * 1000 + cols) * 2 + (fp64 ? 1 : 0);
+  }
+  GW_CUDA(cudaGraphLaunch(sg.exec, c.s));
+  count_launches(sg.kernels);
+  sg.timing_pending = profiling();
+  return GEDWALK_OK;
+}
+
+// After a synchronisation: hands the sweep timings of graph replays to the profiler.
+void read_graph_timing(Workspace& ws) {
+  for (SweepGraph& sg : ws.graphs) {
+    if (!sg.timing_pending) continue;
+    sg.timing_pending = false;
+    float ms = 0.0f;  // the run of sweeps, shared evenly among them
+    if (sg.ev.size() == 2 && cudaEventElapsedTime(&ms, sg.ev[0], sg.ev[1]) == cudaSuccess) {
+      for (int t = 0; t < sg.sweeps; ++t) profile_add(ms / sg.sweeps, sg.bytes, sg.prof_key);
+    } else {
+      cudaGetLastError();
+    }
+  }
+}
+
+// The stream a greedy run uses: the caller's, or (for the legacy default stream, which cannot
+// be captured) the workspace's own stream, ordered after the caller's.
+gedwalk_status greedy_stream(Workspace& ws, cudaStream_t caller, cudaStream_t* out) {
+  if (caller != nullptr) {
+    *out = caller;
+    return GEDWALK_OK;
+  }
+  if (!ws.own_stream) GW_CUDA(cudaStreamCreateWithFlags(&ws.own_stream, cudaStreamNonBlocking));
+  if (!ws.order_ev) GW_CUDA(cudaEventCreateWithFlags(&ws.order_ev, cudaEventDisableTiming));
+  GW_CUDA(cudaEventRecord(ws.order_ev, caller));
+  GW_CUDA(cudaStreamWaitEvent(ws.own_stream, ws.order_ev, 0));
+  *out = ws.own_stream;
+  return GEDWALK_OK;
+}
+
 }  // namespace
 
-gedwalk_status maximize_impl(Graph& g, Workspace& ws, int32_t k, const Resolved& r, int32_t flags,
+gedwalk_status maximize_impl(Graph& g, Workspace& ws, int32_t k, const Resolved& r_in, int32_t flags,
                              const std::vector<int32_t>& init_int, int32_t* group, double* gains, double* score) {
+  Resolved r = r_in;
+  GW_TRY(greedy_stream(ws, r_in.stream, &r.stream));
   cudaStream_t s = r.stream;
   const size_t es = r.fp64 ? 8 : 4;
   // phi^miss + speculative candidates. Every gather costs one L2 sector whatever the row
@@ -393,6 +511,7 @@ gedwalk_status maximize_impl(Graph& g, Workspace& ws, int32_t k, const Resolved&
           double hg[16];
           GW_CUDA(cudaMemcpyAsync(hg, c.d_gains, sizeof(double) * cols_all, cudaMemcpyDeviceToHost, s));
           GW_CUDA(cudaStreamSynchronize(s));
+          read_graph_timing(ws);
           for (size_t j = 0; j < batch.size(); ++j) {
             Cand e{hg[j], batch[j], g.perm[batch[j]]};
             if (best.v < 0 || cand_before(e, best)) best = e;
@@ -418,7 +537,7 @@ gedwalk_status maximize_impl(Graph& g, Workspace& ws, int32_t k, const Resolved&
         }
         // 2. bound + selection pass
         set_int<<<1, 1, 0, s>>>(&c.d_out->zero_min_caller, INT_MAX);
-        const int nb = std::max(1, std::min(kSelBlocks, blocks_for(g.n)));
+        const int nb = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(kSelBlocks, (int64_t(g.n) + 1023) / 1024)));
         if (r.fp64)
           GW_CUDA(launch_ub_select<double>(nb, s, ws.mtab.as<double>(), L, g.n, ws.mask.as<uint32_t>(), stale, step,
                                            g.perm_d.as<int32_t>(), sel_v, sel_id, &c.d_out->zero_min_caller));
@@ -426,10 +545,11 @@ gedwalk_status maximize_impl(Graph& g, Workspace& ws, int32_t k, const Resolved&
           GW_CUDA(launch_ub_select<float>(nb, s, ws.mtab.as<float>(), L, g.n, ws.mask.as<uint32_t>(), stale, step,
                                           g.perm_d.as<int32_t>(), sel_v, sel_id, &c.d_out->zero_min_caller));
         count_launch();
-        select_merge<<<1, kThreads, 0, s>>>(sel_v, sel_id, nb * kTopK, c.d_out);
+        select_merge<<<1, kMergeThreads, 0, s>>>(sel_v, sel_id, nb * kTopK, c.d_out);
         GW_KCHECK();
         GW_CUDA(cudaMemcpyAsync(c.h_out, c.d_out, sizeof(SelOut), cudaMemcpyDeviceToHost, s));
         GW_CUDA(cudaStreamSynchronize(s));
+        read_graph_timing(ws);
         for (size_t j = 0; j < last.size(); ++j) {
           Cand e{c.h_out->gains[j], last[j], g.perm[last[j]]};
           E.push_back(e);
@@ -487,8 +607,10 @@ gedwalk_status maximize_impl(Graph& g, Workspace& ws, int32_t k, const Resolved&
   return GEDWALK_OK;
 }
 
-gedwalk_status gains_impl(Graph& g, Workspace& ws, const std::vector<int32_t>& S_int, const Resolved& r,
+gedwalk_status gains_impl(Graph& g, Workspace& ws, const std::vector<int32_t>& S_int, const Resolved& r_in,
                           double* gains_caller) {
+  Resolved r = r_in;
+  GW_TRY(greedy_stream(ws, r_in.stream, &r.stream));
   cudaStream_t s = r.stream;
   const size_t es = r.fp64 ? 8 : 4;
   const int cols_all = r.fp64 ? 8 : 16;
@@ -512,6 +634,7 @@ gedwalk_status gains_impl(Graph& g, Workspace& ws, const std::vector<int32_t>& S
       double hg[16];
       GW_CUDA(cudaMemcpyAsync(hg, c.d_gains, sizeof(double) * cols_all, cudaMemcpyDeviceToHost, s));
       GW_CUDA(cudaStreamSynchronize(s));
+      read_graph_timing(ws);
       for (size_t j = 0; j < batch.size(); ++j) gains_caller[g.perm[batch[j]]] = hg[j];
       batch.clear();
     }

@@ -80,6 +80,7 @@ constexpr int kSliceEdges = 1024;
 constexpr int kUnitEdges = 1024;      // entries per short-row unit (at least one row)
 constexpr int kLongUnitEdges = 2048;  // entries per long-row unit (at least one row)
 constexpr int kUnitRowsMax = 128;     // rows per unit (short classes); long units take <= 32
+constexpr int kTargetUnits = 4096;    // small graphs get units of fewer rows, aiming at this many
 constexpr int kReduceParts = 64;      // first-stage parts of the deterministic slot reduction
 constexpr int64_t kL1HubBytes = 160 * 1024;  // x rows per SM kept in L1 with high priority
 
@@ -90,6 +91,27 @@ struct Plan {
   int32_t num_slots = 0;   // num_units + num_heavy column-sum slots
   DevBuf units;            // int4[num_units]
   DevBuf heavy;            // int4[num_heavy]: {row, first slice, slice count, 0}
+};
+
+// ---------------------------------------------------------------- captured sweep sequences
+// A greedy sweep sequence (initialisation, L sweeps, column-sum reduction) captured as a CUDA
+// graph and replayed while its configuration is unchanged. Two external event nodes bracket the
+// run of sweeps, so the profiler still sees their device time.
+struct SweepGraph {
+  cudaGraphExec_t exec = nullptr;
+  std::vector<cudaEvent_t> ev;  // start and end of the run of sweeps
+  uint64_t key = 0;             // configuration of the captured sequence
+  int uses = 0;                 // direct runs of this configuration before it is captured
+  int kernels = 0;              // kernel nodes per replay
+  int sweeps = 0;               // sweep kernels per replay
+  double bytes = 0.0;           // algorithmic bytes per sweep
+  int prof_key = 0;
+  bool timing_pending = false;  // replayed while profiling; events not read yet
+  void reset();
+  SweepGraph() = default;
+  SweepGraph(const SweepGraph&) = delete;
+  SweepGraph& operator=(const SweepGraph&) = delete;
+  ~SweepGraph() { reset(); }
 };
 
 // ---------------------------------------------------------------- workspaces
@@ -109,6 +131,9 @@ struct Workspace {
   DevBuf members;    // batched scoring: member ids / group ids / accumulators
   DevBuf pinned_dummy;
   int64_t st_evals = 0, st_batches = 0, st_sweeps = 0, st_spec_miss = 0;  // last maximize
+  SweepGraph graphs[2];             // captured greedy sequences: fused, candidate batch
+  cudaStream_t own_stream = nullptr;  // capturable stream used when the caller passes stream 0
+  cudaEvent_t order_ev = nullptr;     // orders own_stream after the caller's stream
   std::vector<uint8_t> host_small;  // staging
   void* pinned = nullptr;           // pinned host staging buffer
   size_t pinned_bytes = 0;
@@ -192,12 +217,16 @@ struct SweepArgs {
 bool profiling();
 void profile_begin(cudaStream_t s, cudaEvent_t* a);
 void profile_end(cudaStream_t s, cudaEvent_t a, double bytes, int key);
+// Adds one timed sweep launch measured outside the event list (graph replays).
+void profile_add(double ms, double bytes, int key);
+// Counts n kernel launches (graph replays).
+void count_launches(int n);
 // Algorithmic bytes of one sweep launch: CSR once, x read once, y written once, plus the mask
 // and the phi^miss row where the mode reads or writes them.
 double sweep_bytes(int mode, bool fp64, int cols, int32_t n, int64_t nnz);
 
 // Launches one sweep (instantiated for the supported (type, columns, mode) triples).
-gedwalk_status launch_sweep(int mode, bool fp64, int cols, const SweepArgs& a, cudaStream_t s);
+gedwalk_status launch_sweep(int mode, bool fp64, int cols, const SweepArgs& a, cudaStream_t s, bool profile = true);
 // Column-sum count of a mode at width cols.
 int sweep_sums(int mode, int cols);
 // out[c] = sum over slots of slots[slot][c], c < nsum, in a fixed order (parts: nsum*kReduceParts).

@@ -532,10 +532,10 @@ __global__ void reduce_slots_final(const double* __restrict__ parts, int32_t nsu
 }
 
 template <typename T, int C, int MODE>
-gedwalk_status run(const SweepArgs& a, cudaStream_t s) {
+gedwalk_status run(const SweepArgs& a, cudaStream_t s, bool profile) {
   if (a.num_units == 0) return GEDWALK_OK;
   cudaEvent_t ev = nullptr;
-  const bool prof = profiling();
+  const bool prof = profile && profiling();
   if (prof) profile_begin(s, &ev);
   static bool configured = false;  // small shared-memory carveout: the rest of the unified
   if (!configured) {               // L1/shared array caches the gathered rows of x
@@ -568,9 +568,9 @@ int sweep_sums(int mode, int cols) {
   }
 }
 
-gedwalk_status launch_sweep(int mode, bool fp64, int cols, const SweepArgs& a, cudaStream_t s) {
+gedwalk_status launch_sweep(int mode, bool fp64, int cols, const SweepArgs& a, cudaStream_t s, bool profile) {
 #define GW_CASE(M, T, C) \
-  if (mode == M && fp64 == (sizeof(T) == 8) && cols == C) return run<T, C, M>(a, s);
+  if (mode == M && fp64 == (sizeof(T) == 8) && cols == C) return run<T, C, M>(a, s, profile);
   GW_CASE(MODE_TOTALS, double, 1)
   GW_CASE(MODE_SCORE, double, 2)
   GW_CASE(MODE_SCORE, float, 2)
