@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rmat", choices=["rmat", "ba", "ba64", "batch", "serve", "small"])
+    ap.add_argument("--workload", default="rmat", choices=["rmat", "rmat_s", "ba", "ba64", "batch", "serve", "small"])
     ap.add_argument("--scale", type=int, default=22, help="R-MAT scale (22 is the configured size)")
     ap.add_argument("--k", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -53,6 +53,10 @@ def workload_spec(args):
     if args.workload == "rmat":
         return dict(name=f"R-MAT scale {args.scale}, edge factor 16 (0.57/0.19/0.19/0.05), greedy k={args.k} FP32",
                     kind="greedy", graph=("rmat", args.scale), k=args.k, precision="fp32", eps=1e-4)
+    if args.workload == "rmat_s":
+        return dict(name=f"R-MAT scale {args.scale}, edge factor 16, stochastic greedy (eta=0.1) k={args.k} FP32",
+                    kind="greedy", graph=("rmat", args.scale), k=args.k, precision="fp32", eps=1e-4,
+                    stochastic=True, eta=0.1, seed=1)
     if args.workload in ("ba", "ba64"):
         prec = "fp64" if args.workload == "ba64" else "fp32"
         return dict(name=f"Barabasi-Albert n=1M m=8, greedy k={args.k} {prec.upper()}", kind="greedy",
@@ -245,7 +249,9 @@ def run_greedy(args, spec, rank, world, local):
     t_up = time.perf_counter()
     G = gedwalk.Graph.from_host(g)
     upload_s = time.perf_counter() - t_up
-    params = gedwalk.make_params(epsilon=spec["eps"], precision=spec["precision"], stream=stream.cuda_stream)
+    params = gedwalk.make_params(epsilon=spec["eps"], precision=spec["precision"], stream=stream.cuda_stream,
+                                 stochastic=spec.get("stochastic", False), eta=spec.get("eta", 0.1),
+                                 seed=spec.get("seed", 0))
     k = spec["k"]
     for _ in range(args.warmup):
         grp, gains, score, L = G.maximize(k, params=params)
@@ -302,7 +308,7 @@ def run_greedy(args, spec, rank, world, local):
                       "seconds": round(t_e2e, 3), "h2d_bytes_per_step": int(rp.nbytes + ci.nbytes),
                       "d2h_bytes_per_step": int(k * 12 + 16)}
         del np
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and not args.no_cpu_baseline and not spec.get("stochastic"):
         out["cpu_baseline"] = oracle_greedy_sample(g, spec, L)
     return out
 

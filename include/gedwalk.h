@@ -71,7 +71,8 @@ enum {
 
 /* gedwalk_params.flags */
 enum {
-  GEDWALK_GAINS_ALL = 1 /* maximize: evaluate every vertex's exact gain at every step (no pruning) */
+  GEDWALK_GAINS_ALL = 1,  /* maximize: evaluate every vertex's exact gain at every step (no pruning) */
+  GEDWALK_STOCHASTIC = 2  /* maximize: stochastic greedy (Appendix D), see gedwalk_maximize */
 };
 
 /* gedwalk_graph_upload flags */
@@ -85,11 +86,14 @@ typedef struct {
   int32_t L;               /* 0: smallest l with B_l < epsilon (Algorithm 1); > 0: forced length */
   int32_t precision;       /* GEDWALK_FP64 or GEDWALK_FP32 */
   int32_t greedy_eps_rule; /* GEDWALK_EPS_OVER_K (default) or GEDWALK_EPS_PLAIN */
-  int32_t flags;           /* GEDWALK_GAINS_ALL */
+  int32_t flags;           /* GEDWALK_GAINS_ALL, GEDWALK_STOCHASTIC */
   int64_t stream;          /* cudaStream_t to run on (e.g. torch.cuda.current_stream().cuda_stream); 0 = default */
+  double eta;              /* stochastic greedy: sample (n/k) ln(1/eta) vertices per step, 0 < eta < 1 */
+  uint64_t seed;           /* stochastic greedy: seed of the counter-based sample draws */
 } gedwalk_params;
 
-/* Fills *p with the defaults: alpha 0, epsilon 1e-4, L 0, FP32, EPS_OVER_K, no flags, stream 0. */
+/* Fills *p with the defaults: alpha 0, epsilon 1e-4, L 0, FP32, EPS_OVER_K, no flags, stream 0,
+ * eta 0.1, seed 0. */
 GEDWALK_API void gedwalk_params_default(gedwalk_params* p);
 
 /*
@@ -196,6 +200,13 @@ GEDWALK_API gedwalk_status gedwalk_gains(gedwalk_graph_t g, const int32_t* S, in
  *  L_used: may be NULL.
  *  init_group/init_len: resume from this prefix group (may be NULL/0).
  * GEDWALK_GAINS_ALL in params->flags evaluates every vertex at every step.
+ * GEDWALK_STOCHASTIC runs stochastic greedy (Appendix D): at step s only a sample
+ * competes, vertex v (caller id, not in S) being sampled iff
+ *   splitmix64(seed ^ (s << 32) ^ v) < p * 2^64,  p = min(1, m / |V \ S|),
+ *   m = ceil((n/k) ln(1/eta)),
+ * where splitmix64(x) is the first output of that generator started from state x;
+ * an empty sample falls back to all of V \ S. The argmax within the sample is exact.
+ * It cannot be combined with GEDWALK_GAINS_ALL or an init group.
  */
 GEDWALK_API gedwalk_status gedwalk_maximize(gedwalk_graph_t g, int32_t k, const gedwalk_params* params, int32_t* group,
                                 double* gains, double* score, int32_t* L_used, const int32_t* init_group,

@@ -75,6 +75,11 @@ def _load():
             lib.orc_greedy_d.restype = ctypes.c_int
             lib.orc_greedy_d.argtypes = G + [ctypes.c_int32, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
                                              _i32p, ctypes.c_int32, _i32p, _f64p, _i64p]
+            lib.orc_greedy_stochastic_d.restype = ctypes.c_int
+            lib.orc_greedy_stochastic_d.argtypes = G + [ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
+                                                        ctypes.c_double, ctypes.c_uint64, _i32p, _f64p, _i64p]
+            lib.orc_sample_hash.restype = ctypes.c_uint64
+            lib.orc_sample_hash.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32]
             lib.orc_brute_phi.restype = ctypes.c_int
             lib.orc_brute_phi.argtypes = G + [_i32p, ctypes.c_int32, ctypes.c_int32, _u64p, _u64p]
             lib.orc_brute_gain.restype = ctypes.c_int
@@ -185,6 +190,24 @@ def greedy(graph, k: int, alpha: float, L: int, mode: str = "all", init=None):
                               _ptr(ini, _i32p), il, _ptr(group, _i32p), _ptr(gains, _f64p), ctypes.byref(ev))
     if rc != 0:
         raise ValueError("oracle greedy: invalid arguments")
+    return group[:k].copy(), gains[:k].copy(), int(ev.value)
+
+
+def sample_hash(seed: int, step: int, v: int) -> int:
+    """The counter-based draw of stochastic greedy: splitmix64's first output from seed ^ (step<<32) ^ v."""
+    return int(_load().orc_sample_hash(seed, step, v))
+
+
+def greedy_stochastic(graph, k: int, alpha: float, L: int, eta: float, seed: int):
+    """Stochastic greedy (Appendix D) at fixed L: (group, gains, evaluations)."""
+    n, rp, ci = _g(graph)
+    group = np.zeros(max(k, 1), dtype=np.int32)
+    gains = np.zeros(max(k, 1), dtype=np.float64)
+    ev = ctypes.c_int64(0)
+    rc = _load().orc_greedy_stochastic_d(n, _ptr(rp, _i32p), _ptr(ci, _i32p), k, alpha, L, eta, seed,
+                                         _ptr(group, _i32p), _ptr(gains, _f64p), ctypes.byref(ev))
+    if rc != 0:
+        raise ValueError("oracle stochastic greedy: invalid arguments")
     return group[:k].copy(), gains[:k].copy(), int(ev.value)
 
 

@@ -107,6 +107,18 @@ int orc_brute_gain(int32_t n, const int32_t* rp, const int32_t* ci, const int32_
   return 0;
 }
 
+/*
+ * Counter-based draw for stochastic greedy (Appendix D): the first output of splitmix64
+ * (Steele, Lea & Flood, 2014) started from state seed ^ (step << 32) ^ v. Written here from
+ * the published definition; the library implements its own copy.
+ */
+uint64_t orc_sample_hash(uint64_t seed, uint32_t step, uint32_t v) {
+  uint64_t z = (seed ^ ((uint64_t)step << 32) ^ (uint64_t)v) + 0x9e3779b97f4a7c15ULL;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+  return z ^ (z >> 31);
+}
+
 /* long-double entry points exchange values as double for the ctypes wrapper */
 double orc_score_ld_as_d(int32_t n, const int32_t* rp, const int32_t* ci, const int32_t* S, int32_t s_len,
                          double alpha, int32_t L) {

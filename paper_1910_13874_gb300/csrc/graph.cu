@@ -476,6 +476,8 @@ gedwalk_status resolve(Graph& g, const gedwalk_params* p, double eps_override, R
     return fail(GEDWALK_ERR_INVALID, "precision must be GEDWALK_FP64 or GEDWALK_FP32");
   r->fp64 = p->precision == GEDWALK_FP64;
   r->stream = reinterpret_cast<cudaStream_t>(p->stream);
+  r->eta = p->eta;
+  r->seed = p->seed;
   if (p->L < 0) return fail(GEDWALK_ERR_INVALID, "L must be >= 0");
   if (p->L > 0) {
     if (p->L > 4096) return fail(GEDWALK_ERR_INVALID, "L must be <= 4096");
@@ -531,6 +533,8 @@ void gedwalk_params_default(gedwalk_params* p) {
   p->greedy_eps_rule = GEDWALK_EPS_OVER_K;
   p->flags = 0;
   p->stream = 0;
+  p->eta = 0.1;
+  p->seed = 0;
 }
 
 const char* gedwalk_last_error(void) { return t_last_error.c_str(); }

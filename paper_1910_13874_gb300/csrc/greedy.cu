@@ -42,11 +42,28 @@ struct SelOut {  // device -> host after each selection pass
   float val[kTopK];
   int32_t id[kTopK];
   int32_t zero_min_caller;  // smallest caller id among unevaluated vertices with bound exactly 0
-  int32_t pad[3];
+  int32_t sampled;          // stochastic greedy: sampled vertices outside S seen by the pass
+  int32_t pad[2];
   double gains[16];          // exact gains of the last candidate batch
 };
 
 __device__ __forceinline__ bool better(float a, int ia, float b, int ib) { return a > b || (a == b && ia < ib); }
+
+// Stochastic greedy's counter-based draw: the first output of splitmix64 (Steele, Lea & Flood,
+// 2014) started from state seed ^ (step << 32) ^ v, v a caller id.
+__device__ __forceinline__ uint64_t sample_hash(uint64_t seed, uint32_t step, uint32_t v) {
+  uint64_t z = (seed ^ (static_cast<uint64_t>(step) << 32) ^ static_cast<uint64_t>(v)) + 0x9e3779b97f4a7c15ULL;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+  return z ^ (z >> 31);
+}
+
+// Sampling of one selection pass; thr == UINT64_MAX means every vertex takes part.
+struct Sampling {
+  uint64_t thr;
+  uint64_t seed;
+  uint32_t step;
+};
 
 __device__ __forceinline__ void topk_push(float (&v)[kTopK], int (&id)[kTopK], float x, int ix) {
   if (!better(x, ix, v[kTopK - 1], id[kTopK - 1])) return;
@@ -190,7 +207,9 @@ __global__ void __launch_bounds__(kThreads) ub_select(const T* __restrict__ mtab
                                                      const uint32_t* __restrict__ mask,
                                                      const Stale* __restrict__ stale, int32_t step,
                                                      const int32_t* __restrict__ perm, float* __restrict__ sel_v,
-                                                     int* __restrict__ sel_id, int32_t* __restrict__ zero_min) {
+                                                     int* __restrict__ sel_id, int32_t* __restrict__ zero_min,
+                                                     const Sampling smp, int32_t* __restrict__ sampled) {
+  int nsampled = 0;
   float v[kTopK];
   int id[kTopK];
 #pragma unroll
@@ -212,8 +231,12 @@ __global__ void __launch_bounds__(kThreads) ub_select(const T* __restrict__ mtab
       float ub = LF > 0 ? ub_fixed<T, (LF > 0 ? LF : 1)>(mtab + x, n) : ub_any<T>(mtab + x, n, L);
       if (st.step >= 0 && st.ub < ub) ub = st.ub;
       b[k] = ub;
+      bool in_sample = true;
+      if (smp.thr != ~0ull && xr < n && !inS)
+        in_sample = sample_hash(smp.seed, smp.step, static_cast<uint32_t>(__ldg(perm + x))) < smp.thr;
+      if (xr < n && !inS && in_sample) ++nsampled;
       // evaluated with the current S: its exact gain is known
-      live[k] = xr < n && !inS && st.step != step;
+      live[k] = xr < n && !inS && in_sample && st.step != step;
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -225,6 +248,11 @@ __global__ void __launch_bounds__(kThreads) ub_select(const T* __restrict__ mtab
       }
       topk_push(v, id, b[k], x);
     }
+  }
+  if (smp.thr != ~0ull) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nsampled += __shfl_xor_sync(0xffffffffu, nsampled, o);
+    if ((threadIdx.x & 31) == 0 && nsampled) atomicAdd(sampled, nsampled);
   }
   __shared__ float ov[kTopK];
   __shared__ int oi[kTopK];
@@ -238,13 +266,18 @@ __global__ void __launch_bounds__(kThreads) ub_select(const T* __restrict__ mtab
 template <typename T>
 cudaError_t launch_ub_select(int nb, cudaStream_t s, const T* mtab, int32_t L, int32_t n, const uint32_t* mask,
                              const Stale* stale, int32_t step, const int32_t* perm, float* sel_v, int* sel_id,
-                             int32_t* zero_min) {
-#define GW_UB(LL) \
-  case LL: ub_select<T, LL><<<nb, kThreads, 0, s>>>(mtab, L, n, mask, stale, step, perm, sel_v, sel_id, zero_min); break;
+                             int32_t* zero_min, const Sampling& smp, int32_t* sampled) {
+#define GW_UB(LL)                                                                                          \
+  case LL:                                                                                                 \
+    ub_select<T, LL><<<nb, kThreads, 0, s>>>(mtab, L, n, mask, stale, step, perm, sel_v, sel_id, zero_min, smp, \
+                                             sampled);                                                     \
+    break;
   switch (L) {
     GW_UB(1) GW_UB(2) GW_UB(3) GW_UB(4) GW_UB(5) GW_UB(6) GW_UB(7) GW_UB(8)
     GW_UB(9) GW_UB(10) GW_UB(11) GW_UB(12) GW_UB(13) GW_UB(14) GW_UB(15) GW_UB(16)
-    default: ub_select<T, 0><<<nb, kThreads, 0, s>>>(mtab, L, n, mask, stale, step, perm, sel_v, sel_id, zero_min);
+    default:
+      ub_select<T, 0><<<nb, kThreads, 0, s>>>(mtab, L, n, mask, stale, step, perm, sel_v, sel_id, zero_min, smp,
+                                              sampled);
   }
 #undef GW_UB
   return cudaGetLastError();
@@ -273,7 +306,11 @@ __global__ void __launch_bounds__(kMergeThreads) select_merge(const float* __res
   }
 }
 
-__global__ void set_int(int32_t* p, int32_t v) { *p = v; }
+// Resets the per-pass counters of a selection pass.
+__global__ void reset_selection(SelOut* out) {
+  out->zero_min_caller = INT_MAX;
+  out->sampled = 0;
+}
 
 int blocks_for(int64_t n) { return static_cast<int>(std::min<int64_t>((n + 255) / 256, 152 * 16)); }
 
@@ -468,6 +505,12 @@ gedwalk_status maximize_impl(Graph& g, Workspace& ws, int32_t k, const Resolved&
   const int cols_all = r.fp64 ? 8 : 16;
   const double tol = r.fp64 ? 1e-11 : 1e-5;  // relative inflation of bounds against rounding
   const bool gains_all = (flags & GEDWALK_GAINS_ALL) != 0;
+  const bool stochastic = (flags & GEDWALK_STOCHASTIC) != 0;
+  if (stochastic && (gains_all || !init_int.empty()))
+    return fail(GEDWALK_ERR_INVALID, "stochastic greedy cannot be combined with GEDWALK_GAINS_ALL or an init group");
+  if (stochastic && !(r.eta > 0.0 && r.eta < 1.0)) return fail(GEDWALK_ERR_INVALID, "eta must lie in (0, 1)");
+  // stochastic greedy: about m vertices outside S are sampled per step (Appendix D)
+  const double sample_m = std::ceil(static_cast<double>(g.n) / std::max(k, 1) * std::log(1.0 / (stochastic ? r.eta : 0.5)));
   const int32_t L = r.L;
   ws.st_evals = ws.st_batches = ws.st_sweeps = ws.st_spec_miss = 0;
 
@@ -522,6 +565,13 @@ gedwalk_status maximize_impl(Graph& g, Workspace& ws, int32_t k, const Resolved&
         }
       }
     } else {
+      Sampling smp{~0ull, r.seed, static_cast<uint32_t>(step)};
+      if (stochastic) {
+        const double p = sample_m / static_cast<double>(g.n - step);
+        const double scaled = p * 18446744073709551616.0;
+        if (p < 1.0 && scaled < 18446744073709551615.0) smp.thr = static_cast<uint64_t>(scaled);
+        spec.clear();  // the next step draws a new sample: no speculation
+      }
       // 1. fused sweeps: phi^miss under S plus the speculative candidates
       std::vector<int32_t> sc;
       for (const Cand& e : spec) sc.push_back(e.v);
@@ -536,20 +586,26 @@ gedwalk_status maximize_impl(Graph& g, Workspace& ws, int32_t k, const Resolved&
           GW_KCHECK();
         }
         // 2. bound + selection pass
-        set_int<<<1, 1, 0, s>>>(&c.d_out->zero_min_caller, INT_MAX);
+        reset_selection<<<1, 1, 0, s>>>(c.d_out);
         const int nb = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(kSelBlocks, (int64_t(g.n) + 1023) / 1024)));
         if (r.fp64)
           GW_CUDA(launch_ub_select<double>(nb, s, ws.mtab.as<double>(), L, g.n, ws.mask.as<uint32_t>(), stale, step,
-                                           g.perm_d.as<int32_t>(), sel_v, sel_id, &c.d_out->zero_min_caller));
+                                           g.perm_d.as<int32_t>(), sel_v, sel_id, &c.d_out->zero_min_caller, smp,
+                                           &c.d_out->sampled));
         else
           GW_CUDA(launch_ub_select<float>(nb, s, ws.mtab.as<float>(), L, g.n, ws.mask.as<uint32_t>(), stale, step,
-                                          g.perm_d.as<int32_t>(), sel_v, sel_id, &c.d_out->zero_min_caller));
+                                          g.perm_d.as<int32_t>(), sel_v, sel_id, &c.d_out->zero_min_caller, smp,
+                                          &c.d_out->sampled));
         count_launch();
         select_merge<<<1, kMergeThreads, 0, s>>>(sel_v, sel_id, nb * kTopK, c.d_out);
         GW_KCHECK();
         GW_CUDA(cudaMemcpyAsync(c.h_out, c.d_out, sizeof(SelOut), cudaMemcpyDeviceToHost, s));
         GW_CUDA(cudaStreamSynchronize(s));
         read_graph_timing(ws);
+        if (smp.thr != ~0ull && c.h_out->sampled == 0) {  // empty sample: all of V \ S competes
+          smp.thr = ~0ull;
+          continue;
+        }
         for (size_t j = 0; j < last.size(); ++j) {
           Cand e{c.h_out->gains[j], last[j], g.perm[last[j]]};
           E.push_back(e);

@@ -247,6 +247,8 @@ struct Resolved {
   double bound;  // B_L, NaN when L was forced without a valid bound
   bool fp64;
   cudaStream_t stream;
+  double eta = 0.1;    // stochastic greedy sample parameter
+  uint64_t seed = 0;   // stochastic greedy seed
 };
 // Resolves alpha (0 -> default), L (from epsilon unless forced) for a given epsilon.
 gedwalk_status resolve(Graph& g, const gedwalk_params* p, double eps_override, Resolved* r);

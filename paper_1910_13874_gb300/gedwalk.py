@@ -20,6 +20,7 @@ OK, ERR_INVALID, ERR_OOM, ERR_NOT_CONVERGENT, ERR_DEVICE, ERR_TIMEOUT, ERR_BUSY,
 FP64, FP32 = 0, 1
 EPS_OVER_K, EPS_PLAIN = 0, 1
 GAINS_ALL = 1
+STOCHASTIC = 2
 UPLOAD_TRUSTED = 1
 REQ_SCORE, REQ_MAXIMIZE = 0, 1
 
@@ -67,6 +68,8 @@ class Params(ctypes.Structure):
         ("greedy_eps_rule", ctypes.c_int32),
         ("flags", ctypes.c_int32),
         ("stream", ctypes.c_int64),
+        ("eta", ctypes.c_double),
+        ("seed", ctypes.c_uint64),
     ]
 
 
@@ -146,7 +149,8 @@ def _ptr(a: np.ndarray, t):
 
 
 def make_params(alpha: float = 0.0, epsilon: float = 1e-4, L: int = 0, precision: str = "fp32",
-                eps_rule: str = "over_k", gains_all: bool = False, stream: int = 0) -> Params:
+                eps_rule: str = "over_k", gains_all: bool = False, stream: int = 0, stochastic: bool = False,
+                eta: float = 0.1, seed: int = 0) -> Params:
     p = Params()
     load().gedwalk_params_default(ctypes.byref(p))
     p.alpha = alpha
@@ -154,8 +158,10 @@ def make_params(alpha: float = 0.0, epsilon: float = 1e-4, L: int = 0, precision
     p.L = L
     p.precision = FP64 if precision in ("fp64", "f64", FP64) else FP32
     p.greedy_eps_rule = EPS_PLAIN if eps_rule == "plain" else EPS_OVER_K
-    p.flags = GAINS_ALL if gains_all else 0
+    p.flags = (GAINS_ALL if gains_all else 0) | (STOCHASTIC if stochastic else 0)
     p.stream = int(stream)
+    p.eta = eta
+    p.seed = seed
     return p
 
 

@@ -288,3 +288,29 @@ def test_score_batch(cuda_device, name):
     # empty groups and duplicate members
     s2, _ = G.score_batch([0, 0, 4], [5, 5, 6, 5], epsilon=1e-4)
     assert s2[0] == 0.0 and rel(s2[1], oracle.score(g, [5, 6], alpha, L)) < 1e-5
+
+
+# ------------------------------------------------------------------ stochastic greedy (Appendix D)
+@pytest.mark.parametrize("name,k,eta,seed", [("ba5000", 20, 0.1, 1), ("rmat14", 20, 0.2, 5), ("er1000", 8, 0.3, 9)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_stochastic_maximize_matches_oracle(cuda_device, name, k, eta, seed, prec):
+    g = host_graph(name)
+    G = dev_graph(name)
+    alpha = oracle.default_alpha(g)
+    grp, gains, score, L = G.maximize(k, precision=prec, epsilon=1e-4, stochastic=True, eta=eta, seed=seed)
+    ogrp, ogains, _ = oracle.greedy_stochastic(g, k, alpha, L, eta, seed)
+    tol = TOL[prec]
+    for j in range(k):
+        if grp[j] != ogrp[j]:  # sequences may part only at a tie inside the tolerance
+            assert abs(gains[j] - ogains[j]) <= tol * ogains[j], (j, grp[j], ogrp[j])
+            break
+        assert gains[j] == ogains[j] == 0.0 or rel(gains[j], ogains[j]) < tol
+    # every pick lies in its step's sample (the oracle's own draw)
+    import math
+
+    m = math.ceil(g.n / k * math.log(1.0 / eta))
+    for j in range(k):
+        p = m / (g.n - j)
+        if p < 1.0:
+            assert oracle.sample_hash(seed, j, int(grp[j])) < int(p * 2.0 ** 64)
+    assert rel(score, oracle.score(g, grp, alpha, L)) < tol

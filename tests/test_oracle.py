@@ -340,3 +340,61 @@ def test_empty_group_and_isolated_vertices():
     assert oracle.score(g, [4], alpha, 5) == 0.0
     assert oracle.gain(g, [], 3, alpha, 5) == 0.0
     assert oracle.upper_bounds(g, [], alpha, 5)[3] == 0.0
+
+
+# ---------------------------------------------------------------- stochastic greedy (Appendix D)
+def test_sample_hash_is_splitmix64():
+    # splitmix64 started from state 0 first outputs 0xE220A8397B1DCDAF (its published reference value)
+    assert oracle.sample_hash(0, 0, 0) == 0xE220A8397B1DCDAF
+    # the state is seed ^ (step << 32) ^ v: for a fixed seed every (step, v) gives its own draw,
+    # and the draws of one step are uniform (mean of u/2^64 near 1/2)
+    outs = {oracle.sample_hash(7, t, v) for t in range(4) for v in range(64)}
+    assert len(outs) == 256
+    u = np.array([oracle.sample_hash(7, 3, v) for v in range(4000)], dtype=np.float64) / 2.0 ** 64
+    assert abs(u.mean() - 0.5) < 0.02 and abs((u < 0.25).mean() - 0.25) < 0.03
+
+
+def _stochastic_threshold(n, k, step, eta):
+    m = math.ceil(n / k * math.log(1.0 / eta))
+    p = m / (n - step)
+    return None if p >= 1.0 else int(p * 2.0 ** 64)
+
+
+def test_stochastic_greedy_with_full_samples_is_greedy():
+    # with (n/k) ln(1/eta) >= n every vertex is sampled and the algorithm is plain greedy
+    g = gg.erdos_renyi(120, 6, 2)
+    alpha = oracle.default_alpha(g)
+    grp, gains, _ = oracle.greedy_stochastic(g, 4, alpha, 6, 1e-9, 3)
+    full, fgains, _ = oracle.greedy(g, 4, alpha, 6, "all")
+    assert list(grp) == list(full) and np.allclose(gains, fgains, rtol=1e-15, atol=0)
+
+
+def test_stochastic_greedy_picks_the_best_sampled_vertex():
+    g = gg.barabasi_albert(400, 3, 4)
+    alpha = oracle.default_alpha(g)
+    k, eta, seed, L = 8, 0.3, 11, 6
+    grp, gains, evals = oracle.greedy_stochastic(g, k, alpha, L, eta, seed)
+    S = []
+    sizes = []
+    for step in range(k):
+        thr = _stochastic_threshold(g.n, k, step, eta)
+        sample = [v for v in range(g.n) if v not in S and (thr is None or oracle.sample_hash(seed, step, v) < thr)]
+        sizes.append(len(sample))
+        assert int(grp[step]) in sample
+        best = max(oracle.gain(g, S, v, alpha, L) for v in sample)
+        assert gains[step] == best
+        S.append(int(grp[step]))
+    # the samples have about (n/k) ln(1/eta) members
+    m = g.n / k * math.log(1 / eta)
+    assert 0.6 * m < np.mean(sizes) < 1.4 * m
+    assert evals == sum(sizes)
+
+
+def test_stochastic_greedy_approximation_in_expectation():
+    # E[f(S)] >= (1 - 1/e - eta) f(S*) (Appendix D); checked on the mean over seeds
+    g = gg.random_graph_small(10, 0.4, 21)
+    alpha = 1.0 / (1 + g.d_max)
+    L, k, eta = 6, 3, 0.2
+    best = max(oracle.score(g, list(c), alpha, L) for c in itertools.combinations(range(g.n), k))
+    vals = [oracle.score(g, list(oracle.greedy_stochastic(g, k, alpha, L, eta, s)[0]), alpha, L) for s in range(40)]
+    assert np.mean(vals) >= (1 - 1 / math.e - eta) * best
