@@ -78,6 +78,10 @@ def _load():
             lib.orc_greedy_stochastic_d.restype = ctypes.c_int
             lib.orc_greedy_stochastic_d.argtypes = G + [ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
                                                         ctypes.c_double, ctypes.c_uint64, _i32p, _f64p, _i64p]
+            lib.orc_greedy_adaptive_d.restype = ctypes.c_int
+            lib.orc_greedy_adaptive_d.argtypes = G + [ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                                      ctypes.c_int32, _i32p, _f64p, _i32p, _i64p, ctypes.c_int32,
+                                                      _i32p, _i32p, _f64p, _f64p, _f64p, _i32p]
             lib.orc_sample_hash.restype = ctypes.c_uint64
             lib.orc_sample_hash.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32]
             lib.orc_brute_phi.restype = ctypes.c_int
@@ -209,6 +213,38 @@ def greedy_stochastic(graph, k: int, alpha: float, L: int, eta: float, seed: int
     if rc != 0:
         raise ValueError("oracle stochastic greedy: invalid arguments")
     return group[:k].copy(), gains[:k].copy(), int(ev.value)
+
+
+def greedy_adaptive(graph, k: int, alpha: float, eps_sep: float, lcap: int = 4096):
+    """Lazy greedy with l-doubling and eps_sep-separation (Algorithm 2).
+
+    Returns a dict: group, gains (L_l(S, u) at each step's l), ell (each step's l), evals, and
+    the separation tests as arrays att_step, att_ell, att_gu, att_gv (-1 without v), att_B.
+    """
+    n, rp, ci = _g(graph)
+    group = np.zeros(max(k, 1), dtype=np.int32)
+    gains = np.zeros(max(k, 1), dtype=np.float64)
+    ell = np.zeros(max(k, 1), dtype=np.int32)
+    cap = 4 * k + 64
+    a_step = np.zeros(cap, dtype=np.int32)
+    a_ell = np.zeros(cap, dtype=np.int32)
+    a_gu = np.zeros(cap, dtype=np.float64)
+    a_gv = np.zeros(cap, dtype=np.float64)
+    a_B = np.zeros(cap, dtype=np.float64)
+    ev = ctypes.c_int64(0)
+    na = ctypes.c_int32(0)
+    rc = _load().orc_greedy_adaptive_d(n, _ptr(rp, _i32p), _ptr(ci, _i32p), k, alpha, eps_sep, lcap,
+                                       _ptr(group, _i32p), _ptr(gains, _f64p), _ptr(ell, _i32p), ctypes.byref(ev),
+                                       cap, _ptr(a_step, _i32p), _ptr(a_ell, _i32p), _ptr(a_gu, _f64p),
+                                       _ptr(a_gv, _f64p), _ptr(a_B, _f64p), ctypes.byref(na))
+    if rc == -2:
+        raise ValueError("oracle adaptive greedy: l exceeded lcap")
+    if rc != 0:
+        raise ValueError("oracle adaptive greedy: invalid arguments")
+    m = min(int(na.value), cap)
+    return {"group": group[:k].copy(), "gains": gains[:k].copy(), "ell": ell[:k].copy(), "evals": int(ev.value),
+            "att_step": a_step[:m].copy(), "att_ell": a_ell[:m].copy(), "att_gu": a_gu[:m].copy(),
+            "att_gv": a_gv[:m].copy(), "att_B": a_B[:m].copy()}
 
 
 def brute_phi(graph, S, i: int):

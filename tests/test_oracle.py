@@ -398,3 +398,125 @@ def test_stochastic_greedy_approximation_in_expectation():
     best = max(oracle.score(g, list(c), alpha, L) for c in itertools.combinations(range(g.n), k))
     vals = [oracle.score(g, list(oracle.greedy_stochastic(g, k, alpha, L, eta, s)[0]), alpha, L) for s in range(40)]
     assert np.mean(vals) >= (1 - 1 / math.e - eta) * best
+
+
+# ---------------------------------------------------------------- lazy greedy with l-doubling (Algorithm 2)
+def _bound(g, alpha, l):
+    _, Wa = oracle.walk_totals(g, alpha, l)
+    return oracle.comb_bound(g, alpha, Wa[l])
+
+
+def _all_gains(g, S, alpha, l):
+    return np.array([oracle.gain(g, S, x, alpha, l) if x not in S else -np.inf for x in range(g.n)])
+
+
+def _top2(gv):
+    order = sorted(range(len(gv)), key=lambda x: (-gv[x], x))
+    return order[0], (order[1] if len(order) > 1 and np.isfinite(gv[order[1]]) else None)
+
+
+@pytest.mark.parametrize("kind,eps", [("er", 1e-4), ("er", 1e-2), ("ba", 1e-5), ("small", 1e-3)])
+def test_adaptive_greedy_separation_and_doubling(kind, eps):
+    # Every pick is the argmax of L_l(S, .) at the step's l and is eps/k-separated from the runner-up
+    # (Def. separation with U_l = L_l + B_l); every smaller power of two that l passed through on
+    # that step failed the test. Gains come from the independent per-vertex routine.
+    g = {"er": lambda: gg.erdos_renyi(150, 6, 3), "ba": lambda: gg.barabasi_albert(200, 3, 4),
+         "small": lambda: gg.random_graph_small(11, 0.4, 7)}[kind]()
+    alpha = oracle.default_alpha(g)
+    k = 6
+    sep = eps / k
+    r = oracle.greedy_adaptive(g, k, alpha, sep)
+    ell = r["ell"]
+    assert all(int(l) & (int(l) - 1) == 0 for l in ell) and np.all(np.diff(ell) >= 0)
+    L_fixed = oracle.select_L(g, alpha, sep)[0]
+    assert ell[-1] < 2 * L_fixed  # B_l < eps/k forces separation once l >= L(eps/k)
+    prev = 1
+    for j in range(k):
+        S = list(r["group"][:j])
+        # the levels tried and failed on this step
+        l = prev
+        while l < ell[j]:
+            gv = _all_gains(g, S, alpha, l)
+            u, v = _top2(gv)
+            assert v is not None and gv[u] <= gv[v] + _bound(g, alpha, l) - sep + 1e-12 * gv[u]
+            l *= 2
+        gv = _all_gains(g, S, alpha, int(ell[j]))
+        u, v = _top2(gv)
+        assert abs(gv[u] - r["gains"][j]) <= 1e-12 * max(gv[u], 1e-300)
+        assert abs(gv[r["group"][j]] - gv[u]) <= 1e-12 * max(gv[u], 1e-300)  # an argmax (ties: any)
+        if v is not None:
+            assert gv[r["group"][j]] > gv[v] + _bound(g, alpha, int(ell[j])) - sep - 1e-12 * gv[u]
+        prev = int(ell[j])
+
+
+def test_adaptive_greedy_additive_guarantee():
+    # Separation at eps/k makes each pick's true gain within eps/k of the best true gain
+    # (Prop. additive-greedy); "true" here is a truncation far beyond the bound.
+    g = gg.erdos_renyi(120, 5, 11)
+    alpha = oracle.default_alpha(g)
+    k, eps = 5, 1e-3
+    r = oracle.greedy_adaptive(g, k, alpha, eps / k)
+    Lbig = 120
+    for j in range(k):
+        S = list(r["group"][:j])
+        gv = _all_gains(g, S, alpha, Lbig)
+        assert gv[r["group"][j]] >= gv[np.isfinite(gv)].max() - eps / k
+
+
+def test_adaptive_greedy_at_l1_is_remaining_degree_greedy():
+    # With eps/k above B_1 the separation test always passes at l = 1, where L_1(S, x) counts the
+    # two orientations of every edge from x to V \ S: 2 alpha |N(x) \ S|. So the picks follow the
+    # largest remaining degree (lowest id among equals), computed here from the adjacency matrix.
+    g = gg.erdos_renyi(80, 6, 5)
+    alpha = oracle.default_alpha(g)
+    k = 8
+    sep = 2 * _bound(g, alpha, 1)
+    r = oracle.greedy_adaptive(g, k, alpha, sep)
+    assert list(r["ell"]) == [1] * k
+    A = g.to_dense().astype(bool)
+    S = []
+    for j in range(k):
+        rem = np.ones(g.n, dtype=bool)
+        rem[S] = False
+        deg = np.where(rem, (A & rem[None, :]).sum(axis=1), -1)
+        want = int(np.argmax(deg))
+        assert r["group"][j] == want
+        assert abs(r["gains"][j] - 2 * alpha * deg[want]) <= 1e-14
+        S.append(want)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_adaptive_greedy_against_exhaustive_optimum(seed):
+    # (1 - 1/e) OPT - eps for the untruncated objective (Lemma after Algorithm 2); OPT by exhaustion
+    g = gg.random_graph_small(9, 0.35, 70 + seed)
+    alpha = oracle.default_alpha(g)
+    Lbig, eps = 80, 1e-3
+    for k in (1, 2, 3):
+        r = oracle.greedy_adaptive(g, k, alpha, eps / k)
+        best = max(oracle.score(g, list(c), alpha, Lbig) for c in itertools.combinations(range(g.n), k))
+        assert oracle.score(g, list(r["group"]), alpha, Lbig) >= (1 - 1 / math.e) * best - eps
+
+
+def test_adaptive_greedy_records_and_star():
+    g = gg.star(9)
+    alpha = 1.0 / 10
+    r = oracle.greedy_adaptive(g, 3, alpha, 1e-4)
+    assert r["group"][0] == 0  # the centre first
+    # after the centre joins, every gain is 0: no l separates 0 from 0 until B_l < eps, so l grows
+    assert r["gains"][1] == 0.0 and _bound(g, alpha, int(r["ell"][1])) < 1e-4
+    # each failed test is followed by a test of the same step at twice the length
+    st, el, gu, gv, B = r["att_step"], r["att_ell"], r["att_gu"], r["att_gv"], r["att_B"]
+    for i in range(len(st)):
+        sep_ok = gv[i] < 0 or gu[i] > gv[i] + B[i] - 1e-4
+        if not sep_ok:
+            assert st[i + 1] == st[i] and el[i + 1] == 2 * el[i]
+        elif i + 1 < len(st):
+            assert st[i + 1] == st[i] + 1 and el[i + 1] == el[i]
+
+
+def test_adaptive_greedy_rejects_bad_input():
+    g = gg.complete(5)
+    with pytest.raises(ValueError):
+        oracle.greedy_adaptive(g, 2, 0.3, 1e-3)  # alpha * d_max >= 1: no bound
+    with pytest.raises(ValueError):
+        oracle.greedy_adaptive(g, 2, 0.1, 1e-30, lcap=4)  # l would pass the cap
