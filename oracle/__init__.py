@@ -51,35 +51,40 @@ def _load():
         if _lib is None:
             lib = ctypes.CDLL(build())
             G = [ctypes.c_int32, _i32p, _i32p]
+            GW = G + [_f64p]  # graph with optional entry weights (NULL: unweighted)
             lib.orc_dmax.restype = ctypes.c_int32
             lib.orc_dmax.argtypes = [ctypes.c_int32, _i32p]
             lib.orc_walk_totals_d.restype = ctypes.c_int
-            lib.orc_walk_totals_d.argtypes = G + [ctypes.c_double, ctypes.c_int32, _f64p, _f64p]
+            lib.orc_walk_totals_d.argtypes = GW + [ctypes.c_double, ctypes.c_int32, _f64p, _f64p]
             lib.orc_select_L_d.restype = ctypes.c_int32
-            lib.orc_select_L_d.argtypes = G + [ctypes.c_double, ctypes.c_double, ctypes.c_int32, _f64p]
+            lib.orc_select_L_d.argtypes = GW + [ctypes.c_double, ctypes.c_double, ctypes.c_int32, _f64p]
             lib.orc_comb_bound_d.restype = ctypes.c_double
-            lib.orc_comb_bound_d.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_double]
+            lib.orc_comb_bound_d.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
+            lib.orc_delta.restype = ctypes.c_double
+            lib.orc_delta.argtypes = [ctypes.c_int32, _i32p, _f64p]
+            lib.orc_normalized_weights.restype = None
+            lib.orc_normalized_weights.argtypes = G + [_f64p]
             lib.orc_score_d.restype = ctypes.c_double
-            lib.orc_score_d.argtypes = G + [_i32p, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, _f64p]
+            lib.orc_score_d.argtypes = GW + [_i32p, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, _f64p]
             lib.orc_score_ld_as_d.restype = ctypes.c_double
-            lib.orc_score_ld_as_d.argtypes = G + [_i32p, ctypes.c_int32, ctypes.c_double, ctypes.c_int32]
+            lib.orc_score_ld_as_d.argtypes = GW + [_i32p, ctypes.c_int32, ctypes.c_double, ctypes.c_int32]
             lib.orc_score_by_complement_d.restype = ctypes.c_double
-            lib.orc_score_by_complement_d.argtypes = G + [_i32p, ctypes.c_int32, ctypes.c_double, ctypes.c_int32]
+            lib.orc_score_by_complement_d.argtypes = GW + [_i32p, ctypes.c_int32, ctypes.c_double, ctypes.c_int32]
             lib.orc_gain_d.restype = ctypes.c_double
-            lib.orc_gain_d.argtypes = G + [_i32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_int32]
+            lib.orc_gain_d.argtypes = GW + [_i32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_int32]
             lib.orc_gain_ld_as_d.restype = ctypes.c_double
-            lib.orc_gain_ld_as_d.argtypes = G + [_i32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+            lib.orc_gain_ld_as_d.argtypes = GW + [_i32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                                  ctypes.c_int32]
             lib.orc_upper_bounds_d.restype = ctypes.c_int
-            lib.orc_upper_bounds_d.argtypes = G + [_i32p, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, _f64p]
+            lib.orc_upper_bounds_d.argtypes = GW + [_i32p, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, _f64p]
             lib.orc_greedy_d.restype = ctypes.c_int
-            lib.orc_greedy_d.argtypes = G + [ctypes.c_int32, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
+            lib.orc_greedy_d.argtypes = GW + [ctypes.c_int32, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
                                              _i32p, ctypes.c_int32, _i32p, _f64p, _i64p]
             lib.orc_greedy_stochastic_d.restype = ctypes.c_int
-            lib.orc_greedy_stochastic_d.argtypes = G + [ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
+            lib.orc_greedy_stochastic_d.argtypes = GW + [ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
                                                         ctypes.c_double, ctypes.c_uint64, _i32p, _f64p, _i64p]
             lib.orc_greedy_adaptive_d.restype = ctypes.c_int
-            lib.orc_greedy_adaptive_d.argtypes = G + [ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+            lib.orc_greedy_adaptive_d.argtypes = GW + [ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                                                       ctypes.c_int32, _i32p, _f64p, _i32p, _i64p, ctypes.c_int32,
                                                       _i32p, _i32p, _f64p, _f64p, _f64p, _i32p]
             lib.orc_sample_hash.restype = ctypes.c_uint64
@@ -104,6 +109,16 @@ def _ptr(a, t):
     return a.ctypes.data_as(t)
 
 
+def _wp(graph, w):
+    """Entry weights (float64[nnz], Section 5.4's weighted walks) as a pointer; None: unweighted."""
+    if w is None:
+        return None
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    if w.shape != (int(np.asarray(graph.col_idx).shape[0]),):
+        raise ValueError("weights must hold one value per CSR entry")
+    return w.ctypes.data_as(_f64p)  # the pointer keeps the array alive
+
+
 def _S(S):
     s = np.ascontiguousarray(np.asarray(S if S is not None else [], dtype=np.int32).ravel())
     if s.size == 0:
@@ -116,81 +131,95 @@ def dmax(graph) -> int:
     return int(_load().orc_dmax(n, _ptr(rp, _i32p)))
 
 
-def default_alpha(graph) -> float:
-    """alpha = 1/(1 + d_max): below 1/d_max, as the combinatorial bound requires (Sec. 3.1.2)."""
-    return 1.0 / (1.0 + dmax(graph))
+def delta(graph, w=None) -> float:
+    """The degree bound of Eq. comb-bound: d_max, or the largest weighted degree with weights."""
+    n, rp, _ = _g(graph)
+    return float(_load().orc_delta(n, _ptr(rp, _i32p), _wp(graph, w)))
 
 
-def walk_totals(graph, alpha: float, L: int):
+def default_alpha(graph, w=None) -> float:
+    """alpha = 1/(1 + delta): below 1/delta, as the combinatorial bound requires (Sec. 3.1.2)."""
+    return 1.0 / (1.0 + delta(graph, w))
+
+
+def normalized_weights(graph) -> np.ndarray:
+    """Entry weights of D^{-1/2} A D^{-1/2} (Section 5.4), one per CSR entry."""
+    n, rp, ci = _g(graph)
+    out = np.zeros(max(int(np.asarray(graph.col_idx).shape[0]), 1), dtype=np.float64)
+    _load().orc_normalized_weights(n, _ptr(rp, _i32p), _ptr(ci, _i32p), _ptr(out, _f64p))
+    return out[:int(np.asarray(graph.col_idx).shape[0])]
+
+
+def walk_totals(graph, alpha: float, L: int, w=None):
     """(t, Wa): t[r, x] = alpha^r omega_r(x) (Eq. katz-def terms), Wa[r] = alpha^r W_r."""
     n, rp, ci = _g(graph)
     t = np.zeros((L + 1, max(n, 1)), dtype=np.float64)
     Wa = np.zeros(L + 1, dtype=np.float64)
-    rc = _load().orc_walk_totals_d(n, _ptr(rp, _i32p), _ptr(ci, _i32p), alpha, L, _ptr(t, _f64p), _ptr(Wa, _f64p))
+    rc = _load().orc_walk_totals_d(n, _ptr(rp, _i32p), _ptr(ci, _i32p), _wp(graph, w), alpha, L, _ptr(t, _f64p), _ptr(Wa, _f64p))
     if rc != 0:
         raise MemoryError("oracle walk_totals failed")
     return t[:, :n], Wa
 
 
-def comb_bound(graph, alpha: float, Wa_l: float) -> float:
+def comb_bound(graph, alpha: float, Wa_l: float, w=None) -> float:
     """B_l of Eq. comb-bound from Wa_l = alpha^l W_l."""
-    return float(_load().orc_comb_bound_d(dmax(graph), alpha, Wa_l))
+    return float(_load().orc_comb_bound_d(delta(graph, w), alpha, Wa_l))
 
 
-def select_L(graph, alpha: float, eps: float, Lcap: int = 400):
+def select_L(graph, alpha: float, eps: float, Lcap: int = 400, w=None):
     """(L, B_L): smallest l >= 1 with B_l < eps (Algorithm 1 stop test). L = -1 if none."""
     n, rp, ci = _g(graph)
     B = ctypes.c_double(float("nan"))
-    L = _load().orc_select_L_d(n, _ptr(rp, _i32p), _ptr(ci, _i32p), alpha, eps, Lcap, ctypes.byref(B))
+    L = _load().orc_select_L_d(n, _ptr(rp, _i32p), _ptr(ci, _i32p), _wp(graph, w), alpha, eps, Lcap, ctypes.byref(B))
     return int(L), float(B.value)
 
 
-def score(graph, S, alpha: float, L: int, terms: bool = False, long_double: bool = False):
+def score(graph, S, alpha: float, L: int, terms: bool = False, long_double: bool = False, w=None):
     """GED_{<=L}(S) by the two-state recurrences (Sec. 3.1.1). terms=True also returns alpha^i phi_i."""
     n, rp, ci = _g(graph)
     s, sl = _S(S)
     lib = _load()
     if long_double:
-        return float(lib.orc_score_ld_as_d(n, _ptr(rp, _i32p), _ptr(ci, _i32p), _ptr(s, _i32p), sl, alpha, L))
+        return float(lib.orc_score_ld_as_d(n, _ptr(rp, _i32p), _ptr(ci, _i32p), _wp(graph, w), _ptr(s, _i32p), sl, alpha, L))
     tv = np.zeros(L + 1, dtype=np.float64)
-    val = float(lib.orc_score_d(n, _ptr(rp, _i32p), _ptr(ci, _i32p), _ptr(s, _i32p), sl, alpha, L, _ptr(tv, _f64p)))
+    val = float(lib.orc_score_d(n, _ptr(rp, _i32p), _ptr(ci, _i32p), _wp(graph, w), _ptr(s, _i32p), sl, alpha, L, _ptr(tv, _f64p)))
     return (val, tv) if terms else val
 
 
-def score_by_complement(graph, S, alpha: float, L: int) -> float:
+def score_by_complement(graph, S, alpha: float, L: int, w=None) -> float:
     """GED_{<=L}(S) as sum_i alpha^i (W_i - M_i) (Def. ged-walk; cancels for small S)."""
     n, rp, ci = _g(graph)
     s, sl = _S(S)
-    return float(_load().orc_score_by_complement_d(n, _ptr(rp, _i32p), _ptr(ci, _i32p), _ptr(s, _i32p), sl,
+    return float(_load().orc_score_by_complement_d(n, _ptr(rp, _i32p), _ptr(ci, _i32p), _wp(graph, w), _ptr(s, _i32p), sl,
                                                    alpha, L))
 
 
-def gain(graph, S, x: int, alpha: float, L: int, long_double: bool = False) -> float:
+def gain(graph, S, x: int, alpha: float, L: int, long_double: bool = False, w=None) -> float:
     """GED_{<=L}(S, x), counted directly as the weighted walks through x avoiding S."""
     n, rp, ci = _g(graph)
     s, sl = _S(S)
     lib = _load()
     f = lib.orc_gain_ld_as_d if long_double else lib.orc_gain_d
-    return float(f(n, _ptr(rp, _i32p), _ptr(ci, _i32p), _ptr(s, _i32p), sl, int(x), alpha, L))
+    return float(f(n, _ptr(rp, _i32p), _ptr(ci, _i32p), _wp(graph, w), _ptr(s, _i32p), sl, int(x), alpha, L))
 
 
-def upper_bounds(graph, S, alpha: float, L: int) -> np.ndarray:
+def upper_bounds(graph, S, alpha: float, L: int, w=None) -> np.ndarray:
     """sum_{i<=L} alpha^i P_i(S, x) for every x (Lemma initialize)."""
     n, rp, ci = _g(graph)
     s, sl = _S(S)
     ub = np.zeros(max(n, 1), dtype=np.float64)
-    _load().orc_upper_bounds_d(n, _ptr(rp, _i32p), _ptr(ci, _i32p), _ptr(s, _i32p), sl, alpha, L, _ptr(ub, _f64p))
+    _load().orc_upper_bounds_d(n, _ptr(rp, _i32p), _ptr(ci, _i32p), _wp(graph, w), _ptr(s, _i32p), sl, alpha, L, _ptr(ub, _f64p))
     return ub[:n]
 
 
-def greedy(graph, k: int, alpha: float, L: int, mode: str = "all", init=None):
+def greedy(graph, k: int, alpha: float, L: int, mode: str = "all", init=None, w=None):
     """Greedy maximisation at fixed L: (group, gains, evaluations). mode 'all' or 'lazy'."""
     n, rp, ci = _g(graph)
     ini, il = _S(init)
     group = np.zeros(max(k, 1), dtype=np.int32)
     gains = np.zeros(max(k, 1), dtype=np.float64)
     ev = ctypes.c_int64(0)
-    rc = _load().orc_greedy_d(n, _ptr(rp, _i32p), _ptr(ci, _i32p), k, alpha, L, 0 if mode == "all" else 1,
+    rc = _load().orc_greedy_d(n, _ptr(rp, _i32p), _ptr(ci, _i32p), _wp(graph, w), k, alpha, L, 0 if mode == "all" else 1,
                               _ptr(ini, _i32p), il, _ptr(group, _i32p), _ptr(gains, _f64p), ctypes.byref(ev))
     if rc != 0:
         raise ValueError("oracle greedy: invalid arguments")
@@ -202,20 +231,20 @@ def sample_hash(seed: int, step: int, v: int) -> int:
     return int(_load().orc_sample_hash(seed, step, v))
 
 
-def greedy_stochastic(graph, k: int, alpha: float, L: int, eta: float, seed: int):
+def greedy_stochastic(graph, k: int, alpha: float, L: int, eta: float, seed: int, w=None):
     """Stochastic greedy (Appendix D) at fixed L: (group, gains, evaluations)."""
     n, rp, ci = _g(graph)
     group = np.zeros(max(k, 1), dtype=np.int32)
     gains = np.zeros(max(k, 1), dtype=np.float64)
     ev = ctypes.c_int64(0)
-    rc = _load().orc_greedy_stochastic_d(n, _ptr(rp, _i32p), _ptr(ci, _i32p), k, alpha, L, eta, seed,
+    rc = _load().orc_greedy_stochastic_d(n, _ptr(rp, _i32p), _ptr(ci, _i32p), _wp(graph, w), k, alpha, L, eta, seed,
                                          _ptr(group, _i32p), _ptr(gains, _f64p), ctypes.byref(ev))
     if rc != 0:
         raise ValueError("oracle stochastic greedy: invalid arguments")
     return group[:k].copy(), gains[:k].copy(), int(ev.value)
 
 
-def greedy_adaptive(graph, k: int, alpha: float, eps_sep: float, lcap: int = 4096):
+def greedy_adaptive(graph, k: int, alpha: float, eps_sep: float, lcap: int = 4096, w=None):
     """Lazy greedy with l-doubling and eps_sep-separation (Algorithm 2).
 
     Returns a dict: group, gains (L_l(S, u) at each step's l), ell (each step's l), evals, and
@@ -233,7 +262,7 @@ def greedy_adaptive(graph, k: int, alpha: float, eps_sep: float, lcap: int = 409
     a_B = np.zeros(cap, dtype=np.float64)
     ev = ctypes.c_int64(0)
     na = ctypes.c_int32(0)
-    rc = _load().orc_greedy_adaptive_d(n, _ptr(rp, _i32p), _ptr(ci, _i32p), k, alpha, eps_sep, lcap,
+    rc = _load().orc_greedy_adaptive_d(n, _ptr(rp, _i32p), _ptr(ci, _i32p), _wp(graph, w), k, alpha, eps_sep, lcap,
                                        _ptr(group, _i32p), _ptr(gains, _f64p), _ptr(ell, _i32p), ctypes.byref(ev),
                                        cap, _ptr(a_step, _i32p), _ptr(a_ell, _i32p), _ptr(a_gu, _f64p),
                                        _ptr(a_gv, _f64p), _ptr(a_B, _f64p), ctypes.byref(na))

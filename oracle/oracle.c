@@ -11,8 +11,12 @@
  * The numeric routines live in oracle_impl.inc and are compiled twice: in
  * double (suffix _d) and in long double (suffix _ld).
  *
+ * Every routine takes optional CSR entry weights (Section 5.4's weighted walks;
+ * NULL for the unweighted graph).
+ *
  * Pins (see tests/test_oracle.py): brute-force walk enumeration on graphs of at
- * most 12 vertices, closed forms (complete graph, star, cycle, path),
+ * most 12 vertices (with exact rational weights too), closed forms (complete
+ * graph, star, cycle, path; regular graphs for the normalised weights),
  * Prop. katz-relation, monotonicity and submodularity (Prop. ged_submod), the
  * Lemma-initialize upper bound and its equality at L = 1, exhaustive best
  * groups for k <= 3, and double against long double.
@@ -21,6 +25,8 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+
+double orc_delta(int32_t n, const int32_t* rp, const double* w);
 
 #define REAL double
 #define ORC(name) orc_##name##_d
@@ -40,6 +46,35 @@ int32_t orc_dmax(int32_t n, const int32_t* rp) {
   for (int32_t v = 0; v < n; ++v)
     if (rp[v + 1] - rp[v] > d) d = rp[v + 1] - rp[v];
   return d;
+}
+
+/*
+ * The degree bound of Eq. comb-bound for a weighted graph: the largest weighted
+ * degree delta = max_v sum_u w(v,u), so that W_{l+1} <= delta W_l still holds (the
+ * row sums of the weighted adjacency bound the growth of every walk total). For
+ * w = NULL it is d_max.
+ */
+double orc_delta(int32_t n, const int32_t* rp, const double* w) {
+  if (!w) return (double)orc_dmax(n, rp);
+  double d = 0;
+  for (int32_t v = 0; v < n; ++v) {
+    double s = 0;
+    for (int32_t j = rp[v]; j < rp[v + 1]; ++j) s += w[j];
+    if (s > d) d = s;
+  }
+  return d;
+}
+
+/*
+ * Entry weights of the symmetrically normalised adjacency D^{-1/2} A D^{-1/2}
+ * (Section 5.4): w(v,u) = 1 / sqrt(deg(v) deg(u)). out receives nnz values.
+ */
+void orc_normalized_weights(int32_t n, const int32_t* rp, const int32_t* ci, double* out) {
+  for (int32_t v = 0; v < n; ++v)
+    for (int32_t j = rp[v]; j < rp[v + 1]; ++j) {
+      const int32_t u = ci[j];
+      out[j] = 1.0 / sqrt((double)(rp[v + 1] - rp[v]) * (double)(rp[u + 1] - rp[u]));
+    }
 }
 
 /*
@@ -120,12 +155,12 @@ uint64_t orc_sample_hash(uint64_t seed, uint32_t step, uint32_t v) {
 }
 
 /* long-double entry points exchange values as double for the ctypes wrapper */
-double orc_score_ld_as_d(int32_t n, const int32_t* rp, const int32_t* ci, const int32_t* S, int32_t s_len,
-                         double alpha, int32_t L) {
-  return (double)orc_score_ld(n, rp, ci, S, s_len, alpha, L, NULL);
+double orc_score_ld_as_d(int32_t n, const int32_t* rp, const int32_t* ci, const double* w, const int32_t* S,
+                         int32_t s_len, double alpha, int32_t L) {
+  return (double)orc_score_ld(n, rp, ci, w, S, s_len, alpha, L, NULL);
 }
 
-double orc_gain_ld_as_d(int32_t n, const int32_t* rp, const int32_t* ci, const int32_t* S, int32_t s_len, int32_t x,
-                        double alpha, int32_t L) {
-  return (double)orc_gain_ld(n, rp, ci, S, s_len, x, alpha, L);
+double orc_gain_ld_as_d(int32_t n, const int32_t* rp, const int32_t* ci, const double* w, const int32_t* S,
+                        int32_t s_len, int32_t x, double alpha, int32_t L) {
+  return (double)orc_gain_ld(n, rp, ci, w, S, s_len, x, alpha, L);
 }

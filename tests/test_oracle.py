@@ -520,3 +520,131 @@ def test_adaptive_greedy_rejects_bad_input():
         oracle.greedy_adaptive(g, 2, 0.3, 1e-3)  # alpha * d_max >= 1: no bound
     with pytest.raises(ValueError):
         oracle.greedy_adaptive(g, 2, 0.1, 1e-30, lcap=4)  # l would pass the cap
+
+
+# ---------------------------------------------------------------- weighted walks (Section 5.4)
+def _scaled_weights(g, scale):
+    """w(v, u) = scale[v] * scale[u] per CSR entry (input construction for the weighted tests)."""
+    rows = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
+    return np.asarray(scale, dtype=np.float64)[rows] * np.asarray(scale, dtype=np.float64)[g.col_idx]
+
+
+def _weighted_dense(g, w):
+    M = np.zeros((g.n, g.n))
+    rows = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
+    M[rows, g.col_idx] = w
+    return M
+
+
+def test_normalized_weights_are_sym_normalised_adjacency():
+    g = gg.erdos_renyi(40, 5, 3)
+    A = g.to_dense().astype(float)
+    d = A.sum(axis=1)
+    with np.errstate(divide="ignore"):
+        Dm = np.where(d > 0, 1.0 / np.sqrt(d), 0.0)
+    N = Dm[:, None] * A * Dm[None, :]
+    assert np.allclose(_weighted_dense(g, oracle.normalized_weights(g)), N, rtol=1e-15, atol=0)
+
+
+@pytest.mark.parametrize("g", [gg.cycle(7), gg.complete(6)], ids=["cycle7", "k6"])
+def test_weighted_regular_graph_rescales_alpha(g):
+    # On a d-regular graph D^{-1/2} A D^{-1/2} = A / d: every i-walk weighs d^{-i}, so the weighted
+    # objective at alpha is the unweighted one at alpha / d.
+    d = g.d_max
+    w = oracle.normalized_weights(g)
+    alpha, L = 0.3, 7
+    for S in ([0], [1, 3], [0, 2, 4]):
+        assert _rel(oracle.score(g, S, alpha, L, w=w), oracle.score(g, S, alpha / d, L)) < 1e-14
+        assert _rel(oracle.gain(g, S, 5, alpha, L, w=w), oracle.gain(g, S, 5, alpha / d, L)) < 1e-14
+    _, Wa_w = oracle.walk_totals(g, alpha, L, w=w)
+    _, Wa = oracle.walk_totals(g, alpha / d, L)
+    assert np.allclose(Wa_w, Wa, rtol=1e-14, atol=0)
+
+
+def _brute_weighted(g, S, wmat, i, x=None):
+    """Sum over i-walks (exhaustive) of the product of their edge weights: the walks that contain a
+    vertex of S, or (x given) the walks that avoid S and visit x."""
+    from fractions import Fraction
+
+    A = g.to_dense().astype(bool)
+    Sset = set(S)
+    tot = Fraction(0)
+    for walk in itertools.product(range(g.n), repeat=i + 1):
+        if not all(A[walk[j], walk[j + 1]] for j in range(i)):
+            continue
+        if x is None and not (Sset & set(walk)):
+            continue
+        if x is not None and (Sset & set(walk) or x not in walk):
+            continue
+        p = Fraction(1)
+        for j in range(i):
+            p *= wmat[walk[j]][walk[j + 1]]
+        tot += p
+    return tot
+
+
+@pytest.mark.parametrize("gi", range(4))
+def test_weighted_score_and_gain_match_brute_force(gi):
+    from fractions import Fraction
+
+    g = gg.random_graph_small(6 + gi % 2, 0.5, 30 + gi)
+    rng = np.random.default_rng(gi)
+    num = rng.integers(1, 9, size=g.n)
+    scale = [Fraction(int(a), 8) for a in num]  # rational scales keep the brute force exact
+    wmat = [[scale[v] * scale[u] for u in range(g.n)] for v in range(g.n)]
+    w = _scaled_weights(g, [float(s) for s in scale])
+    alpha = Fraction(1, 5)
+    S = [0, g.n - 1]
+    L = 4
+    val, terms = oracle.score(g, S, float(alpha), L, terms=True, w=w)
+    for i in range(1, L + 1):
+        want = float(alpha ** i * _brute_weighted(g, S, wmat, i))
+        assert abs(terms[i] - want) <= 1e-14 * max(want, 1e-300), i
+    x = 2
+    want = float(sum(alpha ** i * _brute_weighted(g, S, wmat, i, x) for i in range(1, L + 1)))
+    assert abs(oracle.gain(g, S, x, float(alpha), L, w=w) - want) <= 1e-14 * max(want, 1e-300)
+    # the complement form and the two-state form agree with weights as well
+    assert _rel(oracle.score_by_complement(g, S, float(alpha), L, w=w), val) < 1e-12
+
+
+def test_weighted_katz_relation_and_tail_bound():
+    # GED(V) = sum_i alpha^i 1^T N^i 1 (Prop. katz-relation with weights) by dense powers, and the
+    # weighted combinatorial bound with delta = max weighted degree covers the true tail.
+    g = gg.barabasi_albert(60, 3, 5)
+    w = oracle.normalized_weights(g)
+    N = _weighted_dense(g, w)
+    delta = N.sum(axis=1).max()
+    assert abs(oracle.delta(g, w) - delta) <= 1e-14 * delta
+    alpha = 0.9 / delta
+    one = np.ones(g.n)
+    Ls = 12
+    katz, v = [], one.copy()
+    for i in range(1, 400):
+        v = N @ v
+        katz.append(alpha ** i * v.sum())
+    assert _rel(oracle.score(g, list(range(g.n)), alpha, Ls, w=w), sum(katz[:Ls])) < 1e-12
+    _, Wa = oracle.walk_totals(g, alpha, Ls, w=w)
+    for l in range(1, Ls):
+        assert sum(katz[l:]) <= oracle.comb_bound(g, alpha, Wa[l], w=w) * (1 + 1e-12)
+    L, B = oracle.select_L(g, alpha, 1e-3, w=w)
+    assert B < 1e-3 and oracle.comb_bound(g, alpha, Wa[L - 1], w=w) >= 1e-3
+
+
+def test_weighted_bounds_submodularity_and_greedy():
+    g = gg.erdos_renyi(60, 5, 8)
+    w = oracle.normalized_weights(g)
+    alpha = oracle.default_alpha(g, w)
+    L = 6
+    S = [1, 7, 20]
+    ub = oracle.upper_bounds(g, S, alpha, L, w=w)
+    ub1 = oracle.upper_bounds(g, S, alpha, 1, w=w)
+    for x in range(0, g.n, 3):
+        gx = oracle.gain(g, S, x, alpha, L, w=w)
+        assert gx <= ub[x] * (1 + 1e-12)
+        assert abs(oracle.gain(g, S, x, alpha, 1, w=w) - ub1[x]) <= 1e-15  # Lemma initialize, L = 1
+        assert gx <= oracle.gain(g, S[:1], x, alpha, L, w=w) * (1 + 1e-12) or x in S  # submodular
+    grp_a, gains_a, _ = oracle.greedy(g, 5, alpha, L, "all", w=w)
+    grp_l, gains_l, _ = oracle.greedy(g, 5, alpha, L, "lazy", w=w)
+    assert list(grp_a) == list(grp_l) and np.allclose(gains_a, gains_l, rtol=1e-12)
+    r = oracle.greedy_adaptive(g, 3, alpha, 1e-4, w=w)
+    assert r["group"][0] == grp_a[0]
