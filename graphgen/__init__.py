@@ -59,6 +59,11 @@ def _load():
             lib.gg_rmat.restype = P(_CSR)
             lib.gg_rmat.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                                     ctypes.c_double, ctypes.c_uint64, ctypes.c_int32]
+            lib.gg_rmat_ex.restype = P(_CSR)
+            lib.gg_rmat_ex.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32]
+            lib.gg_from_arcs.restype = P(_CSR)
+            lib.gg_from_arcs.argtypes = [ctypes.c_int32, ctypes.c_int64, P(ctypes.c_int32), P(ctypes.c_int32)]
             lib.gg_from_edges.restype = P(_CSR)
             lib.gg_from_edges.argtypes = [ctypes.c_int32, ctypes.c_int64, P(ctypes.c_int32), P(ctypes.c_int32)]
             lib.gg_free.restype = None
@@ -123,9 +128,10 @@ def barabasi_albert(n: int, m: int, seed: int) -> Graph:
 
 
 def rmat(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.19, c: float = 0.19,
-         seed: int = 1, permute: bool = True) -> Graph:
-    return _take(_load().gg_rmat(scale, edge_factor, a, b, c, seed, int(permute)),
-                 f"rmat(scale={scale},ef={edge_factor},seed={seed})")
+         seed: int = 1, permute: bool = True, directed: bool = False) -> Graph:
+    """R-MAT; directed keeps the tuples as arcs (successor-list CSR) instead of symmetrising."""
+    return _take(_load().gg_rmat_ex(scale, edge_factor, a, b, c, seed, int(permute), int(directed)),
+                 f"rmat(scale={scale},ef={edge_factor},seed={seed}{',directed' if directed else ''})")
 
 
 def from_edges(n: int, edges) -> Graph:
@@ -136,6 +142,27 @@ def from_edges(n: int, edges) -> Graph:
     P = ctypes.POINTER(ctypes.c_int32)
     return _take(_load().gg_from_edges(n, e.shape[0], src.ctypes.data_as(P), dst.ctypes.data_as(P)),
                  f"edges(n={n},m={e.shape[0]})")
+
+
+def from_arcs(n: int, arcs) -> Graph:
+    """Directed CSR of successor lists (row u: the v with u -> v); duplicates and self-loops dropped."""
+    e = np.asarray(arcs, dtype=np.int32).reshape(-1, 2)
+    src = np.ascontiguousarray(e[:, 0])
+    dst = np.ascontiguousarray(e[:, 1])
+    P = ctypes.POINTER(ctypes.c_int32)
+    return _take(_load().gg_from_arcs(n, e.shape[0], src.ctypes.data_as(P), dst.ctypes.data_as(P)),
+                 f"arcs(n={n},m={e.shape[0]})")
+
+
+def random_digraph(n: int, p: float, seed: int) -> Graph:
+    """Directed G(n, p): every ordered pair (u, v), u != v, is an arc with probability p (numpy RNG)."""
+    rng = np.random.default_rng(seed)
+    a = rng.random((n, n)) < p
+    np.fill_diagonal(a, False)
+    u, v = np.nonzero(a)
+    if u.size == 0:
+        return Graph(np.zeros(n + 1, np.int32), np.zeros(0, np.int32))
+    return from_arcs(n, np.stack([u, v], axis=1))
 
 
 def complete(n: int) -> Graph:

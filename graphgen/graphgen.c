@@ -188,6 +188,65 @@ gg_csr* gg_from_edges(int32_t n, int64_t m, const int32_t* src, const int32_t* d
 }
 
 /*
+ * Directed arc list (m tuples u -> v) -> CSR of successor lists: row u holds the v with an arc
+ * u -> v, sorted; repeated arcs collapse to one; self-loops are dropped.
+ */
+gg_csr* gg_from_arcs(int32_t n, int64_t m, const int32_t* src, const int32_t* dst) {
+  if (n < 0 || m < 0) return NULL;
+  gg_csr* g = (gg_csr*)calloc(1, sizeof(gg_csr));
+  if (!g) return NULL;
+  g->n = n;
+  int64_t* cnt = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+  if (!cnt) {
+    free(g);
+    return NULL;
+  }
+  for (int64_t e = 0; e < m; ++e) {
+    const int32_t u = src[e], v = dst[e];
+    if (u < 0 || v < 0 || u >= n || v >= n) {
+      free(cnt);
+      free(g);
+      return NULL;
+    }
+    if (u != v) cnt[u + 1]++;
+  }
+  for (int32_t i = 0; i < n; ++i) cnt[i + 1] += cnt[i];
+  const int64_t total = cnt[n];
+  int32_t* tmp = (int32_t*)malloc((size_t)(total > 0 ? total : 1) * sizeof(int32_t));
+  int64_t* pos = (int64_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+  g->row_ptr = (int32_t*)malloc(((size_t)n + 1) * sizeof(int32_t));
+  if (!tmp || !pos || !g->row_ptr) {
+    free(tmp);
+    free(pos);
+    free(cnt);
+    free(g->row_ptr);
+    free(g);
+    return NULL;
+  }
+  memcpy(pos, cnt, (size_t)n * sizeof(int64_t));
+  for (int64_t e = 0; e < m; ++e)
+    if (src[e] != dst[e]) tmp[pos[src[e]]++] = dst[e];
+  free(pos);
+  int64_t w = 0;
+  g->row_ptr[0] = 0;
+  for (int32_t i = 0; i < n; ++i) {
+    int32_t* row = tmp + cnt[i];
+    const int64_t len = cnt[i + 1] - cnt[i];
+    sort_small(row, len);
+    for (int64_t j = 0; j < len; ++j) {
+      if (j > 0 && row[j] == row[j - 1]) continue;
+      tmp[w++] = row[j];
+    }
+    g->row_ptr[i + 1] = (int32_t)w;
+  }
+  free(cnt);
+  g->nnz = w;
+  g->col_idx = (int32_t*)realloc(tmp, (size_t)(w > 0 ? w : 1) * sizeof(int32_t));
+  if (!g->col_idx) g->col_idx = tmp;
+  return g;
+}
+
+/*
  * Erdos-Renyi G(n, p), undirected. Small graphs (n <= 4096) test every pair
  * against an integer threshold, so the graph is identical on every platform.
  * Larger graphs use geometric skipping over the pair sequence (Batagelj &
@@ -315,9 +374,10 @@ gg_csr* gg_ba(int32_t n, int32_t m, uint64_t seed) {
  * partition with probabilities (a, b, c, 1-a-b-c). Vertex labels are then
  * shuffled by a uniform random permutation when `permute` is set (as the
  * Graph 500 generator does), and the result is symmetrised with duplicates and
- * self-loops removed.
+ * self-loops removed (directed: the tuples are kept as arcs u -> v instead).
  */
-gg_csr* gg_rmat(int32_t scale, int32_t ef, double a, double b, double c, uint64_t seed, int32_t permute) {
+gg_csr* gg_rmat_ex(int32_t scale, int32_t ef, double a, double b, double c, uint64_t seed, int32_t permute,
+                   int32_t directed) {
   if (scale < 1 || scale > 30 || ef < 1 || a < 0 || b < 0 || c < 0 || a + b + c > 1.0) return NULL;
   const int32_t n = (int32_t)1 << scale;
   const int64_t m = (int64_t)ef * n;
@@ -378,8 +438,12 @@ gg_csr* gg_rmat(int32_t scale, int32_t ef, double a, double b, double c, uint64_
     }
     free(perm);
   }
-  gg_csr* g = gg_from_edges(n, m, su, sv);
+  gg_csr* g = directed ? gg_from_arcs(n, m, su, sv) : gg_from_edges(n, m, su, sv);
   free(su);
   free(sv);
   return g;
+}
+
+gg_csr* gg_rmat(int32_t scale, int32_t ef, double a, double b, double c, uint64_t seed, int32_t permute) {
+  return gg_rmat_ex(scale, ef, a, b, c, seed, permute, 0);
 }

@@ -57,11 +57,15 @@ def _load():
             lib.orc_walk_totals_d.restype = ctypes.c_int
             lib.orc_walk_totals_d.argtypes = GW + [ctypes.c_double, ctypes.c_int32, _f64p, _f64p]
             lib.orc_select_L_d.restype = ctypes.c_int32
-            lib.orc_select_L_d.argtypes = GW + [ctypes.c_double, ctypes.c_double, ctypes.c_int32, _f64p]
+            lib.orc_select_L_d.argtypes = GW + [_i32p, _f64p, ctypes.c_double, ctypes.c_double, ctypes.c_int32, _f64p]
             lib.orc_comb_bound_d.restype = ctypes.c_double
             lib.orc_comb_bound_d.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
             lib.orc_delta.restype = ctypes.c_double
             lib.orc_delta.argtypes = [ctypes.c_int32, _i32p, _f64p]
+            lib.orc_delta2.restype = ctypes.c_double
+            lib.orc_delta2.argtypes = [ctypes.c_int32, _i32p, _f64p, _i32p, _f64p]
+            lib.orc_transpose.restype = None
+            lib.orc_transpose.argtypes = G + [_f64p, _i32p, _i32p, _f64p]
             lib.orc_normalized_weights.restype = None
             lib.orc_normalized_weights.argtypes = G + [_f64p]
             lib.orc_score_d.restype = ctypes.c_double
@@ -76,15 +80,16 @@ def _load():
             lib.orc_gain_ld_as_d.argtypes = GW + [_i32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                                  ctypes.c_int32]
             lib.orc_upper_bounds_d.restype = ctypes.c_int
-            lib.orc_upper_bounds_d.argtypes = GW + [_i32p, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, _f64p]
+            lib.orc_upper_bounds_d.argtypes = GW + [_i32p, _i32p, _f64p, _i32p, ctypes.c_int32, ctypes.c_double,
+                                                   ctypes.c_int32, _f64p]
             lib.orc_greedy_d.restype = ctypes.c_int
-            lib.orc_greedy_d.argtypes = GW + [ctypes.c_int32, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
+            lib.orc_greedy_d.argtypes = GW + [_i32p, _i32p, _f64p, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
                                              _i32p, ctypes.c_int32, _i32p, _f64p, _i64p]
             lib.orc_greedy_stochastic_d.restype = ctypes.c_int
             lib.orc_greedy_stochastic_d.argtypes = GW + [ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
                                                         ctypes.c_double, ctypes.c_uint64, _i32p, _f64p, _i64p]
             lib.orc_greedy_adaptive_d.restype = ctypes.c_int
-            lib.orc_greedy_adaptive_d.argtypes = GW + [ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+            lib.orc_greedy_adaptive_d.argtypes = GW + [_i32p, _i32p, _f64p, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                                                       ctypes.c_int32, _i32p, _f64p, _i32p, _i64p, ctypes.c_int32,
                                                       _i32p, _i32p, _f64p, _f64p, _f64p, _i32p]
             lib.orc_sample_hash.restype = ctypes.c_uint64
@@ -131,15 +136,39 @@ def dmax(graph) -> int:
     return int(_load().orc_dmax(n, _ptr(rp, _i32p)))
 
 
-def delta(graph, w=None) -> float:
-    """The degree bound of Eq. comb-bound: d_max, or the largest weighted degree with weights."""
+def transpose(graph, w=None):
+    """(row_ptr, col_idx, weights or None) of the transposed CSR (the reverse graph)."""
+    n, rp, ci = _g(graph)
+    nnz = int(np.asarray(graph.col_idx).shape[0])
+    rpt = np.zeros(n + 1, dtype=np.int32)
+    cit = np.zeros(max(nnz, 1), dtype=np.int32)
+    wt = np.zeros(max(nnz, 1), dtype=np.float64) if w is not None else None
+    _load().orc_transpose(n, _ptr(rp, _i32p), _ptr(ci, _i32p), _wp(graph, w), _ptr(rpt, _i32p), _ptr(cit, _i32p),
+                          None if wt is None else _ptr(wt, _f64p))
+    return rpt, cit[:nnz], (None if wt is None else wt[:nnz])
+
+
+def _tp(graph, w, directed):
+    """Pointers to the transposed CSR for a directed graph (psi of Lemma initialize), else NULLs."""
+    if not directed:
+        return None, None, None
+    rpt, cit, wt = transpose(graph, w)
+    if cit.size == 0:
+        cit = np.zeros(1, dtype=np.int32)
+    return _ptr(rpt, _i32p), _ptr(cit, _i32p), (None if wt is None else _ptr(wt, _f64p))
+
+
+def delta(graph, w=None, directed: bool = False) -> float:
+    """The degree bound of Eq. comb-bound: d_max (min of the largest in- and out-degree for a
+    directed graph), or the largest weighted degree with weights."""
     n, rp, _ = _g(graph)
-    return float(_load().orc_delta(n, _ptr(rp, _i32p), _wp(graph, w)))
+    rpt, _, wt = _tp(graph, w, directed)
+    return float(_load().orc_delta2(n, _ptr(rp, _i32p), _wp(graph, w), rpt, wt))
 
 
-def default_alpha(graph, w=None) -> float:
+def default_alpha(graph, w=None, directed: bool = False) -> float:
     """alpha = 1/(1 + delta): below 1/delta, as the combinatorial bound requires (Sec. 3.1.2)."""
-    return 1.0 / (1.0 + delta(graph, w))
+    return 1.0 / (1.0 + delta(graph, w, directed))
 
 
 def normalized_weights(graph) -> np.ndarray:
@@ -161,16 +190,18 @@ def walk_totals(graph, alpha: float, L: int, w=None):
     return t[:, :n], Wa
 
 
-def comb_bound(graph, alpha: float, Wa_l: float, w=None) -> float:
+def comb_bound(graph, alpha: float, Wa_l: float, w=None, directed: bool = False) -> float:
     """B_l of Eq. comb-bound from Wa_l = alpha^l W_l."""
-    return float(_load().orc_comb_bound_d(delta(graph, w), alpha, Wa_l))
+    return float(_load().orc_comb_bound_d(delta(graph, w, directed), alpha, Wa_l))
 
 
-def select_L(graph, alpha: float, eps: float, Lcap: int = 400, w=None):
+def select_L(graph, alpha: float, eps: float, Lcap: int = 400, w=None, directed: bool = False):
     """(L, B_L): smallest l >= 1 with B_l < eps (Algorithm 1 stop test). L = -1 if none."""
     n, rp, ci = _g(graph)
     B = ctypes.c_double(float("nan"))
-    L = _load().orc_select_L_d(n, _ptr(rp, _i32p), _ptr(ci, _i32p), _wp(graph, w), alpha, eps, Lcap, ctypes.byref(B))
+    rpt, _, wt = _tp(graph, w, directed)
+    L = _load().orc_select_L_d(n, _ptr(rp, _i32p), _ptr(ci, _i32p), _wp(graph, w), rpt, wt, alpha, eps, Lcap,
+                               ctypes.byref(B))
     return int(L), float(B.value)
 
 
@@ -203,23 +234,27 @@ def gain(graph, S, x: int, alpha: float, L: int, long_double: bool = False, w=No
     return float(f(n, _ptr(rp, _i32p), _ptr(ci, _i32p), _wp(graph, w), _ptr(s, _i32p), sl, int(x), alpha, L))
 
 
-def upper_bounds(graph, S, alpha: float, L: int, w=None) -> np.ndarray:
+def upper_bounds(graph, S, alpha: float, L: int, w=None, directed: bool = False) -> np.ndarray:
     """sum_{i<=L} alpha^i P_i(S, x) for every x (Lemma initialize)."""
     n, rp, ci = _g(graph)
     s, sl = _S(S)
     ub = np.zeros(max(n, 1), dtype=np.float64)
-    _load().orc_upper_bounds_d(n, _ptr(rp, _i32p), _ptr(ci, _i32p), _wp(graph, w), _ptr(s, _i32p), sl, alpha, L, _ptr(ub, _f64p))
+    rpt, cit, wt = _tp(graph, w, directed)
+    _load().orc_upper_bounds_d(n, _ptr(rp, _i32p), _ptr(ci, _i32p), _wp(graph, w), rpt, cit, wt, _ptr(s, _i32p), sl,
+                               alpha, L, _ptr(ub, _f64p))
     return ub[:n]
 
 
-def greedy(graph, k: int, alpha: float, L: int, mode: str = "all", init=None, w=None):
+def greedy(graph, k: int, alpha: float, L: int, mode: str = "all", init=None, w=None, directed: bool = False):
     """Greedy maximisation at fixed L: (group, gains, evaluations). mode 'all' or 'lazy'."""
     n, rp, ci = _g(graph)
     ini, il = _S(init)
     group = np.zeros(max(k, 1), dtype=np.int32)
     gains = np.zeros(max(k, 1), dtype=np.float64)
     ev = ctypes.c_int64(0)
-    rc = _load().orc_greedy_d(n, _ptr(rp, _i32p), _ptr(ci, _i32p), _wp(graph, w), k, alpha, L, 0 if mode == "all" else 1,
+    rpt, cit, wt = _tp(graph, w, directed)
+    rc = _load().orc_greedy_d(n, _ptr(rp, _i32p), _ptr(ci, _i32p), _wp(graph, w), rpt, cit, wt, k, alpha, L,
+                              0 if mode == "all" else 1,
                               _ptr(ini, _i32p), il, _ptr(group, _i32p), _ptr(gains, _f64p), ctypes.byref(ev))
     if rc != 0:
         raise ValueError("oracle greedy: invalid arguments")
@@ -244,7 +279,7 @@ def greedy_stochastic(graph, k: int, alpha: float, L: int, eta: float, seed: int
     return group[:k].copy(), gains[:k].copy(), int(ev.value)
 
 
-def greedy_adaptive(graph, k: int, alpha: float, eps_sep: float, lcap: int = 4096, w=None):
+def greedy_adaptive(graph, k: int, alpha: float, eps_sep: float, lcap: int = 4096, w=None, directed: bool = False):
     """Lazy greedy with l-doubling and eps_sep-separation (Algorithm 2).
 
     Returns a dict: group, gains (L_l(S, u) at each step's l), ell (each step's l), evals, and
@@ -262,7 +297,9 @@ def greedy_adaptive(graph, k: int, alpha: float, eps_sep: float, lcap: int = 409
     a_B = np.zeros(cap, dtype=np.float64)
     ev = ctypes.c_int64(0)
     na = ctypes.c_int32(0)
-    rc = _load().orc_greedy_adaptive_d(n, _ptr(rp, _i32p), _ptr(ci, _i32p), _wp(graph, w), k, alpha, eps_sep, lcap,
+    rpt, cit, wt = _tp(graph, w, directed)
+    rc = _load().orc_greedy_adaptive_d(n, _ptr(rp, _i32p), _ptr(ci, _i32p), _wp(graph, w), rpt, cit, wt, k, alpha,
+                                       eps_sep, lcap,
                                        _ptr(group, _i32p), _ptr(gains, _f64p), _ptr(ell, _i32p), ctypes.byref(ev),
                                        cap, _ptr(a_step, _i32p), _ptr(a_ell, _i32p), _ptr(a_gu, _f64p),
                                        _ptr(a_gv, _f64p), _ptr(a_B, _f64p), ctypes.byref(na))

@@ -27,6 +27,7 @@
 #include <string.h>
 
 double orc_delta(int32_t n, const int32_t* rp, const double* w);
+double orc_delta2(int32_t n, const int32_t* rp, const double* w, const int32_t* rpt, const double* wt);
 
 #define REAL double
 #define ORC(name) orc_##name##_d
@@ -63,6 +64,40 @@ double orc_delta(int32_t n, const int32_t* rp, const double* w) {
     if (s > d) d = s;
   }
   return d;
+}
+
+/*
+ * For a directed graph (rpt/wt: the transposed CSR) the walk totals grow at most by the largest
+ * row sum of either orientation: an l-walk extends at its end along at most d_out arcs and at its
+ * start along at most d_in arcs, so W_{l+1} <= min(d_out, d_in) W_l. rpt = NULL: undirected.
+ */
+double orc_delta2(int32_t n, const int32_t* rp, const double* w, const int32_t* rpt, const double* wt) {
+  const double a = orc_delta(n, rp, w);
+  if (!rpt) return a;
+  const double b = orc_delta(n, rpt, wt);
+  return a < b ? a : b;
+}
+
+/*
+ * Transpose of a CSR (row v of the result lists the u with v in row u), rows sorted, entry
+ * weights carried along when w is given. rpt[n+1], cit[nnz], wt[nnz] (wt may be NULL).
+ */
+void orc_transpose(int32_t n, const int32_t* rp, const int32_t* ci, const double* w, int32_t* rpt, int32_t* cit,
+                   double* wt) {
+  for (int32_t v = 0; v <= n; ++v) rpt[v] = 0;
+  for (int32_t u = 0; u < n; ++u)
+    for (int32_t j = rp[u]; j < rp[u + 1]; ++j) rpt[ci[j] + 1]++;
+  for (int32_t v = 0; v < n; ++v) rpt[v + 1] += rpt[v];
+  int32_t* fill = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+  if (!fill) return;
+  for (int32_t v = 0; v < n; ++v) fill[v] = rpt[v];
+  for (int32_t u = 0; u < n; ++u) /* rows u in increasing order: every transposed row comes out sorted */
+    for (int32_t j = rp[u]; j < rp[u + 1]; ++j) {
+      const int32_t p = fill[ci[j]]++;
+      cit[p] = u;
+      if (wt) wt[p] = w[j];
+    }
+  free(fill);
 }
 
 /*

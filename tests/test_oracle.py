@@ -648,3 +648,104 @@ def test_weighted_bounds_submodularity_and_greedy():
     assert list(grp_a) == list(grp_l) and np.allclose(gains_a, gains_l, rtol=1e-12)
     r = oracle.greedy_adaptive(g, 3, alpha, 1e-4, w=w)
     assert r["group"][0] == grp_a[0]
+
+
+# ---------------------------------------------------------------- directed graphs (Section 2; Lemma initialize's psi)
+def _digraph(seed, n=7, p=0.35):
+    return gg.random_digraph(n, p, seed)
+
+
+def _transposed_graph(g):
+    rpt, cit, _ = oracle.transpose(g)
+    return gg.Graph(rpt, cit)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_directed_score_and_gain_match_brute_force(seed):
+    # the CSR rows are successor lists; the brute force follows them, so both count directed walks
+    g = _digraph(seed)
+    alpha = 0.2
+    S = [0, 3]
+    val, terms = oracle.score(g, S, alpha, 5, terms=True)
+    for i in range(1, 6):
+        phi, _ = oracle.brute_phi(g, S, i)
+        assert abs(terms[i] - alpha ** i * phi) <= 1e-14 * max(terms[i], 1e-300)
+    for x in (1, 4, 6):
+        want = sum(alpha ** i * oracle.brute_gain(g, S, x, i) for i in range(1, 6))
+        assert abs(oracle.gain(g, S, x, alpha, 5) - want) <= 1e-14 * max(want, 1e-300)
+    # reversing every walk is a bijection that keeps its vertex set: GED is the same on the reverse graph
+    gt = _transposed_graph(g)
+    assert _rel(oracle.score(gt, S, alpha, 5), val) < 1e-14
+
+
+def _brute_psi_phi(g, S, x, i):
+    """(S-avoiding i-walks ending at x, S-avoiding i-walks starting at x), by enumeration."""
+    A = g.to_dense().astype(bool)
+    end = start = 0
+    for walk in itertools.product(range(g.n), repeat=i + 1):
+        if any(v in S for v in walk) or not all(A[walk[j], walk[j + 1]] for j in range(i)):
+            continue
+        end += walk[-1] == x
+        start += walk[0] == x
+    return end, start
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_directed_upper_bound_uses_walks_from_and_to_x(seed):
+    # Lemma initialize on a digraph: P_i = sum_j phi^miss_{i-j}(x) psi^miss_j(x), phi ending at x and
+    # psi starting at x. Built here from enumerated counts; the oracle must take psi from the reverse.
+    g = _digraph(10 + seed)
+    alpha, L = 0.25, 4
+    S = [2]
+    ub = oracle.upper_bounds(g, S, alpha, L, directed=True)
+    for x in range(g.n):
+        if x in S:
+            assert ub[x] == 0.0
+            continue
+        cnt = [_brute_psi_phi(g, S, x, i) for i in range(L + 1)]
+        want = sum(alpha ** i * sum(cnt[i - j][1] * cnt[j][0] for j in range(i + 1)) for i in range(1, L + 1))
+        # orientation: the oracle's rows are successor lists, so its phi^miss counts walks that
+        # start at x and psi those that end there; the product is symmetric in the two
+        assert abs(ub[x] - want) <= 1e-13 * max(want, 1e-300), x
+        gain = oracle.gain(g, S, x, alpha, L)
+        assert gain <= ub[x] * (1 + 1e-12)
+    ub1 = oracle.upper_bounds(g, S, alpha, 1, directed=True)
+    for x in range(g.n):
+        assert abs(oracle.gain(g, S, x, alpha, 1) - ub1[x]) <= 1e-15  # P_1 is exact without self-loops
+
+
+def test_directed_greedy_all_equals_lazy_and_adaptive_separates():
+    g = gg.rmat(8, 8, seed=5, directed=True)
+    alpha = oracle.default_alpha(g, directed=True)
+    L = 6
+    a, ga, _ = oracle.greedy(g, 6, alpha, L, "all")
+    b, gb, _ = oracle.greedy(g, 6, alpha, L, "lazy", directed=True)
+    assert list(a) == list(b) and np.allclose(ga, gb, rtol=1e-12)
+    k, eps = 4, 1e-3
+    r = oracle.greedy_adaptive(g, k, alpha, eps / k, directed=True)
+    for j in range(k):
+        S = list(r["group"][:j])
+        gv = _all_gains(g, S, alpha, int(r["ell"][j]))
+        u, v = _top2(gv)
+        assert abs(gv[r["group"][j]] - gv[u]) <= 1e-12 * gv[u]
+        assert gv[u] > gv[v] + oracle.comb_bound(g, alpha, oracle.walk_totals(g, alpha, int(r["ell"][j]))[1][-1],
+                                                  directed=True) - eps / k - 1e-12 * gv[u]
+
+
+def test_directed_delta_and_tail_bound():
+    # out-star: the centre has out-degree n-1 but every in-degree is <= 1, so walks cannot grow
+    g = gg.from_arcs(6, [(0, v) for v in range(1, 6)])
+    assert oracle.delta(g, directed=True) == 1.0 and oracle.delta(g) == 5.0
+    # random digraph: the bound with delta = min(max in, max out) covers the true tail (dense powers)
+    g = gg.rmat(7, 8, seed=9, directed=True)
+    A = g.to_dense().astype(float)
+    d = min(A.sum(axis=0).max(), A.sum(axis=1).max())
+    assert oracle.delta(g, directed=True) == d
+    alpha = 0.95 / d
+    terms, v = [], np.ones(g.n)
+    for i in range(1, 600):
+        v = alpha * (A @ v)  # alpha-scaled, so that nothing overflows
+        terms.append(v.sum())
+    _, Wa = oracle.walk_totals(g, alpha, 10)
+    for l in range(1, 10):
+        assert sum(terms[l:]) <= oracle.comb_bound(g, alpha, Wa[l], directed=True) * (1 + 1e-12)
