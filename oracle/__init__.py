@@ -60,6 +60,11 @@ def _load():
             lib.orc_select_L_d.argtypes = GW + [_i32p, _f64p, ctypes.c_double, ctypes.c_double, ctypes.c_int32, _f64p]
             lib.orc_comb_bound_d.restype = ctypes.c_double
             lib.orc_comb_bound_d.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
+            lib.orc_spectral_bound_d.restype = ctypes.c_double
+            lib.orc_spectral_bound_d.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+            lib.orc_select_L_spectral_d.restype = ctypes.c_int32
+            lib.orc_select_L_spectral_d.argtypes = GW + [ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                                         ctypes.c_int32, _f64p]
             lib.orc_delta.restype = ctypes.c_double
             lib.orc_delta.argtypes = [ctypes.c_int32, _i32p, _f64p]
             lib.orc_delta2.restype = ctypes.c_double
@@ -202,6 +207,21 @@ def select_L(graph, alpha: float, eps: float, Lcap: int = 400, w=None, directed:
     rpt, _, wt = _tp(graph, w, directed)
     L = _load().orc_select_L_d(n, _ptr(rp, _i32p), _ptr(ci, _i32p), _wp(graph, w), rpt, wt, alpha, eps, Lcap,
                                ctypes.byref(B))
+    return int(L), float(B.value)
+
+
+def spectral_bound(graph, alpha: float, Wa_l: float, sigma: float) -> float:
+    """B_l of Lemma spectral-bound from Wa_l = alpha^l W_l and sigma >= sigma_max."""
+    n = int(np.asarray(graph.row_ptr).shape[0] - 1)
+    return float(_load().orc_spectral_bound_d(n, sigma, alpha, Wa_l))
+
+
+def select_L_spectral(graph, alpha: float, eps: float, sigma: float, Lcap: int = 4000, w=None):
+    """(L, B_L) of Algorithm 1's stop test with the spectral bound. L = -1 if none."""
+    n, rp, ci = _g(graph)
+    B = ctypes.c_double(float("nan"))
+    L = _load().orc_select_L_spectral_d(n, _ptr(rp, _i32p), _ptr(ci, _i32p), _wp(graph, w), sigma, alpha, eps, Lcap,
+                                        ctypes.byref(B))
     return int(L), float(B.value)
 
 

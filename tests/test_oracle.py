@@ -749,3 +749,37 @@ def test_directed_delta_and_tail_bound():
     _, Wa = oracle.walk_totals(g, alpha, 10)
     for l in range(1, 10):
         assert sum(terms[l:]) <= oracle.comb_bound(g, alpha, Wa[l], directed=True) * (1 + 1e-12)
+
+
+# ---------------------------------------------------------------- spectral bound (Lemma spectral-bound, Appendix E)
+@pytest.mark.parametrize("kind", ["ba", "er", "digraph"])
+def test_spectral_bound_covers_the_tail_up_to_one_over_sigma(kind):
+    # sigma_max from a dense SVD; alpha = delta / sigma_max up to 0.9, beyond the reach of the
+    # combinatorial bound (alpha < 1/d_max) on these graphs
+    g = {"ba": lambda: gg.barabasi_albert(80, 3, 2), "er": lambda: gg.erdos_renyi(70, 6, 4),
+         "digraph": lambda: gg.rmat(6, 6, seed=2, directed=True)}[kind]()
+    A = g.to_dense().astype(float)
+    sigma = np.linalg.norm(A, 2)
+    assert sigma <= oracle.dmax(g)
+    for delta in (0.3, 0.6, 0.9):
+        alpha = delta / sigma
+        terms, v = [], np.ones(g.n)
+        for i in range(1, 3000):
+            v = alpha * (A @ v)
+            terms.append(v.sum())
+        _, Wa = oracle.walk_totals(g, alpha, 30)
+        for l in range(1, 30):
+            assert sum(terms[l:]) <= oracle.spectral_bound(g, alpha, Wa[l], sigma) * (1 + 1e-12)
+        L, B = oracle.select_L_spectral(g, alpha, 1e-4, sigma)
+        _, WaL = oracle.walk_totals(g, alpha, L)
+        assert B < 1e-4 and oracle.spectral_bound(g, alpha, WaL[L - 1], sigma) >= 1e-4 and sum(terms[L:]) < 1e-4
+
+
+def test_spectral_bound_on_regular_graph_is_sqrt_n_times_combinatorial():
+    # d-regular: sigma_max = d, so the two bounds differ exactly by the factor sqrt(|V|)
+    g = gg.cycle(9)
+    alpha = 0.2
+    _, Wa = oracle.walk_totals(g, alpha, 6)
+    for l in range(1, 7):
+        assert _rel(oracle.spectral_bound(g, alpha, Wa[l], 2.0), 3.0 * oracle.comb_bound(g, alpha, Wa[l])) < 1e-15
+    assert oracle.select_L_spectral(g, 0.6, 1e-3, 2.0)[0] == -1  # alpha * sigma >= 1: no bound
