@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rmat", choices=["rmat", "rmat_s", "ba", "ba64", "batch", "serve", "small"])
+    ap.add_argument("--workload", default="rmat", choices=["rmat", "rmat_s", "rmat_a", "rmat_w", "ba", "ba64", "batch", "serve", "small"])
     ap.add_argument("--scale", type=int, default=22, help="R-MAT scale (22 is the configured size)")
     ap.add_argument("--k", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -57,6 +57,14 @@ def workload_spec(args):
         return dict(name=f"R-MAT scale {args.scale}, edge factor 16, stochastic greedy (eta=0.1) k={args.k} FP32",
                     kind="greedy", graph=("rmat", args.scale), k=args.k, precision="fp32", eps=1e-4,
                     stochastic=True, eta=0.1, seed=1)
+    if args.workload == "rmat_a":
+        return dict(name=f"R-MAT scale {args.scale}, edge factor 16, lazy greedy with l-doubling (Algorithm 2) "
+                         f"k={args.k} FP32", kind="greedy", graph=("rmat", args.scale), k=args.k, precision="fp32",
+                    eps=1e-4, adaptive=True)
+    if args.workload == "rmat_w":
+        return dict(name=f"R-MAT scale {args.scale}, edge factor 16, weighted D^-1/2 A D^-1/2 (Section 5.4), "
+                         f"greedy k={args.k} FP32", kind="greedy", graph=("rmat", args.scale), k=args.k,
+                    precision="fp32", eps=1e-4, weighted=True)
     if args.workload in ("ba", "ba64"):
         prec = "fp64" if args.workload == "ba64" else "fp32"
         return dict(name=f"Barabasi-Albert n=1M m=8, greedy k={args.k} {prec.upper()}", kind="greedy",
@@ -135,7 +143,8 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-MODE_NAMES = {0: "totals", 1: "two-state score", 2: "fused greedy", 3: "candidate batch", 4: "batched scoring"}
+MODE_NAMES = {0: "totals", 1: "two-state score", 2: "fused greedy", 3: "candidate batch", 4: "batched scoring",
+              5: "lookahead greedy"}
 
 
 def recorded_traffic(top, workload_key):
@@ -239,6 +248,7 @@ def oracle_greedy_sample(g, spec, L, budget_s=20.0):
 
 # ----------------------------------------------------------------------------- greedy workload
 def run_greedy(args, spec, rank, world, local):
+    import numpy as np
     import torch
 
     from paper_1910_13874_gb300 import gedwalk
@@ -247,11 +257,11 @@ def run_greedy(args, spec, rank, world, local):
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
     t_up = time.perf_counter()
-    G = gedwalk.Graph.from_host(g)
+    G = gedwalk.Graph.from_host(g, weighted=spec.get("weighted", False))
     upload_s = time.perf_counter() - t_up
     params = gedwalk.make_params(epsilon=spec["eps"], precision=spec["precision"], stream=stream.cuda_stream,
                                  stochastic=spec.get("stochastic", False), eta=spec.get("eta", 0.1),
-                                 seed=spec.get("seed", 0))
+                                 seed=spec.get("seed", 0), adaptive=spec.get("adaptive", False))
     k = spec["k"]
     for _ in range(args.warmup):
         grp, gains, score, L = G.maximize(k, params=params)
@@ -273,7 +283,10 @@ def run_greedy(args, spec, rank, world, local):
     clk = clocks.stop()
     stats = G.maximize_stats()
     t_step = dist_max(e0.elapsed_time(e1) / 1e3 / args.steps, world)
-    gteps = k * 2 * L * G.nnz / t_step / 1e9 * world
+    ell, sep_fail = G.maximize_lengths()
+    # algorithmic edges: 2l sweeps per step (l for phi^miss, l for the winner's column) at that step's l
+    edges = int(2 * ell.astype(np.int64).sum()) * G.nnz
+    gteps = edges / t_step / 1e9 * world
     out = {
         "metric": METRIC, "value": round(gteps, 3), "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(t_step * 1e3, 3), "higher_is_better": True,
@@ -288,27 +301,26 @@ def run_greedy(args, spec, rank, world, local):
         "clocks": clk,
         "greedy": {"evaluations": stats["evaluations"], "batches": stats["batches"],
                    "sweeps_per_run": stats["sweeps"], "spec_misses": stats["spec_misses"],
+                   "ell_per_step": {int(v): int(c) for v, c in zip(*np.unique(ell, return_counts=True))},
+                   "separation_failures": sep_fail,
                    "group_head": [int(x) for x in grp[:10]], "score": score},
         "upload_s": round(upload_s, 3),
     }
     if not args.no_e2e:
         # end to end through the C ABI: host CSR -> device (upload, relabel), maximise, results back
-        import numpy as np
-
         rp = torch.from_numpy(g.row_ptr).pin_memory().numpy()
         ci = torch.from_numpy(g.col_idx).pin_memory().numpy()
         n_e2e = max(1, min(args.steps, 2))
         t0 = time.perf_counter()
         for _ in range(n_e2e):
-            G2 = gedwalk.Graph(rp, ci)
+            G2 = gedwalk.Graph(rp, ci, weighted=spec.get("weighted", False))
             r = G2.maximize(k, params=params)
             G2.free()
         t_e2e = dist_max((time.perf_counter() - t0) / n_e2e, world)
-        out["e2e"] = {"value": round(k * 2 * L * G.nnz / t_e2e / 1e9 * world, 3), "unit": "GTEPS",
+        out["e2e"] = {"value": round(edges / t_e2e / 1e9 * world, 3), "unit": "GTEPS",
                       "seconds": round(t_e2e, 3), "h2d_bytes_per_step": int(rp.nbytes + ci.nbytes),
                       "d2h_bytes_per_step": int(k * 12 + 16)}
-        del np
-    if rank == 0 and not args.no_cpu_baseline and not spec.get("stochastic"):
+    if rank == 0 and not args.no_cpu_baseline and not any(spec.get(f) for f in ("stochastic", "adaptive", "weighted")):
         out["cpu_baseline"] = oracle_greedy_sample(g, spec, L)
     return out
 

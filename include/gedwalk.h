@@ -72,12 +72,14 @@ enum {
 /* gedwalk_params.flags */
 enum {
   GEDWALK_GAINS_ALL = 1,  /* maximize: evaluate every vertex's exact gain at every step (no pruning) */
-  GEDWALK_STOCHASTIC = 2  /* maximize: stochastic greedy (Appendix D), see gedwalk_maximize */
+  GEDWALK_STOCHASTIC = 2, /* maximize: stochastic greedy (Appendix D), see gedwalk_maximize */
+  GEDWALK_ADAPTIVE_L = 4  /* maximize: lazy greedy with l-doubling (Algorithm 2), see gedwalk_maximize */
 };
 
 /* gedwalk_graph_upload flags */
 enum {
-  GEDWALK_UPLOAD_TRUSTED = 1 /* skip the sortedness / symmetry / self-loop validation */
+  GEDWALK_UPLOAD_TRUSTED = 1, /* skip the sortedness / symmetry / self-loop validation */
+  GEDWALK_UPLOAD_DIRECTED = 2 /* the rows are successor lists of a directed graph (no symmetry) */
 };
 
 typedef struct {
@@ -90,10 +92,18 @@ typedef struct {
   int64_t stream;          /* cudaStream_t to run on (e.g. torch.cuda.current_stream().cuda_stream); 0 = default */
   double eta;              /* stochastic greedy: sample (n/k) ln(1/eta) vertices per step, 0 < eta < 1 */
   uint64_t seed;           /* stochastic greedy: seed of the counter-based sample draws */
+  int32_t bound;           /* GEDWALK_BOUND_COMBINATORIAL (default) or GEDWALK_BOUND_SPECTRAL */
+  int32_t reserved;        /* 0 */
 } gedwalk_params;
 
+/* gedwalk_params.bound: the tail bound behind every truncation length */
+enum {
+  GEDWALK_BOUND_COMBINATORIAL = 0, /* Eq. comb-bound: needs alpha < 1/d_max (1/delta) */
+  GEDWALK_BOUND_SPECTRAL = 1       /* Lemma spectral-bound: needs alpha < 1/sigma_max, see gedwalk_sigma_max */
+};
+
 /* Fills *p with the defaults: alpha 0, epsilon 1e-4, L 0, FP32, EPS_OVER_K, no flags, stream 0,
- * eta 0.1, seed 0. */
+ * eta 0.1, seed 0, the combinatorial bound. */
 GEDWALK_API void gedwalk_params_default(gedwalk_params* p);
 
 /*
@@ -123,6 +133,30 @@ GEDWALK_API gedwalk_status gedwalk_set_allocator(gedwalk_alloc_fn alloc, gedwalk
 GEDWALK_API gedwalk_status gedwalk_graph_upload(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int64_t nnz,
                                     int32_t flags, gedwalk_graph_t* out);
 
+/*
+ * Weighted GED-Walk (Section 5.4): a walk of length i contributes alpha^i times
+ * the product of its edge weights, the weights entering the recurrences as
+ * coefficients. This upload takes vertex-separable weights
+ *   w(v, u) = vertex_scale[v] * vertex_scale[u]
+ * on the edges of the same undirected CSR as gedwalk_graph_upload. With
+ * vertex_scale NULL the weights are those of the symmetrically normalised
+ * adjacency D^{-1/2} A D^{-1/2} (vertex_scale[v] = deg(v)^{-1/2}), the weighting
+ * the paper's applications use. No per-entry value array is stored: sweeps
+ * gather the scaled vectors s * x and scale each row once.
+ *  vertex_scale: host double[n] (copied; positive and finite) or NULL.
+ * The combinatorial bound then uses delta = max_v s_v sum_{u ~ v} s_u (the
+ * largest weighted degree, which bounds W_{l+1}/W_l) in place of d_max, and
+ * the default alpha is 1/(1 + delta). Every other entry point works on the
+ * weighted graph unchanged. Errors as gedwalk_graph_upload.
+ */
+GEDWALK_API gedwalk_status gedwalk_graph_upload_weighted(const int32_t* row_ptr, const int32_t* col_idx, int32_t n,
+                                             int64_t nnz, const double* vertex_scale, int32_t flags,
+                                             gedwalk_graph_t* out);
+
+/* *weighted = 1 for a graph from gedwalk_graph_upload_weighted; *delta the degree of the
+ * combinatorial bound (d_max, or the largest weighted degree). Either pointer may be NULL. */
+GEDWALK_API gedwalk_status gedwalk_graph_info_weighted(gedwalk_graph_t g, int32_t* weighted, double* delta);
+
 /* Releases a graph and all device memory tied to it. NULL is accepted. */
 GEDWALK_API gedwalk_status gedwalk_graph_free(gedwalk_graph_t g);
 
@@ -140,6 +174,31 @@ GEDWALK_API gedwalk_status gedwalk_graph_info(gedwalk_graph_t g, int32_t* n, int
  * l <= 4096 qualifies).
  */
 GEDWALK_API gedwalk_status gedwalk_truncation(gedwalk_graph_t g, double alpha, double epsilon, int32_t* L, double* bound);
+
+/*
+ * Largest singular value of the adjacency matrix A, sigma_max = ||A||_2 (the
+ * spectral bound's sigma, Lemma spectral-bound; Appendix E takes alpha =
+ * delta / sigma_max). Power iteration on A (undirected or weighted: symmetric,
+ * sigma_max = its spectral radius) or on A^T A (directed: sigma_max^2), in FP64
+ * sweeps on the device, from the all-ones vector kept positive. Every iterate x
+ * certifies rho <= max_v (M x)(v) / x(v) (Collatz-Wielandt bound of a
+ * non-negative matrix); *upper is the smallest such value met, inflated by
+ * 1e-12 relative against rounding, so upper >= sigma_max always holds. *lower
+ * is the last Rayleigh quotient, sqrt(x^T M x / x^T x) <= sigma_max. The graph
+ * keeps the smallest upper value as the sigma of its spectral bound.
+ *  iters: power iterations, 1..100000. upper/lower: may be NULL.
+ */
+GEDWALK_API gedwalk_status gedwalk_sigma_max(gedwalk_graph_t g, int32_t iters, double* upper, double* lower);
+
+/*
+ * gedwalk_truncation with a choice of bound: GEDWALK_BOUND_COMBINATORIAL as
+ * above, or GEDWALK_BOUND_SPECTRAL (Lemma spectral-bound):
+ *   B_l = sqrt(n) alpha^{l+1} sigma / (1 - alpha sigma) W_l,  sigma >= sigma_max
+ * the graph's certified value (computed on first use with 300 iterations when
+ * gedwalk_sigma_max has not run). Errors: NOT_CONVERGENT when alpha * sigma >= 1.
+ */
+GEDWALK_API gedwalk_status gedwalk_truncation_ex(gedwalk_graph_t g, double alpha, double epsilon, int32_t bound_kind,
+                                     int32_t* L, double* bound);
 
 /*
  * GED_{<=L}(S) of one group (problem (i), Algorithm 1), by the two-state
@@ -207,6 +266,16 @@ GEDWALK_API gedwalk_status gedwalk_gains(gedwalk_graph_t g, const int32_t* S, in
  * where splitmix64(x) is the first output of that generator started from state x;
  * an empty sample falls back to all of V \ S. The argmax within the sample is exact.
  * It cannot be combined with GEDWALK_GAINS_ALL or an init group.
+ * GEDWALK_ADAPTIVE_L runs the lazy greedy of Algorithm 2 (Section 3.2.3): the
+ * walk length l starts at 1 and only doubles. At each step u, the vertex with the
+ * largest L_l(S, u) = GED_{<=l}(S, u), is taken when it is separated from v, the
+ * best of the rest: L_l(S, u) > L_l(S, v) + B_l - eps_sep, with B_l the
+ * combinatorial bound (Eq. comb-bound) and eps_sep = epsilon/k (EPS_OVER_K) or
+ * epsilon (EPS_PLAIN); otherwise l doubles and the step is retried. Then
+ * gains[j] is L_l(S, u) at step j's l, *L_used the final l, and score the value
+ * computed without the flag (GED_{<=L} of the group, L from the bound at
+ * eps_sep). It needs params->L = 0 and cannot be combined with
+ * GEDWALK_GAINS_ALL, GEDWALK_STOCHASTIC or an init group (INVALID).
  */
 GEDWALK_API gedwalk_status gedwalk_maximize(gedwalk_graph_t g, int32_t k, const gedwalk_params* params, int32_t* group,
                                 double* gains, double* score, int32_t* L_used, const int32_t* init_group,
@@ -220,6 +289,16 @@ GEDWALK_API gedwalk_status gedwalk_maximize(gedwalk_graph_t g, int32_t k, const 
  */
 GEDWALK_API gedwalk_status gedwalk_maximize_stats(gedwalk_graph_t g, int64_t* evaluations, int64_t* batches, int64_t* sweeps,
                                       int64_t* spec_misses);
+
+/*
+ * Walk lengths of the last gedwalk_maximize on this graph: ell[j] (j < min(cap,
+ * *count)) is the l at which step j's vertex was taken (the fixed L without
+ * GEDWALK_ADAPTIVE_L); *count the number of steps; *separation_failures the
+ * number of failed separation tests (doublings of l) of Algorithm 2. ell may be
+ * NULL when cap = 0; count and separation_failures may be NULL.
+ */
+GEDWALK_API gedwalk_status gedwalk_maximize_lengths(gedwalk_graph_t g, int32_t* ell, int32_t cap, int32_t* count,
+                                        int64_t* separation_failures);
 
 /* ---------------------------------------------------------------------------
  * Serving: a continuous-batching request loop over device-resident graphs.

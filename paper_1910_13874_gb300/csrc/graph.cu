@@ -102,11 +102,13 @@ void profile_end(cudaStream_t s, cudaEvent_t a, double bytes, int key) {
   p.recs.push_back({a, b, bytes, key});
 }
 
-double sweep_bytes(int mode, bool fp64, int cols, int32_t n, int64_t nnz) {
+double sweep_bytes(int mode, bool fp64, int cols, int32_t n, int64_t nnz, bool weighted) {
   const double es = mode == MODE_TOTALS ? 8.0 : (fp64 ? 8.0 : 4.0);
   double b = 4.0 * double(nnz) + 4.0 * (double(n) + 1.0) + 2.0 * cols * es * double(n);
-  if (mode == MODE_SCORE || mode == MODE_FUSED || mode == MODE_CAND) b += double(n) / 8.0;
+  if (mode == MODE_SCORE || mode == MODE_FUSED || mode == MODE_CAND || mode == MODE_LOOK) b += double(n) / 8.0;
   if (mode == MODE_FUSED) b += es * double(n);
+  if (mode == MODE_LOOK) b += es * double(n) * (cols / 2);  // one phi^miss row per level
+  if (weighted) b += es * double(n);  // the vertex scales
   return b;
 }
 
@@ -203,7 +205,7 @@ static void parallel_rows(int64_t n, F&& f) {
 
 // First malformed row (or -1) and a reason.
 static int64_t validate_csr(const int32_t* rp, const int32_t* ci, int32_t n, int64_t nnz, bool full,
-                            std::string* why) {
+                            std::string* why, bool symmetric = true) {
   if (rp[0] != 0) {
     *why = "row_ptr[0] != 0";
     return 0;
@@ -229,7 +231,7 @@ static int64_t validate_csr(const int32_t* rp, const int32_t* ci, int32_t n, int
         else if (!full) continue;
         else if (u == v) k = 2;
         else if (j > rp[v] && ci[j - 1] >= u) k = 3;
-        else if (full && !std::binary_search(ci + rp[u], ci + rp[u + 1], static_cast<int32_t>(v))) k = 4;
+        else if (symmetric && !std::binary_search(ci + rp[u], ci + rp[u + 1], static_cast<int32_t>(v))) k = 4;
       }
       if (k) {
         int64_t cur = bad.load();
@@ -257,53 +259,60 @@ static int row_class(int32_t d) {
   return cls;
 }
 
-static gedwalk_status build_plan(Graph& g, const std::vector<int32_t>& rp) {
+// Work units of one CSR. Heavy rows (degree > kHeavyDeg) are cut into slices wherever they sit;
+// the other rows [0, n_active) form contiguous runs of one degree class. Rows from n_active on have
+// no units (isolated vertices: nothing gathers them). With rows sorted by decreasing degree (the
+// relabelled forward CSR) the heavy rows are the prefix and every class is one contiguous run; the
+// reverse CSR of a directed graph keeps the forward order, so its runs are shorter.
+static gedwalk_status build_plan(Plan& plan, const std::vector<int32_t>& deg, const std::vector<int32_t>& rp,
+                                 int32_t n_active, int32_t n) {
   std::vector<int4> units, heavy;
-  int32_t nh = 0;
-  while (nh < g.n && g.deg[nh] > kHeavyDeg) ++nh;
   int32_t slice = 0;
-  for (int32_t h = 0; h < nh; ++h) {
-    const int32_t d = g.deg[h];
+  for (int32_t r = 0; r < n_active; ++r) {
+    const int32_t d = deg[r];
+    if (d <= kHeavyDeg) continue;
     const int32_t ns = (d + kSliceEdges - 1) / kSliceEdges;
-    heavy.push_back(make_int4(h, slice, ns, 0));
+    const int32_t hi = static_cast<int32_t>(heavy.size());
+    heavy.push_back(make_int4(r, slice, ns, 0));
     for (int32_t k = 0; k < ns; ++k) {
-      const int32_t e0 = rp[h] + static_cast<int32_t>(static_cast<int64_t>(d) * k / ns);
-      const int32_t e1 = rp[h] + static_cast<int32_t>(static_cast<int64_t>(d) * (k + 1) / ns);
-      units.push_back(make_int4(h, e0, e1, slice + k));
+      const int32_t e0 = rp[r] + static_cast<int32_t>(static_cast<int64_t>(d) * k / ns);
+      const int32_t e1 = rp[r] + static_cast<int32_t>(static_cast<int64_t>(d) * (k + 1) / ns);
+      units.push_back(make_int4(hi, e0, e1, slice + k));
     }
     slice += ns;
   }
-  g.plan.num_slices = slice;
-  g.plan.num_heavy = nh;
-  // isolated rows (degree 0, sorted last) get no units: their sums are 0, nothing gathers
-  // their x, and the few outputs read back at such rows are zeroed by the callers
-  g.n_active = g.n;
-  while (g.n_active > 0 && g.deg[g.n_active - 1] == 0) --g.n_active;
-  int32_t r = nh;
-  while (r < g.n_active) {
-    const int cls = row_class(g.deg[r]);
+  plan.num_slices = slice;
+  plan.num_heavy = static_cast<int32_t>(heavy.size());
+  int32_t r = 0;
+  while (r < n_active) {
+    if (deg[r] > kHeavyDeg) {
+      ++r;
+      continue;
+    }
+    const int cls = row_class(deg[r]);
     // a short-row unit takes up to kUnitRowsMax rows; on small graphs fewer, down to one
     // iteration of its warp (2 rows per lane group), so that every SM gets work
     const int32_t iter_rows = cls == 6 ? 1 : 2 * (32 >> cls);
-    const int32_t small_cap = std::max<int32_t>(iter_rows, g.n_active / kTargetUnits);
+    const int32_t small_cap = std::max<int32_t>(iter_rows, n_active / kTargetUnits);
     const int32_t max_rows = std::min<int32_t>(cls == 6 ? 32 : kUnitRowsMax, small_cap);
     const int64_t max_edges = cls == 6 ? kLongUnitEdges : kUnitEdges;
     int32_t r1 = r;
     int64_t edges = 0;
-    while (r1 < g.n_active && row_class(g.deg[r1]) == cls && r1 - r < max_rows &&
-           (r1 == r || edges + g.deg[r1] <= max_edges)) {
-      edges += g.deg[r1];
+    while (r1 < n_active && deg[r1] <= kHeavyDeg && row_class(deg[r1]) == cls && r1 - r < max_rows &&
+           (r1 == r || edges + deg[r1] <= max_edges)) {
+      edges += deg[r1];
       ++r1;
     }
     units.push_back(make_int4(r, r1, cls, -1));
     r = r1;
   }
-  g.plan.num_units = static_cast<int32_t>(units.size());
-  g.plan.num_slots = g.plan.num_units + nh;
-  GW_TRY(g.plan.units.ensure(units.size() * sizeof(int4) + 16, 0));
-  GW_TRY(g.plan.heavy.ensure(heavy.size() * sizeof(int4) + 16, 0));
-  if (!units.empty()) GW_CUDA(cudaMemcpy(g.plan.units.p, units.data(), units.size() * sizeof(int4), cudaMemcpyHostToDevice));
-  if (!heavy.empty()) GW_CUDA(cudaMemcpy(g.plan.heavy.p, heavy.data(), heavy.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  (void)n;
+  plan.num_units = static_cast<int32_t>(units.size());
+  plan.num_slots = plan.num_units + plan.num_heavy;
+  GW_TRY(plan.units.ensure(units.size() * sizeof(int4) + 16, 0));
+  GW_TRY(plan.heavy.ensure(heavy.size() * sizeof(int4) + 16, 0));
+  if (!units.empty()) GW_CUDA(cudaMemcpy(plan.units.p, units.data(), units.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  if (!heavy.empty()) GW_CUDA(cudaMemcpy(plan.heavy.p, heavy.data(), heavy.size() * sizeof(int4), cudaMemcpyHostToDevice));
   return GEDWALK_OK;
 }
 
@@ -347,21 +356,38 @@ SweepArgs base_args(Graph& g, Workspace& ws) {
   a.slots = ws.slots.as<double>();
   a.accumulate = 0;
   a.cand = nullptr;
+  a.rs_f = g.weighted ? g.rs_f.as<float>() : nullptr;
+  a.rs_d = g.weighted ? g.rs_d.as<double>() : nullptr;
+  return a;
+}
+
+SweepArgs base_args_rev(Graph& g, Workspace& ws) {
+  SweepArgs a = base_args(g, ws);
+  a.rp = g.rp_r.as<int32_t>();
+  a.ci = g.ci_r.as<int32_t>();
+  a.units = g.plan_r.units.as<int4>();
+  a.heavy = g.plan_r.heavy.as<int4>();
+  a.num_units = g.plan_r.num_units;
   return a;
 }
 
 gedwalk_status ensure_sweep_scratch(Graph& g, Workspace& ws, int cols, bool fp64, cudaStream_t s) {
   const size_t es = fp64 ? 8 : 4;
-  GW_TRY(ws.partial.ensure(static_cast<size_t>(std::max(g.plan.num_slices, 1)) * cols * es, s));
-  const size_t cbytes = static_cast<size_t>(std::max(g.plan.num_heavy, 1)) * sizeof(unsigned);
+  // sized for the larger of the two plans of a directed graph
+  const int32_t slices = std::max(g.plan.num_slices, g.directed ? g.plan_r.num_slices : 0);
+  const int32_t heavy = std::max(g.plan.num_heavy, g.directed ? g.plan_r.num_heavy : 0);
+  const int32_t slots = std::max(g.plan.num_slots, g.directed ? g.plan_r.num_slots : 0);
+  GW_TRY(ws.partial.ensure(static_cast<size_t>(std::max(slices, 1)) * cols * es, s));
+  const size_t cbytes = static_cast<size_t>(std::max(heavy, 1)) * sizeof(unsigned);
   if (ws.counters.bytes < cbytes || !ws.counters.p) GW_TRY(ws.counters.ensure(cbytes, s, /*zero=*/true));
-  GW_TRY(ws.slots.ensure(static_cast<size_t>(std::max(g.plan.num_slots, 1)) * cols * sizeof(double), s));
+  GW_TRY(ws.slots.ensure(static_cast<size_t>(std::max(slots, 1)) * cols * sizeof(double), s));
   GW_TRY(ws.parts.ensure(static_cast<size_t>(cols) * kReduceParts * sizeof(double), s));
   return GEDWALK_OK;
 }
 
-gedwalk_status reduce_slots(Graph& g, Workspace& ws, int nsum, double* out, cudaStream_t s) {
-  return launch_reduce_slots(ws.slots.as<double>(), g.plan.num_slots, nsum, out, ws.parts.as<double>(), s);
+gedwalk_status reduce_slots(Graph& g, Workspace& ws, int nsum, double* out, cudaStream_t s, bool rev) {
+  return launch_reduce_slots(ws.slots.as<double>(), rev ? g.plan_r.num_slots : g.plan.num_slots, nsum, out,
+                             ws.parts.as<double>(), s);
 }
 
 // ---------------------------------------------------------------- walk totals
@@ -395,12 +421,20 @@ gedwalk_status ensure_totals(Graph& g, double alpha, int32_t rows, cudaStream_t 
   double* dWa = ws.small.as<double>();
   int32_t r0 = g.tt_rows;
   if (r0 == 0) {
-    fill_f64_kernel<<<grid_for(g.n), 256, 0, s>>>(T, g.n, 1.0);
-    GW_KCHECK();
+    // t_0 = 1, stored scaled (t~_0 = s) on a weighted graph: the rows of the table are sweep inputs
+    if (g.weighted) {
+      GW_CUDA(cudaMemcpyAsync(T, g.rs_d.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    } else {
+      fill_f64_kernel<<<grid_for(g.n), 256, 0, s>>>(T, g.n, 1.0);
+      GW_KCHECK();
+    }
     g.Wa.assign(1, static_cast<double>(g.n));
     r0 = 1;
   }
-  SweepArgs a = base_args(g, ws);
+  // t_r counts the walks that start at a vertex; on a directed graph batched scoring needs the
+  // walks that end there (the sweeps' other orientation), so the table runs on the reverse CSR.
+  // The totals W_r are the same either way.
+  SweepArgs a = g.directed ? base_args_rev(g, ws) : base_args(g, ws);
   a.alpha = alpha;
   a.accumulate = 0;
   for (int32_t r = r0; r < rows; ++r) {
@@ -410,7 +444,7 @@ gedwalk_status ensure_totals(Graph& g, double alpha, int32_t rows, cudaStream_t 
       GW_CUDA(cudaMemsetAsync(T + static_cast<size_t>(r) * n + g.n_active, 0,
                               sizeof(double) * (n - static_cast<size_t>(g.n_active)), s));
     GW_TRY(launch_sweep(MODE_TOTALS, true, 1, a, s));
-    GW_TRY(reduce_slots(g, ws, 1, dWa + r, s));
+    GW_TRY(reduce_slots(g, ws, 1, dWa + r, s, g.directed));
   }
   std::vector<double> tmp(rows);
   GW_CUDA(cudaMemcpyAsync(tmp.data() + r0, dWa + r0, sizeof(double) * (rows - r0), cudaMemcpyDeviceToHost, s));
@@ -421,20 +455,167 @@ gedwalk_status ensure_totals(Graph& g, double alpha, int32_t rows, cudaStream_t 
   return GEDWALK_OK;
 }
 
-gedwalk_status truncation_length(Graph& g, double alpha, double eps, int32_t* L, double* bound, cudaStream_t s) {
-  if (!(alpha > 0.0) || !std::isfinite(alpha)) return fail(GEDWALK_ERR_INVALID, "alpha must be positive");
-  if (!(eps > 0.0)) return fail(GEDWALK_ERR_INVALID, "epsilon must be positive");
-  if (!(alpha * g.dmax < 1.0))
+// ---------------------------------------------------------------- sigma_max by power iteration
+// Statistics of one power step y = M x on the true vectors (a weighted graph stores s * x; the
+// scale cancels in the ratio): per block the largest y(v)/x(v) over x(v) > 0 (Collatz-Wielandt),
+// sum x(v) y(v), sum x(v)^2 and the largest y(v). rs: vertex scales or nullptr.
+constexpr int kPiBlocks = 304;
+__global__ void pi_stats_kernel(const double* __restrict__ X, const double* __restrict__ Y,
+                                const double* __restrict__ rs, int32_t n, double* __restrict__ part) {
+  double rmax = 0.0, num = 0.0, den = 0.0, ymax = 0.0;
+  for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const double xs = X[v], ys = Y[v];
+    if (!(xs > 0.0)) continue;  // a weighted vertex without edges (scale 0)
+    rmax = fmax(rmax, ys / xs);
+    const double sv = rs ? rs[v] : 1.0;
+    const double x = xs / sv, y = ys / sv;
+    num += x * y;
+    den += x * x;
+    ymax = fmax(ymax, y);
+  }
+  __shared__ double sm[4][256];
+  sm[0][threadIdx.x] = rmax;
+  sm[1][threadIdx.x] = num;
+  sm[2][threadIdx.x] = den;
+  sm[3][threadIdx.x] = ymax;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      sm[0][threadIdx.x] = fmax(sm[0][threadIdx.x], sm[0][threadIdx.x + o]);
+      sm[1][threadIdx.x] += sm[1][threadIdx.x + o];
+      sm[2][threadIdx.x] += sm[2][threadIdx.x + o];
+      sm[3][threadIdx.x] = fmax(sm[3][threadIdx.x], sm[3][threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < 4) part[threadIdx.x * kPiBlocks + blockIdx.x] = sm[threadIdx.x][0];
+}
+
+// st = {smallest Collatz-Wielandt value so far, last Rayleigh quotient, normaliser for the next x}
+__global__ void pi_finish_kernel(const double* __restrict__ part, double* __restrict__ st) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double rmax = 0.0, num = 0.0, den = 0.0, ymax = 0.0;
+  for (int b = 0; b < kPiBlocks; ++b) {
+    rmax = fmax(rmax, part[b]);
+    num += part[kPiBlocks + b];
+    den += part[2 * kPiBlocks + b];
+    ymax = fmax(ymax, part[3 * kPiBlocks + b]);
+  }
+  st[0] = fmin(st[0], rmax);
+  st[1] = den > 0.0 ? num / den : 0.0;
+  st[2] = ymax > 0.0 ? ymax : 1.0;
+}
+
+// x <- y / ymax + tau (true values): positive everywhere, as the Collatz-Wielandt bound needs.
+__global__ void pi_next_kernel(double* __restrict__ X, const double* __restrict__ Y, const double* __restrict__ rs,
+                               int32_t n, const double* __restrict__ st, double tau) {
+  const double inv = 1.0 / st[2];
+  for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+    X[v] = Y[v] * inv + tau * (rs ? rs[v] : 1.0);
+}
+
+__global__ void pi_init_kernel(double* __restrict__ X, double* __restrict__ Y, double* __restrict__ Z,
+                               const double* __restrict__ rs, int32_t n, double* __restrict__ st) {
+  for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    X[v] = rs ? rs[v] : 1.0;  // x = 1, stored scaled
+    Y[v] = 0.0;               // rows without units are never written: they stay 0
+    Z[v] = 0.0;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st[0] = INFINITY;
+    st[1] = 0.0;
+    st[2] = 1.0;
+  }
+}
+
+static gedwalk_status power_iteration(Graph& g, int32_t iters, cudaStream_t s) {
+  Workspace& ws = g.ws;
+  const size_t n = static_cast<size_t>(g.n);
+  GW_TRY(ws.pvec.ensure((3 * n + 4 * kPiBlocks + 8) * sizeof(double), s));
+  GW_TRY(ensure_sweep_scratch(g, ws, 1, true, s));
+  double* X = ws.pvec.as<double>();
+  double* Y = X + n;
+  double* Z = Y + n;  // directed: A x before A^T
+  double* part = Z + n;
+  double* st = part + 4 * kPiBlocks;
+  const double* rs = g.weighted ? g.rs_d.as<double>() : nullptr;
+  pi_init_kernel<<<grid_for(g.n), 256, 0, s>>>(X, Y, Z, rs, g.n, st);
+  GW_KCHECK();
+  SweepArgs a = base_args(g, ws);
+  a.alpha = 1.0;
+  a.accumulate = 0;
+  SweepArgs ar = g.directed ? base_args_rev(g, ws) : a;
+  ar.alpha = 1.0;
+  ar.accumulate = 0;
+  for (int32_t it = 0; it < iters; ++it) {
+    if (g.directed) {  // M = A^T A: sigma_max^2 = rho(M)
+      a.X = X;
+      a.Y = Z;
+      GW_TRY(launch_sweep(MODE_TOTALS, true, 1, a, s, false));
+      ar.X = Z;
+      ar.Y = Y;
+      GW_TRY(launch_sweep(MODE_TOTALS, true, 1, ar, s, false));
+    } else {  // symmetric M = A: sigma_max = rho(A)
+      a.X = X;
+      a.Y = Y;
+      GW_TRY(launch_sweep(MODE_TOTALS, true, 1, a, s, false));
+    }
+    pi_stats_kernel<<<kPiBlocks, 256, 0, s>>>(X, Y, rs, g.n, part);
+    pi_finish_kernel<<<1, 32, 0, s>>>(part, st);
+    pi_next_kernel<<<grid_for(g.n), 256, 0, s>>>(X, Y, rs, g.n, st, 1e-9);
+    GW_KCHECK();
+    count_launches(3);
+  }
+  double h[2];
+  GW_CUDA(cudaMemcpyAsync(h, st, sizeof h, cudaMemcpyDeviceToHost, s));
+  GW_CUDA(cudaStreamSynchronize(s));
+  // rounding of the FP64 sums (at most d_max terms each) stays far below 1e-10 relative
+  double up = h[0] * (1.0 + 1e-10), lo = h[1];
+  if (g.directed) {
+    up = std::sqrt(up);
+    lo = std::sqrt(std::max(lo, 0.0));
+  }
+  if (g.sigma_up == 0.0 || up < g.sigma_up) g.sigma_up = up;
+  g.sigma_lo = std::max(g.sigma_lo, lo);
+  // cached spectral truncation lengths were found with the old sigma
+  g.trunc_cache.erase(std::remove_if(g.trunc_cache.begin(), g.trunc_cache.end(),
+                                     [](const Graph::Trunc& t) { return t.kind == GEDWALK_BOUND_SPECTRAL; }),
+                      g.trunc_cache.end());
+  return GEDWALK_OK;
+}
+
+gedwalk_status bound_coef(Graph& g, double alpha, int32_t kind, cudaStream_t s, double* coef) {
+  if (kind == GEDWALK_BOUND_SPECTRAL) {
+    if (g.sigma_up == 0.0) GW_TRY(power_iteration(g, 300, s));
+    if (!(alpha * g.sigma_up < 1.0))
+      return fail(GEDWALK_ERR_NOT_CONVERGENT,
+                  "alpha * sigma_max = %g >= 1: the spectral bound needs alpha < 1/sigma_max (force L instead)",
+                  alpha * g.sigma_up);
+    // Lemma spectral-bound: B_l = sqrt(n) alpha sigma / (1 - alpha sigma) * alpha^l W_l
+    *coef = std::sqrt(static_cast<double>(g.n)) * alpha * g.sigma_up / (1.0 - alpha * g.sigma_up);
+    return GEDWALK_OK;
+  }
+  if (kind != GEDWALK_BOUND_COMBINATORIAL) return fail(GEDWALK_ERR_INVALID, "unknown bound kind %d", kind);
+  if (!(alpha * g.delta < 1.0))
     return fail(GEDWALK_ERR_NOT_CONVERGENT,
                 "alpha * d_max = %g >= 1: the combinatorial bound needs alpha < 1/d_max (force L instead)",
-                alpha * g.dmax);
-  for (const Graph::Trunc& t : g.trunc_cache)  // L depends only on (graph, alpha, epsilon)
-    if (t.alpha == alpha && t.eps == eps) {
+                alpha * g.delta);
+  *coef = alpha * g.delta / (1.0 - alpha * g.delta);
+  return GEDWALK_OK;
+}
+
+gedwalk_status truncation_length(Graph& g, double alpha, double eps, int32_t* L, double* bound, cudaStream_t s,
+                                 int32_t kind) {
+  if (!(alpha > 0.0) || !std::isfinite(alpha)) return fail(GEDWALK_ERR_INVALID, "alpha must be positive");
+  if (!(eps > 0.0)) return fail(GEDWALK_ERR_INVALID, "epsilon must be positive");
+  double coef = 0.0;
+  GW_TRY(bound_coef(g, alpha, kind, s, &coef));
+  for (const Graph::Trunc& t : g.trunc_cache)  // L depends only on (graph, alpha, epsilon, bound)
+    if (t.alpha == alpha && t.eps == eps && t.kind == kind) {
       *L = t.L;
       if (bound) *bound = t.bound;
       return GEDWALK_OK;
     }
-  const double coef = alpha * g.dmax / (1.0 - alpha * g.dmax);
   const int32_t kCap = 4096;
   int32_t rows = std::max(g.tt_alpha == alpha ? g.tt_rows : 0, 4);
   Workspace& ws = g.ws;
@@ -457,7 +638,7 @@ gedwalk_status truncation_length(Graph& g, double alpha, double eps, int32_t* L,
       *L = hl;
       if (bound) *bound = hb;
       if (g.trunc_cache.size() >= 64) g.trunc_cache.erase(g.trunc_cache.begin());
-      g.trunc_cache.push_back({alpha, eps, hl, hb});
+      g.trunc_cache.push_back({alpha, eps, hl, hb, kind});
       return GEDWALK_OK;
     }
     if (rows >= kCap) return fail(GEDWALK_ERR_INVALID, "no truncation length <= %d reaches epsilon %g", kCap, eps);
@@ -478,19 +659,24 @@ gedwalk_status resolve(Graph& g, const gedwalk_params* p, double eps_override, R
   r->stream = reinterpret_cast<cudaStream_t>(p->stream);
   r->eta = p->eta;
   r->seed = p->seed;
+  if (p->bound != GEDWALK_BOUND_COMBINATORIAL && p->bound != GEDWALK_BOUND_SPECTRAL)
+    return fail(GEDWALK_ERR_INVALID, "bound must be GEDWALK_BOUND_COMBINATORIAL or GEDWALK_BOUND_SPECTRAL");
+  r->bound_kind = p->bound;
   if (p->L < 0) return fail(GEDWALK_ERR_INVALID, "L must be >= 0");
   if (p->L > 0) {
     if (p->L > 4096) return fail(GEDWALK_ERR_INVALID, "L must be <= 4096");
     r->L = p->L;
     r->bound = NAN;
-    if (r->alpha * g.dmax < 1.0) {
+    double coef = 0.0;
+    if (bound_coef(g, r->alpha, p->bound, r->stream, &coef) == GEDWALK_OK) {
       GW_TRY(ensure_totals(g, r->alpha, p->L + 1, r->stream));
-      r->bound = r->alpha * g.dmax / (1.0 - r->alpha * g.dmax) * g.Wa[p->L];
+      r->bound = coef * g.Wa[p->L];
     }
     return GEDWALK_OK;
   }
   const double eps = eps_override > 0.0 ? eps_override : p->epsilon;
-  return truncation_length(g, r->alpha, eps, &r->L, &r->bound, r->stream);
+  r->eps = eps;
+  return truncation_length(g, r->alpha, eps, &r->L, &r->bound, r->stream, p->bound);
 }
 
 gedwalk_status map_group(const Graph& g, const int32_t* S, int32_t s_len, std::vector<int32_t>* out) {
@@ -535,6 +721,8 @@ void gedwalk_params_default(gedwalk_params* p) {
   p->stream = 0;
   p->eta = 0.1;
   p->seed = 0;
+  p->bound = GEDWALK_BOUND_COMBINATORIAL;
+  p->reserved = 0;
 }
 
 const char* gedwalk_last_error(void) { return t_last_error.c_str(); }
@@ -611,18 +799,20 @@ gedwalk_status gedwalk_set_allocator(gedwalk_alloc_fn alloc, gedwalk_free_fn rel
   return GEDWALK_OK;
 }
 
-gedwalk_status gedwalk_graph_upload(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int64_t nnz,
-                                    int32_t flags, gedwalk_graph_t* out) {
+static gedwalk_status upload_impl(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int64_t nnz,
+                                  int32_t flags, bool weighted, const double* vertex_scale, gedwalk_graph_t* out) {
   if (!out) return fail(GEDWALK_ERR_INVALID, "out is NULL");
   if (n < 1) return fail(GEDWALK_ERR_INVALID, "n must be >= 1");
   if (nnz < 0 || nnz >= (int64_t(1) << 31) - 8) return fail(GEDWALK_ERR_INVALID, "nnz must be in [0, 2^31 - 8)");
   if (!row_ptr || (nnz > 0 && !col_idx)) return fail(GEDWALK_ERR_INVALID, "row_ptr/col_idx is NULL");
+  const bool directed = (flags & GEDWALK_UPLOAD_DIRECTED) != 0;
+  if (directed && weighted) return fail(GEDWALK_ERR_INVALID, "weighted directed graphs are not supported");
   std::string why;
   const bool trusted = (flags & GEDWALK_UPLOAD_TRUSTED) != 0;
   {
     // row_ptr and index ranges are always checked (the plan and the kernels index with
     // them); TRUSTED skips the sortedness, self-loop and symmetry checks
-    const int64_t bad = validate_csr(row_ptr, col_idx, n, nnz, !trusted, &why);
+    const int64_t bad = validate_csr(row_ptr, col_idx, n, nnz, !trusted, &why, !directed);
     if (bad >= 0)
       return fail(GEDWALK_ERR_INVALID, "malformed graph at row %lld: %s", static_cast<long long>(bad), why.c_str());
   }
@@ -630,25 +820,66 @@ gedwalk_status gedwalk_graph_upload(const int32_t* row_ptr, const int32_t* col_i
   GW_CUDA(cudaGetDevice(&g->device));
   g->n = n;
   g->nnz = nnz;
-  std::vector<int32_t> deg_old(n);
+  g->directed = directed;
+  // degrees by caller id: the rows' own lengths; for a directed graph also the reverse (in) degree
+  std::vector<int32_t> deg_old(n), rdeg_old;
   int32_t dmax = 0;
   for (int32_t v = 0; v < n; ++v) {
     deg_old[v] = row_ptr[v + 1] - row_ptr[v];
     dmax = std::max(dmax, deg_old[v]);
   }
+  int32_t rdmax = 0;
+  if (directed) {
+    rdeg_old.assign(n, 0);
+    for (int64_t j = 0; j < nnz; ++j) rdeg_old[col_idx[j]]++;
+    for (int32_t v = 0; v < n; ++v) rdmax = std::max(rdmax, rdeg_old[v]);
+  }
   g->dmax = dmax;
-  g->alpha_default = 1.0 / (1.0 + dmax);
-  // relabel: decreasing degree, ties by caller id (stable counting sort)
-  std::vector<int64_t> start(static_cast<size_t>(dmax) + 2, 0);
-  for (int32_t v = 0; v < n; ++v) start[dmax - deg_old[v] + 1]++;
-  for (size_t i = 1; i < start.size(); ++i) start[i] += start[i - 1];
+  // W_{l+1} <= d W_l with d = d_max; on a digraph an l-walk extends at its end along at most
+  // max out-degree arcs and at its start along at most max in-degree arcs, so the smaller counts
+  g->delta = directed ? std::min(dmax, rdmax) : dmax;
+  std::vector<double> scale;  // caller order
+  if (weighted) {
+    // w(v,u) = s_v s_u; without scales the symmetrically normalised adjacency D^{-1/2} A D^{-1/2}
+    // (Section 5.4), s_v = deg(v)^{-1/2} (0 for a vertex without edges, which no walk visits)
+    scale.resize(n);
+    for (int32_t v = 0; v < n; ++v) {
+      if (vertex_scale) {
+        if (!(vertex_scale[v] > 0.0) || !std::isfinite(vertex_scale[v]))
+          return fail(GEDWALK_ERR_INVALID, "vertex_scale[%d] = %g must be positive and finite", v, vertex_scale[v]);
+        scale[v] = vertex_scale[v];
+      } else {
+        scale[v] = deg_old[v] > 0 ? 1.0 / std::sqrt(static_cast<double>(deg_old[v])) : 0.0;
+      }
+    }
+    // the degree of the combinatorial bound: the largest weighted degree s_v sum_u s_u
+    double delta = 0.0;
+    for (int32_t v = 0; v < n; ++v) {
+      double acc = 0.0;
+      for (int64_t j = row_ptr[v]; j < row_ptr[v + 1]; ++j) acc += scale[col_idx[j]];
+      delta = std::max(delta, scale[v] * acc);
+    }
+    g->delta = delta;
+    g->weighted = true;
+  }
+  g->alpha_default = 1.0 / (1.0 + g->delta);
+  // relabel: decreasing degree, ties by (directed) decreasing reverse degree, then caller id. A
+  // vertex with no arc at all sorts last, so the isolated rows form the tail.
   g->perm.resize(n);
   g->inv.resize(n);
-  for (int32_t v = 0; v < n; ++v) {
-    const int64_t pos = start[dmax - deg_old[v]]++;
-    g->perm[pos] = v;
-    g->inv[v] = static_cast<int32_t>(pos);
+  if (!directed) {
+    std::vector<int64_t> start(static_cast<size_t>(dmax) + 2, 0);  // stable counting sort
+    for (int32_t v = 0; v < n; ++v) start[dmax - deg_old[v] + 1]++;
+    for (size_t i = 1; i < start.size(); ++i) start[i] += start[i - 1];
+    for (int32_t v = 0; v < n; ++v) g->perm[start[dmax - deg_old[v]]++] = v;
+  } else {
+    for (int32_t v = 0; v < n; ++v) g->perm[v] = v;
+    std::stable_sort(g->perm.begin(), g->perm.end(), [&](int32_t a, int32_t b) {
+      if (deg_old[a] != deg_old[b]) return deg_old[a] > deg_old[b];
+      return rdeg_old[a] > rdeg_old[b];
+    });
   }
+  for (int32_t i = 0; i < n; ++i) g->inv[g->perm[i]] = i;
   g->deg.resize(n);
   std::vector<int32_t> rp(static_cast<size_t>(n) + 1);
   rp[0] = 0;
@@ -667,14 +898,67 @@ gedwalk_status gedwalk_graph_upload(const int32_t* row_ptr, const int32_t* col_i
       std::sort(dst, dst + len);
     }
   });
+  // rows from n_active on are isolated: no entry in either direction
+  g->n_active = n;
+  if (!directed) {
+    while (g->n_active > 0 && g->deg[g->n_active - 1] == 0) --g->n_active;
+  } else {
+    while (g->n_active > 0 && g->deg[g->n_active - 1] == 0 && rdeg_old[g->perm[g->n_active - 1]] == 0) --g->n_active;
+  }
   GW_TRY(g->rp.ensure(rp.size() * sizeof(int32_t), 0));
   GW_TRY(g->ci.ensure(ci.size() * sizeof(int32_t), 0));
   GW_TRY(g->perm_d.ensure(static_cast<size_t>(n) * sizeof(int32_t), 0));
   GW_CUDA(cudaMemcpy(g->rp.p, rp.data(), rp.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
   GW_CUDA(cudaMemcpy(g->ci.p, ci.data(), ci.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
   GW_CUDA(cudaMemcpy(g->perm_d.p, g->perm.data(), static_cast<size_t>(n) * sizeof(int32_t), cudaMemcpyHostToDevice));
-  GW_TRY(build_plan(*g, rp));
+  if (weighted) {
+    std::vector<double> sd(n);
+    std::vector<float> sf(n);
+    for (int32_t i = 0; i < n; ++i) {
+      sd[i] = scale[g->perm[i]];
+      sf[i] = static_cast<float>(sd[i]);
+    }
+    GW_TRY(g->rs_d.ensure(static_cast<size_t>(n) * sizeof(double), 0));
+    GW_TRY(g->rs_f.ensure(static_cast<size_t>(n) * sizeof(float), 0));
+    GW_CUDA(cudaMemcpy(g->rs_d.p, sd.data(), sd.size() * sizeof(double), cudaMemcpyHostToDevice));
+    GW_CUDA(cudaMemcpy(g->rs_f.p, sf.data(), sf.size() * sizeof(float), cudaMemcpyHostToDevice));
+  }
+  GW_TRY(build_plan(g->plan, g->deg, rp, g->n_active, n));
+  if (directed) {
+    // the reverse CSR (row v: the u with an arc u -> v), same ids, rows sorted
+    g->deg_r.assign(n, 0);
+    for (int32_t i = 0; i < n; ++i) g->deg_r[i] = rdeg_old[g->perm[i]];
+    std::vector<int32_t> rpr(static_cast<size_t>(n) + 1, 0);
+    for (int32_t i = 0; i < n; ++i) rpr[i + 1] = rpr[i] + g->deg_r[i];
+    std::vector<int32_t> cir(static_cast<size_t>(nnz) + 4, 0);
+    std::vector<int32_t> fill(rpr.begin(), rpr.end() - 1);
+    for (int32_t i = 0; i < n; ++i)  // rows i in increasing order: every reverse row comes out sorted
+      for (int32_t j = rp[i]; j < rp[i + 1]; ++j) cir[fill[ci[j]]++] = i;
+    GW_TRY(g->rp_r.ensure(rpr.size() * sizeof(int32_t), 0));
+    GW_TRY(g->ci_r.ensure(cir.size() * sizeof(int32_t), 0));
+    GW_CUDA(cudaMemcpy(g->rp_r.p, rpr.data(), rpr.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    GW_CUDA(cudaMemcpy(g->ci_r.p, cir.data(), cir.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    GW_TRY(build_plan(g->plan_r, g->deg_r, rpr, g->n_active, n));
+  }
   *out = reinterpret_cast<gedwalk_graph_t>(g.release());
+  return GEDWALK_OK;
+}
+
+gedwalk_status gedwalk_graph_upload(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int64_t nnz,
+                                    int32_t flags, gedwalk_graph_t* out) {
+  return upload_impl(row_ptr, col_idx, n, nnz, flags, false, nullptr, out);
+}
+
+gedwalk_status gedwalk_graph_upload_weighted(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int64_t nnz,
+                                             const double* vertex_scale, int32_t flags, gedwalk_graph_t* out) {
+  return upload_impl(row_ptr, col_idx, n, nnz, flags, true, vertex_scale, out);
+}
+
+gedwalk_status gedwalk_graph_info_weighted(gedwalk_graph_t h, int32_t* weighted, double* delta) {
+  if (!h) return fail(GEDWALK_ERR_INVALID, "graph is NULL");
+  Graph* g = G(h);
+  if (weighted) *weighted = g->weighted ? 1 : 0;
+  if (delta) *delta = g->delta;
   return GEDWALK_OK;
 }
 
@@ -707,6 +991,34 @@ gedwalk_status gedwalk_truncation(gedwalk_graph_t h, double alpha, double epsilo
   GW_TRY(truncation_length(*g, alpha, epsilon, &l, &b, 0));
   *L = l;
   if (bound) *bound = b;
+  return GEDWALK_OK;
+}
+
+gedwalk_status gedwalk_truncation_ex(gedwalk_graph_t h, double alpha, double epsilon, int32_t bound_kind, int32_t* L,
+                                     double* bound) {
+  if (!h || !L) return fail(GEDWALK_ERR_INVALID, "graph or L is NULL");
+  Graph* g = G(h);
+  std::lock_guard<std::mutex> lk(g->mu);
+  GW_CUDA(cudaSetDevice(g->device));
+  if (alpha < 0.0 || std::isnan(alpha)) return fail(GEDWALK_ERR_INVALID, "alpha must be positive (0 = default)");
+  if (alpha == 0.0) alpha = g->alpha_default;
+  double b = 0;
+  int32_t l = 0;
+  GW_TRY(truncation_length(*g, alpha, epsilon, &l, &b, 0, bound_kind));
+  *L = l;
+  if (bound) *bound = b;
+  return GEDWALK_OK;
+}
+
+gedwalk_status gedwalk_sigma_max(gedwalk_graph_t h, int32_t iters, double* upper, double* lower) {
+  if (!h) return fail(GEDWALK_ERR_INVALID, "graph is NULL");
+  if (iters < 1 || iters > 100000) return fail(GEDWALK_ERR_INVALID, "iters must be in [1, 100000]");
+  Graph* g = G(h);
+  std::lock_guard<std::mutex> lk(g->mu);
+  GW_CUDA(cudaSetDevice(g->device));
+  GW_TRY(power_iteration(*g, iters, 0));
+  if (upper) *upper = g->sigma_up;
+  if (lower) *lower = g->sigma_lo;
   return GEDWALK_OK;
 }
 

@@ -135,20 +135,56 @@ __device__ void block_topk(float (&v)[kTopK], int (&id)[kTopK], float* out_v, in
 }
 
 // mtab row 0 = phi^miss_0 = 1_{V\S}; X column 0 (fused) = the same; candidate columns = e_c.
+// On a weighted graph X holds the scaled vectors (times s_v, rs); the table the true values.
 template <typename T>
 __global__ void greedy_init(T* __restrict__ m0, T* __restrict__ X, int cols, int first_cand_col,
-                            const int32_t* __restrict__ cand, const uint32_t* __restrict__ mask, int32_t n) {
+                            const int32_t* __restrict__ cand, const uint32_t* __restrict__ mask, int32_t n,
+                            const T* __restrict__ rs) {
   __shared__ int sc[16];
   if (threadIdx.x < 16) sc[threadIdx.x] = threadIdx.x < cols - first_cand_col ? cand[threadIdx.x] : -1;
   __syncthreads();
   for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
     const bool inS = (mask[v >> 5] >> (v & 31)) & 1u;
     const T m = inS ? T(0) : T(1);
+    const T sv = rs ? rs[v] : T(1);
     if (m0) m0[v] = m;
     T* row = X + static_cast<size_t>(v) * cols;
-    if (first_cand_col == 1) row[0] = m;
-    for (int j = first_cand_col; j < cols; ++j) row[j] = (sc[j - first_cand_col] == v) ? T(1) : T(0);
+    if (first_cand_col == 1) row[0] = m * sv;
+    for (int j = first_cand_col; j < cols; ++j) row[j] = (sc[j - first_cand_col] == v) ? sv : T(0);
   }
+}
+
+// MODE_LOOK initialisation: level d (columns 2d, 2d+1) runs under S + {c_1..c_d}: column 2d is
+// its phi^miss_0 (also table d, row 0), column 2d+1 the unit vector of c_{d+1} (0 without one).
+template <typename T>
+__global__ void look_init(T* __restrict__ tab, int64_t tab_stride, T* __restrict__ X, int levels,
+                          const int32_t* __restrict__ cand, const uint32_t* __restrict__ mask, int32_t n,
+                          const T* __restrict__ rs) {
+  __shared__ int sc[8];
+  if (threadIdx.x < 8) sc[threadIdx.x] = threadIdx.x < levels ? cand[threadIdx.x] : -1;
+  __syncthreads();
+  const int cols = 2 * levels;
+  for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    bool out = (mask[v >> 5] >> (v & 31)) & 1u;
+    const T sv = rs ? rs[v] : T(1);
+    T* row = X + static_cast<size_t>(v) * cols;
+    for (int d = 0; d < levels; ++d) {
+      if (d > 0 && sc[d - 1] == v) out = true;
+      const T m = out ? T(0) : T(1);
+      tab[tab_stride * d + v] = m;
+      row[2 * d] = m * sv;
+      row[2 * d + 1] = sc[d] == v ? sv : T(0);
+    }
+  }
+}
+
+// Records one exact gain known on the host (a lookahead level's candidate) for this step.
+__global__ void set_stale(Stale* __restrict__ stale, int32_t v, double gain, int32_t step, double* __restrict__ out) {
+  Stale st;
+  st.ub = __double2float_ru(gain);
+  st.step = step;
+  stale[v] = st;
+  out[0] = gain;
 }
 
 __global__ void update_stale(Stale* __restrict__ stale, const int32_t* __restrict__ cand,
@@ -168,23 +204,31 @@ __device__ __forceinline__ float to_f32_up(float v) { return v; }
 __device__ __forceinline__ float to_f32_up(double v) { return __double2float_ru(v); }
 
 // Lemma-initialize bound of vertex x:
-//   ub(x) = sum_{i=1..L} alpha^i P_i(S, x) = sum over ordered pairs 1 <= a+b <= L of y_a(x) y_b(x)
-//         = y_0 (Q_L - y_0) + sum_{a=1..L} y_a Q_{L-a},   Q_q = sum_{b <= q} y_b,
-// y_a = alpha^a phi^miss_a(x) (psi^miss = phi^miss on an undirected graph). Evaluated in FP32
-// with every operation rounded toward +infinity on non-negative inputs (FP64 inputs are
+//   ub(x) = sum_{i=1..L} alpha^i P_i(S, x) = sum over ordered pairs 1 <= a+b <= L of y_a(x) z_b(x)
+//         = y_0 (Q_L - z_0) + sum_{a=1..L} y_a Q_{L-a},   Q_q = sum_{b <= q} z_b,
+// y_a = alpha^a phi^miss_a(x) and z_b = alpha^b psi^miss_b(x), the S-avoiding walks in the other
+// orientation (a directed graph's reverse; on an undirected graph z = y, zcol == col). Evaluated
+// in FP32 with every operation rounded toward +infinity on non-negative inputs (FP64 inputs are
 // first rounded up), so the result never falls below the bound of the stored vectors.
 template <typename T, int L>
-__device__ __forceinline__ float ub_fixed(const T* __restrict__ col, int32_t n) {
-  float y[L + 1];
+__device__ __forceinline__ float ub_fixed(const T* __restrict__ col, const T* __restrict__ zcol, int32_t n) {
+  float y[L + 1], z[L + 1];
 #pragma unroll
   for (int a = 0; a <= L; ++a) y[a] = to_f32_up(__ldcs(col + static_cast<size_t>(a) * n));
+  if (zcol == col) {
+#pragma unroll
+    for (int a = 0; a <= L; ++a) z[a] = y[a];
+  } else {
+#pragma unroll
+    for (int a = 0; a <= L; ++a) z[a] = to_f32_up(__ldcs(zcol + static_cast<size_t>(a) * n));
+  }
   float Q[L + 1];
-  Q[0] = y[0];
+  Q[0] = z[0];
   float R = 0.0f;
 #pragma unroll
   for (int q = 1; q <= L; ++q) {
-    Q[q] = __fadd_ru(Q[q - 1], y[q]);
-    R = __fadd_ru(R, y[q]);
+    Q[q] = __fadd_ru(Q[q - 1], z[q]);
+    R = __fadd_ru(R, z[q]);
   }
   float ub = __fmul_ru(y[0], R);
 #pragma unroll
@@ -193,17 +237,18 @@ __device__ __forceinline__ float ub_fixed(const T* __restrict__ col, int32_t n) 
 }
 
 template <typename T>
-__device__ float ub_any(const T* __restrict__ col, int32_t n, int32_t L) {
+__device__ float ub_any(const T* __restrict__ col, const T* __restrict__ zcol, int32_t n, int32_t L) {
   float ub = 0.0f;
   for (int i = 1; i <= L; ++i)
     for (int j = 0; j <= i; ++j)
-      ub = __fmaf_ru(to_f32_up(col[static_cast<size_t>(i - j) * n]), to_f32_up(col[static_cast<size_t>(j) * n]), ub);
+      ub = __fmaf_ru(to_f32_up(col[static_cast<size_t>(i - j) * n]), to_f32_up(zcol[static_cast<size_t>(j) * n]), ub);
   return ub;
 }
 
 // Lemma-initialize bound + selection over all vertices. LF = L when L <= 16, else 0 (any L).
 template <typename T, int LF>
-__global__ void __launch_bounds__(kThreads) ub_select(const T* __restrict__ mtab, int32_t L, int32_t n,
+__global__ void __launch_bounds__(kThreads) ub_select(const T* __restrict__ mtab, const T* __restrict__ ztab,
+                                                     int32_t L, int32_t n,
                                                      const uint32_t* __restrict__ mask,
                                                      const Stale* __restrict__ stale, int32_t step,
                                                      const int32_t* __restrict__ perm, float* __restrict__ sel_v,
@@ -228,7 +273,7 @@ __global__ void __launch_bounds__(kThreads) ub_select(const T* __restrict__ mtab
       const int32_t x = xr < n ? xr : n - 1;
       const bool inS = (__ldg(mask + (x >> 5)) >> (x & 31)) & 1u;
       const Stale st = stale[x];
-      float ub = LF > 0 ? ub_fixed<T, (LF > 0 ? LF : 1)>(mtab + x, n) : ub_any<T>(mtab + x, n, L);
+      float ub = LF > 0 ? ub_fixed<T, (LF > 0 ? LF : 1)>(mtab + x, ztab + x, n) : ub_any<T>(mtab + x, ztab + x, n, L);
       if (st.step >= 0 && st.ub < ub) ub = st.ub;
       b[k] = ub;
       bool in_sample = true;
@@ -264,19 +309,20 @@ __global__ void __launch_bounds__(kThreads) ub_select(const T* __restrict__ mtab
 }
 
 template <typename T>
-cudaError_t launch_ub_select(int nb, cudaStream_t s, const T* mtab, int32_t L, int32_t n, const uint32_t* mask,
+cudaError_t launch_ub_select(int nb, cudaStream_t s, const T* mtab, const T* ztab, int32_t L, int32_t n,
+                             const uint32_t* mask,
                              const Stale* stale, int32_t step, const int32_t* perm, float* sel_v, int* sel_id,
                              int32_t* zero_min, const Sampling& smp, int32_t* sampled) {
 #define GW_UB(LL)                                                                                          \
   case LL:                                                                                                 \
-    ub_select<T, LL><<<nb, kThreads, 0, s>>>(mtab, L, n, mask, stale, step, perm, sel_v, sel_id, zero_min, smp, \
+    ub_select<T, LL><<<nb, kThreads, 0, s>>>(mtab, ztab, L, n, mask, stale, step, perm, sel_v, sel_id, zero_min, smp, \
                                              sampled);                                                     \
     break;
   switch (L) {
     GW_UB(1) GW_UB(2) GW_UB(3) GW_UB(4) GW_UB(5) GW_UB(6) GW_UB(7) GW_UB(8)
     GW_UB(9) GW_UB(10) GW_UB(11) GW_UB(12) GW_UB(13) GW_UB(14) GW_UB(15) GW_UB(16)
     default:
-      ub_select<T, 0><<<nb, kThreads, 0, s>>>(mtab, L, n, mask, stale, step, perm, sel_v, sel_id, zero_min, smp,
+      ub_select<T, 0><<<nb, kThreads, 0, s>>>(mtab, ztab, L, n, mask, stale, step, perm, sel_v, sel_id, zero_min, smp,
                                               sampled);
   }
 #undef GW_UB
@@ -343,24 +389,42 @@ struct GreedyCtx {
   double* d_gains;
   SelOut* h_out;
   int64_t sweeps = 0;
+  size_t tab_off = 0;  // elements: the phi^miss table in use (lookahead level) within ws.mtab
 };
 
 // Issues init + L sweeps + column-sum reduction on c.s. ev (optional): two external events
 // around each sweep (graph capture).
-gedwalk_status issue_sweeps(GreedyCtx& c, int mode, int cols, bool profile, const std::vector<cudaEvent_t>* ev) {
+// rev (directed graphs, MODE_FUSED with one column): the sweeps run on the reverse CSR and fill
+// the psi^miss table instead.
+gedwalk_status issue_sweeps(GreedyCtx& c, int mode, int cols, bool profile, const std::vector<cudaEvent_t>* ev,
+                            bool rev) {
   Graph& g = c.g;
   Workspace& ws = c.ws;
   const bool fp64 = c.r.fp64;
   const int first = mode == MODE_FUSED ? 1 : 0;
-  void* m0 = mode == MODE_FUSED ? ws.mtab.p : nullptr;
-  if (fp64)
+  DevBuf& tab = rev ? ws.ztab : ws.mtab;
+  const size_t off = rev ? 0 : c.tab_off;  // elements
+  const int64_t look_stride = static_cast<int64_t>(c.L + 1) * g.n;  // elements between level tables
+  void* m0 = mode == MODE_FUSED ? tab.as<char>() + off * c.es : nullptr;
+  if (mode == MODE_LOOK) {
+    if (fp64)
+      look_init<double><<<blocks_for(g.n), 256, 0, c.s>>>(ws.mtab.as<double>(), look_stride, ws.x0.as<double>(),
+                                                          cols / 2, c.d_cand, ws.mask.as<uint32_t>(), g.n,
+                                                          g.weighted ? g.rs_d.as<double>() : nullptr);
+    else
+      look_init<float><<<blocks_for(g.n), 256, 0, c.s>>>(ws.mtab.as<float>(), look_stride, ws.x0.as<float>(),
+                                                         cols / 2, c.d_cand, ws.mask.as<uint32_t>(), g.n,
+                                                         g.weighted ? g.rs_f.as<float>() : nullptr);
+  } else if (fp64)
     greedy_init<double><<<blocks_for(g.n), 256, 0, c.s>>>(static_cast<double*>(m0), ws.x0.as<double>(), cols, first,
-                                                           c.d_cand, ws.mask.as<uint32_t>(), g.n);
+                                                           c.d_cand, ws.mask.as<uint32_t>(), g.n,
+                                                           g.weighted ? g.rs_d.as<double>() : nullptr);
   else
     greedy_init<float><<<blocks_for(g.n), 256, 0, c.s>>>(static_cast<float*>(m0), ws.x0.as<float>(), cols, first,
-                                                          c.d_cand, ws.mask.as<uint32_t>(), g.n);
+                                                          c.d_cand, ws.mask.as<uint32_t>(), g.n,
+                                                          g.weighted ? g.rs_f.as<float>() : nullptr);
   GW_KCHECK();
-  SweepArgs a = base_args(g, ws);
+  SweepArgs a = rev ? base_args_rev(g, ws) : base_args(g, ws);
   a.alpha = c.r.alpha;
   a.cand = c.d_cand;
   void* cur = ws.x0.p;
@@ -369,9 +433,11 @@ gedwalk_status issue_sweeps(GreedyCtx& c, int mode, int cols, bool profile, cons
     a.X = cur;
     a.Y = nxt;
     a.accumulate = t > 1;
-    char* row = ws.mtab.as<char>() + static_cast<size_t>(t) * g.n * c.es;
+    char* row = tab.as<char>() + (off + static_cast<size_t>(t) * g.n) * c.es;
     if (mode == MODE_FUSED) a.Mout = row;
+    else if (mode == MODE_LOOK) a.Mout = tab.as<char>() + static_cast<size_t>(t) * g.n * c.es;
     else a.Min = row;
+    a.mout_stride = look_stride;
     // external events bracket the whole run of sweeps (event nodes between kernel nodes cost
     // a few microseconds each)
     if (ev && t == 1) GW_CUDA(cudaEventRecordWithFlags((*ev)[0], c.s, cudaEventRecordExternal));
@@ -380,7 +446,7 @@ gedwalk_status issue_sweeps(GreedyCtx& c, int mode, int cols, bool profile, cons
     std::swap(cur, nxt);
   }
   const int nsum = sweep_sums(mode, cols);
-  if (nsum > 0) GW_TRY(reduce_slots(g, ws, nsum, c.d_gains, c.s));
+  if (nsum > 0) GW_TRY(reduce_slots(g, ws, nsum, c.d_gains, c.s, rev));
   return GEDWALK_OK;
 }
 
@@ -392,7 +458,7 @@ uint64_t mix_key(uint64_t h, uint64_t v) {
 // Runs L sweeps. mode MODE_FUSED (column 0 = phi^miss, table rows written) or MODE_CAND. On a
 // capturable stream the sequence is captured once per configuration (on its second use) and
 // replayed as a CUDA graph.
-gedwalk_status run_sweeps(GreedyCtx& c, int mode, int cols, const std::vector<int32_t>& cand) {
+gedwalk_status run_sweeps(GreedyCtx& c, int mode, int cols, const std::vector<int32_t>& cand, bool rev = false) {
   Graph& g = c.g;
   Workspace& ws = c.ws;
   const bool fp64 = c.r.fp64;
@@ -404,10 +470,12 @@ gedwalk_status run_sweeps(GreedyCtx& c, int mode, int cols, const std::vector<in
   GW_TRY(ws.x1.ensure(vbytes, c.s));
   GW_TRY(ensure_sweep_scratch(g, ws, cols, fp64, c.s));
   c.sweeps += c.L;
-  if (c.s == nullptr || g.plan.num_units == 0) return issue_sweeps(c, mode, cols, true, nullptr);
-  SweepGraph& sg = ws.graphs[mode == MODE_FUSED ? 0 : 1];
+  if (c.s == nullptr || g.plan.num_units == 0) return issue_sweeps(c, mode, cols, true, nullptr, rev);
+  SweepGraph& sg = ws.graphs[rev ? 2 : mode == MODE_LOOK ? 3 : mode == MODE_FUSED ? 0 : 1];
   uint64_t key = 0;
-  for (uint64_t v : {uint64_t(mode), uint64_t(cols), uint64_t(fp64), uint64_t(c.L), uint64_t(g.n),
+  for (uint64_t v : {uint64_t(mode), uint64_t(cols), uint64_t(fp64), uint64_t(c.L), uint64_t(g.n), uint64_t(rev),
+                     uint64_t(c.tab_off),
+                     reinterpret_cast<uint64_t>(ws.ztab.p),
                      reinterpret_cast<uint64_t>(&g), reinterpret_cast<uint64_t>(c.s),
                      reinterpret_cast<uint64_t>(ws.x0.p), reinterpret_cast<uint64_t>(ws.x1.p),
                      reinterpret_cast<uint64_t>(ws.mtab.p), reinterpret_cast<uint64_t>(ws.slots.p),
@@ -424,11 +492,11 @@ gedwalk_status run_sweeps(GreedyCtx& c, int mode, int cols, const std::vector<in
     sg.key = key;
   }
   if (!sg.exec) {
-    if (sg.uses++ < 1) return issue_sweeps(c, mode, cols, true, nullptr);  // set-up happens outside capture
+    if (sg.uses++ < 1) return issue_sweeps(c, mode, cols, true, nullptr, rev);  // set-up happens outside capture
     sg.ev.assign(2, nullptr);
     for (cudaEvent_t& e : sg.ev) GW_CUDA(cudaEventCreate(&e));
     GW_CUDA(cudaStreamBeginCapture(c.s, cudaStreamCaptureModeThreadLocal));
-    const gedwalk_status st = issue_sweeps(c, mode, cols, false, &sg.ev);
+    const gedwalk_status st = issue_sweeps(c, mode, cols, false, &sg.ev, rev);
     cudaGraph_t graph = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(c.s, &graph);
     if (st != GEDWALK_OK || ce != cudaSuccess || !graph) {
@@ -446,7 +514,7 @@ gedwalk_status run_sweeps(GreedyCtx& c, int mode, int cols, const std::vector<in
     }
     sg.kernels = 1 + c.L + (sweep_sums(mode, cols) > 0 ? 2 : 0);
     sg.sweeps = c.L;
-    sg.bytes = sweep_bytes(mode, fp64, cols, g.n, g.nnz);
+    sg.bytes = sweep_bytes(mode, fp64, cols, g.n, g.nnz, g.weighted);
     sg.prof_key = (mode * 1000 + cols) * 2 + (fp64 ? 1 : 0);
   }
   GW_CUDA(cudaGraphLaunch(sg.exec, c.s));
@@ -495,12 +563,27 @@ gedwalk_status maximize_impl(Graph& g, Workspace& ws, int32_t k, const Resolved&
   // phi^miss + speculative candidates. Every gather costs one L2 sector whatever the row
   // width, so narrow rows are cheapest; one speculative candidate certifies most steps (a
   // miss costs one extra candidate batch). GEDWALK_SPEC_COLS (2, 4 or 8) overrides.
-  int cols_fused = 2;
+  const bool adaptive = (flags & GEDWALK_ADAPTIVE_L) != 0;
+  // The adaptive variant certifies the best two exact gains (u and v of its separation test),
+  // so it speculates on three candidates.
+  int cols_fused = adaptive ? 4 : 2;
   if (const char* e = getenv("GEDWALK_SPEC_COLS")) {
     const int v = atoi(e);
     if (v == 2 || v == 4 || (v == 8 && !r.fp64)) cols_fused = v;
   }
-  const int n_spec = cols_fused - 1;
+  // Lookahead (plain greedy on an undirected graph): one run of sweeps carries `levels` steps,
+  // level d under S + {c_1..c_d} with the guessed winners c_d; a step whose winner was guessed
+  // needs no sweep of its own. GEDWALK_LOOKAHEAD (1 = off, 2, 4) overrides the default of 2.
+  int levels = 1;
+  if (!(flags & (GEDWALK_ADAPTIVE_L | GEDWALK_STOCHASTIC | GEDWALK_GAINS_ALL)) && !g.directed) {
+    levels = 2;
+    if (const char* e = getenv("GEDWALK_LOOKAHEAD")) {
+      const int v = atoi(e);
+      if (v == 1 || v == 2 || (v == 4 && !r.fp64)) levels = v;
+    }
+  }
+  const bool look = levels > 1;
+  const int n_spec = look ? levels : cols_fused - 1;
   const int cols_cand = r.fp64 ? 4 : 8;
   const int cols_all = r.fp64 ? 8 : 16;
   const double tol = r.fp64 ? 1e-11 : 1e-5;  // relative inflation of bounds against rounding
@@ -509,21 +592,44 @@ gedwalk_status maximize_impl(Graph& g, Workspace& ws, int32_t k, const Resolved&
   if (stochastic && (gains_all || !init_int.empty()))
     return fail(GEDWALK_ERR_INVALID, "stochastic greedy cannot be combined with GEDWALK_GAINS_ALL or an init group");
   if (stochastic && !(r.eta > 0.0 && r.eta < 1.0)) return fail(GEDWALK_ERR_INVALID, "eta must lie in (0, 1)");
+  if (adaptive && (gains_all || stochastic || !init_int.empty()))
+    return fail(GEDWALK_ERR_INVALID,
+                "GEDWALK_ADAPTIVE_L cannot be combined with GEDWALK_GAINS_ALL, GEDWALK_STOCHASTIC or an init group");
+  if (adaptive && !(r.eps > 0.0)) return fail(GEDWALK_ERR_INVALID, "GEDWALK_ADAPTIVE_L needs epsilon (L must be 0)");
   // stochastic greedy: about m vertices outside S are sampled per step (Appendix D)
   const double sample_m = std::ceil(static_cast<double>(g.n) / std::max(k, 1) * std::log(1.0 / (stochastic ? r.eta : 0.5)));
-  const int32_t L = r.L;
-  ws.st_evals = ws.st_batches = ws.st_sweeps = ws.st_spec_miss = 0;
+  // adaptive: l runs through the powers of two from 1; B_l < eps_sep separates any pair, and r.L
+  // (the first l with B_l < eps_sep) bounds the largest power reached.
+  const double eps_sep = r.eps;
+  int32_t ell_max = 1;
+  while (adaptive && ell_max < r.L) ell_max *= 2;
+  const int32_t L = adaptive ? ell_max : r.L;  // rows of the miss table
+  double coef = 0.0;  // B_l = coef * Wa_l (Eq. comb-bound, or Lemma spectral-bound)
+  if (adaptive) {
+    GW_TRY(bound_coef(g, r.alpha, r.bound_kind, s, &coef));
+    GW_TRY(ensure_totals(g, r.alpha, ell_max + 1, s));
+  }
+  auto bound_at = [&](int32_t l) { return coef * g.Wa[l]; };
+  ws.st_evals = ws.st_batches = ws.st_sweeps = ws.st_spec_miss = ws.st_sep_fail = 0;
+  ws.st_ell.clear();
 
-  GW_TRY(ws.mtab.ensure(static_cast<size_t>(L + 1) * g.n * es, s));
-  GW_TRY(zero_isolated_tail(g, ws.mtab.p, es, L, s));
+  const size_t tab_elems = static_cast<size_t>(L + 1) * g.n;  // one phi^miss table
+  GW_TRY(ws.mtab.ensure(tab_elems * levels * es, s));
+  for (int d = 0; d < levels; ++d) GW_TRY(zero_isolated_tail(g, ws.mtab.as<char>() + d * tab_elems * es, es, L, s));
+  if (g.directed) {
+    GW_TRY(ws.ztab.ensure(static_cast<size_t>(L + 1) * g.n * es, s));
+    GW_TRY(zero_isolated_tail(g, ws.ztab.p, es, L, s));
+  }
   GW_TRY(ws.stale.ensure(static_cast<size_t>(g.n) * sizeof(Stale), s));
   GW_TRY(ws.sel.ensure(static_cast<size_t>(kSelBlocks) * kTopK * 8, s));
   GW_TRY(ws.small.ensure(sizeof(SelOut) + 16 * sizeof(int32_t) + 16 * sizeof(double) + 256, s));
-  GW_TRY(ws.ensure_pinned(sizeof(SelOut) + 64));
+  GW_TRY(ws.ensure_pinned(sizeof(SelOut) + 64 + 8 * sizeof(double)));
+  double* h_look = reinterpret_cast<double*>(static_cast<char*>(ws.pinned) + sizeof(SelOut) + 64);
   GW_TRY(upload_mask(g, ws, init_int, s));
   GW_CUDA(cudaMemsetAsync(ws.stale.p, 0xff, static_cast<size_t>(g.n) * sizeof(Stale), s));  // step -1, ub NaN
 
-  GreedyCtx c{g, ws, r, s, L, es};
+  GreedyCtx c{g, ws, r, s, adaptive ? 1 : r.L, es};
+  const int need = adaptive ? 2 : 1;
   c.d_out = ws.small.as<SelOut>();
   c.d_cand = reinterpret_cast<int32_t*>(c.d_out + 1);
   c.d_gains = reinterpret_cast<double*>(c.d_cand + 16);
@@ -540,6 +646,42 @@ gedwalk_status maximize_impl(Graph& g, Workspace& ws, int32_t k, const Resolved&
   }
   std::vector<int32_t> S_all = init_int;
   std::vector<Cand> spec;  // next step's speculative candidates (internal ids)
+  int look_lvl = -1;                  // lookahead level of the next step (-1: none valid)
+  std::vector<int32_t> look_c;        // guessed winners c_1..c_levels of the last lookahead run
+  double look_g[8] = {0};             // their exact gains, each under S + {c_1..c_d}
+  // The step's sample: vertex v (caller id) is drawn when hash(seed, step, v) < thr, i.e. with
+  // probability p = m / |V \ S| (all of V \ S when p >= 1).
+  auto sampling_for = [&](int32_t st) {
+    Sampling smp{~0ull, r.seed, static_cast<uint32_t>(st)};
+    if (stochastic) {
+      const double p = sample_m / static_cast<double>(g.n - st);
+      const double scaled = p * 18446744073709551616.0;
+      if (p < 1.0 && scaled < 18446744073709551615.0) smp.thr = static_cast<uint64_t>(scaled);
+    }
+    return smp;
+  };
+  const int nb_sel = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(kSelBlocks, (int64_t(g.n) + 1023) / 1024)));
+  // One bound + selection pass into c.d_out / c.h_out; `step` decides which stale gains are exact.
+  auto select_pass = [&](int32_t st, const Sampling& smp) -> gedwalk_status {
+    reset_selection<<<1, 1, 0, s>>>(c.d_out);
+    if (r.fp64)
+      GW_CUDA(launch_ub_select<double>(nb_sel, s, ws.mtab.as<double>() + c.tab_off,
+                                       g.directed ? ws.ztab.as<double>() : ws.mtab.as<double>() + c.tab_off, c.L, g.n, ws.mask.as<uint32_t>(), stale, st,
+                                       g.perm_d.as<int32_t>(), sel_v, sel_id, &c.d_out->zero_min_caller, smp,
+                                       &c.d_out->sampled));
+    else
+      GW_CUDA(launch_ub_select<float>(nb_sel, s, ws.mtab.as<float>() + c.tab_off,
+                                      g.directed ? ws.ztab.as<float>() : ws.mtab.as<float>() + c.tab_off, c.L, g.n, ws.mask.as<uint32_t>(), stale, st,
+                                      g.perm_d.as<int32_t>(), sel_v, sel_id, &c.d_out->zero_min_caller, smp,
+                                      &c.d_out->sampled));
+    count_launch();
+    select_merge<<<1, kMergeThreads, 0, s>>>(sel_v, sel_id, nb_sel * kTopK, c.d_out);
+    GW_KCHECK();
+    GW_CUDA(cudaMemcpyAsync(c.h_out, c.d_out, sizeof(SelOut), cudaMemcpyDeviceToHost, s));
+    GW_CUDA(cudaStreamSynchronize(s));
+    read_graph_timing(ws);
+    return GEDWALK_OK;
+  };
 
   for (int32_t step = 0; step < k; ++step) {
     std::vector<Cand> E;  // evaluated with the current S
@@ -565,83 +707,122 @@ gedwalk_status maximize_impl(Graph& g, Workspace& ws, int32_t k, const Resolved&
         }
       }
     } else {
-      Sampling smp{~0ull, r.seed, static_cast<uint32_t>(step)};
-      if (stochastic) {
-        const double p = sample_m / static_cast<double>(g.n - step);
-        const double scaled = p * 18446744073709551616.0;
-        if (p < 1.0 && scaled < 18446744073709551615.0) smp.thr = static_cast<uint64_t>(scaled);
-        spec.clear();  // the next step draws a new sample: no speculation
-      }
-      // 1. fused sweeps: phi^miss under S plus the speculative candidates
-      std::vector<int32_t> sc;
-      for (const Cand& e : spec) sc.push_back(e.v);
-      const int cf = sc.empty() ? 1 : cols_fused;
-      GW_TRY(run_sweeps(c, MODE_FUSED, cf, sc));
-      std::vector<int32_t> last = sc;
-      bool first_batch = true;
-      for (;;) {
-        if (!last.empty()) {
-          update_stale<<<1, 32, 0, s>>>(stale, c.d_cand, c.d_gains, static_cast<int>(last.size()), step,
-                                        c.d_out->gains);
+      Sampling smp = sampling_for(step);
+      for (;;) {  // one attempt per walk length (a single attempt unless adaptive)
+        // 1. fused sweeps: phi^miss under S plus the speculative candidates (on a directed graph
+        // first psi^miss, the walks of the other orientation, on the reverse CSR)
+        std::vector<int32_t> sc, last;
+        E.clear();
+        bool look_run = false;
+        if (look && look_lvl > 0 && look_lvl < levels && look_c[look_lvl] >= 0) {
+          // the last winner was this level's predecessor: its table and its candidate's exact gain
+          // were computed with the current S
+          const int32_t cl = look_c[look_lvl];
+          c.tab_off = static_cast<size_t>(look_lvl) * tab_elems;
+          set_stale<<<1, 1, 0, s>>>(stale, cl, look_g[look_lvl], step, c.d_out->gains);
           GW_KCHECK();
+          E.push_back(Cand{look_g[look_lvl], cl, g.perm[cl]});
+          sc.push_back(cl);
+        } else if (look && !spec.empty()) {
+          sc.assign(levels, -1);
+          for (size_t j = 0; j < spec.size() && j < static_cast<size_t>(levels); ++j) sc[j] = spec[j].v;
+          c.tab_off = 0;
+          GW_TRY(run_sweeps(c, MODE_LOOK, 2 * levels, sc));
+          GW_CUDA(cudaMemcpyAsync(h_look, c.d_gains, sizeof(double) * levels, cudaMemcpyDeviceToHost, s));
+          look_lvl = 0;
+          look_c = sc;
+          look_run = true;
+          last.push_back(sc[0]);  // level 0's candidate is exact now; deeper levels wait for theirs
+          for (int32_t v : sc) ws.st_evals += v >= 0;
+          ++ws.st_batches;
+          sc.resize(1);
+        } else {
+          if (g.directed) GW_TRY(run_sweeps(c, MODE_FUSED, 1, {}, true));
+          for (const Cand& e : spec) sc.push_back(e.v);
+          const int cf = sc.empty() ? 1 : cols_fused;
+          c.tab_off = 0;
+          look_lvl = -1;
+          GW_TRY(run_sweeps(c, MODE_FUSED, cf, sc));
+          last = sc;
         }
-        // 2. bound + selection pass
-        reset_selection<<<1, 1, 0, s>>>(c.d_out);
-        const int nb = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(kSelBlocks, (int64_t(g.n) + 1023) / 1024)));
-        if (r.fp64)
-          GW_CUDA(launch_ub_select<double>(nb, s, ws.mtab.as<double>(), L, g.n, ws.mask.as<uint32_t>(), stale, step,
-                                           g.perm_d.as<int32_t>(), sel_v, sel_id, &c.d_out->zero_min_caller, smp,
-                                           &c.d_out->sampled));
-        else
-          GW_CUDA(launch_ub_select<float>(nb, s, ws.mtab.as<float>(), L, g.n, ws.mask.as<uint32_t>(), stale, step,
-                                          g.perm_d.as<int32_t>(), sel_v, sel_id, &c.d_out->zero_min_caller, smp,
-                                          &c.d_out->sampled));
-        count_launch();
-        select_merge<<<1, kMergeThreads, 0, s>>>(sel_v, sel_id, nb * kTopK, c.d_out);
-        GW_KCHECK();
-        GW_CUDA(cudaMemcpyAsync(c.h_out, c.d_out, sizeof(SelOut), cudaMemcpyDeviceToHost, s));
-        GW_CUDA(cudaStreamSynchronize(s));
-        read_graph_timing(ws);
-        if (smp.thr != ~0ull && c.h_out->sampled == 0) {  // empty sample: all of V \ S competes
-          smp.thr = ~0ull;
-          continue;
-        }
-        for (size_t j = 0; j < last.size(); ++j) {
-          Cand e{c.h_out->gains[j], last[j], g.perm[last[j]]};
-          E.push_back(e);
-          if (best.v < 0 || cand_before(e, best)) best = e;
-        }
-        ws.st_evals += static_cast<int64_t>(last.size());
-        if (!last.empty()) ++ws.st_batches;
-        // 3. certify
+        bool first_batch = true;
+        std::vector<Cand> X;  // exact values for the current S, best first
         std::vector<int32_t> top;
-        for (int j = 0; j < kTopK; ++j)
-          if (c.h_out->id[j] != INT_MAX) top.push_back(c.h_out->id[j]);
-        const int32_t zmin = c.h_out->zero_min_caller;
-        if (zmin != INT_MAX && (best.v < 0 || best.g < 0.0 || (best.g == 0.0 && zmin < best.caller)))
-          best = Cand{0.0, g.inv[zmin], zmin};
-        const bool certified =
-            top.empty() || (best.v >= 0 && static_cast<double>(c.h_out->val[0]) * (1.0 + tol) < best.g);
-        if (certified) {
-          // speculative candidates for the next step: best remaining bounds, exact or not
-          std::vector<Cand> pool;
-          for (const Cand& e : E)
-            if (e.v != best.v) pool.push_back(e);
-          for (size_t j = 0; j < top.size(); ++j)
-            pool.push_back(Cand{static_cast<double>(c.h_out->val[j]), top[j], g.perm[top[j]]});
-          std::sort(pool.begin(), pool.end(), cand_before);
-          spec.clear();
-          for (const Cand& e : pool) {
-            if (static_cast<int>(spec.size()) == n_spec) break;
-            if (e.g > 0.0) spec.push_back(e);
+        for (;;) {
+          if (!last.empty()) {
+            update_stale<<<1, 32, 0, s>>>(stale, c.d_cand, c.d_gains, static_cast<int>(last.size()), step,
+                                          c.d_out->gains);
+            GW_KCHECK();
           }
-          break;
+          // 2. bound + selection pass
+          GW_TRY(select_pass(step, smp));
+          if (smp.thr != ~0ull && c.h_out->sampled == 0) {  // empty sample: all of V \ S competes
+            smp.thr = ~0ull;
+            continue;
+          }
+          if (look_run) {  // the gains of every level arrived with the first synchronisation
+            for (int d = 0; d < levels; ++d) look_g[d] = h_look[d];
+            look_run = false;
+            for (size_t j = 0; j < last.size(); ++j) E.push_back(Cand{c.h_out->gains[j], last[j], g.perm[last[j]]});
+          } else {
+            for (size_t j = 0; j < last.size(); ++j) E.push_back(Cand{c.h_out->gains[j], last[j], g.perm[last[j]]});
+            ws.st_evals += static_cast<int64_t>(last.size());
+            if (!last.empty()) ++ws.st_batches;
+          }
+          // 3. certify: the first `need` exact values beat every bound not yet evaluated (a zero
+          // bound is an exact zero gain; the lowest such caller id stands for all of them)
+          top.clear();
+          for (int j = 0; j < kTopK; ++j)
+            if (c.h_out->id[j] != INT_MAX) top.push_back(c.h_out->id[j]);
+          X = E;
+          const int32_t zmin = c.h_out->zero_min_caller;
+          if (zmin != INT_MAX) X.push_back(Cand{0.0, g.inv[zmin], zmin});
+          std::sort(X.begin(), X.end(), cand_before);
+          const double ub0 = top.empty() ? -1.0 : static_cast<double>(c.h_out->val[0]) * (1.0 + tol);
+          const bool certified =
+              top.empty() || (static_cast<int>(X.size()) >= need && ub0 < X[need - 1].g);
+          if (certified) break;
+          if (first_batch && !sc.empty()) ++ws.st_spec_miss;
+          first_batch = false;
+          last.assign(top.begin(), top.begin() + std::min<size_t>(top.size(), cols_cand));
+          GW_TRY(run_sweeps(c, MODE_CAND, cols_cand, last));
         }
-        if (first_batch && !sc.empty()) ++ws.st_spec_miss;
-        first_batch = false;
-        last.assign(top.begin(), top.begin() + std::min<size_t>(top.size(), cols_cand));
-        GW_TRY(run_sweeps(c, MODE_CAND, cols_cand, last));
+        best = X.empty() ? Cand{-1.0, -1, INT_MAX} : X[0];
+        // speculative candidates for the next step (or attempt): best remaining values, exact or not
+        std::vector<Cand> pool(X.begin() + (X.empty() ? 0 : 1), X.end());
+        for (size_t j = 0; j < top.size(); ++j)
+          pool.push_back(Cand{static_cast<double>(c.h_out->val[j]), top[j], g.perm[top[j]]});
+        std::sort(pool.begin(), pool.end(), cand_before);
+        spec.clear();
+        for (const Cand& e : pool) {
+          if (static_cast<int>(spec.size()) == n_spec) break;
+          if (e.g > 0.0) spec.push_back(e);
+        }
+        if (!adaptive) break;
+        // separation test (Algorithm 2): u = best is taken when L(u) > U(v) - eps_sep, where v is
+        // the best of the rest and U = L + B_l. With every other vertex unevaluated the rest has
+        // zero gains; with u the last vertex outside S there is no v.
+        const int32_t left = g.n - static_cast<int32_t>(S_all.size());
+        const double gv = X.size() >= 2 ? X[1].g : 0.0;
+        if (left <= 1 || best.g > (gv + bound_at(c.L)) - eps_sep) break;
+        ++ws.st_sep_fail;
+        if (2 * c.L > ell_max) return fail(GEDWALK_ERR_DEVICE, "walk length passed %d without separation", ell_max);
+        c.L *= 2;
+        // the bounds of the shorter length are no upper bounds for the longer one: reset them
+        GW_CUDA(cudaMemsetAsync(ws.stale.p, 0xff, static_cast<size_t>(g.n) * sizeof(Stale), s));
+        spec.clear();  // u and the runners-up are the best guesses at the longer length
+        for (const Cand& e : X) {
+          if (static_cast<int>(spec.size()) == n_spec) break;
+          if (e.g > 0.0) spec.push_back(e);
+        }
       }
+    }
+    ws.st_ell.push_back(c.L);
+    if (look) {  // the next level is valid only when this step took the vertex it assumed
+      if (look_lvl >= 0 && best.v == look_c[look_lvl] && look_lvl + 1 < levels && look_c[look_lvl + 1] >= 0)
+        ++look_lvl;
+      else
+        look_lvl = -1;
     }
     if (best.v < 0) return fail(GEDWALK_ERR_INVALID, "no vertex left to add");
     group[step] = best.caller;
@@ -652,6 +833,19 @@ gedwalk_status maximize_impl(Graph& g, Workspace& ws, int32_t k, const Resolved&
     hmask[w >> 5] |= 1u << (w & 31);
     GW_CUDA(cudaMemcpyAsync(ws.mask.as<uint32_t>() + (w >> 5), &hmask[w >> 5], 4, cudaMemcpyHostToDevice, s));
     spec.erase(std::remove_if(spec.begin(), spec.end(), [&](const Cand& e) { return e.v == w; }), spec.end());
+    if (stochastic && step + 1 < k) {
+      // The next step draws a new sample, so its speculative candidates are the best bounds
+      // inside that sample: bounds and exact gains under the current S stay upper bounds once
+      // w joins S (submodularity), which is all a speculative choice needs.
+      spec.clear();
+      const Sampling nxt = sampling_for(step + 1);
+      GW_TRY(select_pass(step + 1, nxt));
+      for (int j = 0; j < kTopK && static_cast<int>(spec.size()) < n_spec; ++j) {
+        const int32_t id = c.h_out->id[j];
+        if (id == INT_MAX || !(c.h_out->val[j] > 0.0f)) break;
+        spec.push_back(Cand{static_cast<double>(c.h_out->val[j]), id, g.perm[id]});
+      }
+    }
   }
   ws.st_sweeps = c.sweeps;
   if (score) {
@@ -731,12 +925,27 @@ gedwalk_status gedwalk_maximize(gedwalk_graph_t h, int32_t k, const gedwalk_para
   g->st_batches = g->ws.st_batches;
   g->st_sweeps = g->ws.st_sweeps;
   g->st_spec_miss = g->ws.st_spec_miss;
+  g->st_ell = g->ws.st_ell;
+  g->st_sep_fail = g->ws.st_sep_fail;
   for (int32_t j = 0; j < k; ++j) {
     group[j] = grp[j];
     if (gains) gains[j] = gn[j];
   }
   if (score) *score = sc;
-  if (L_used) *L_used = r.L;
+  if (L_used) *L_used = (p->flags & GEDWALK_ADAPTIVE_L) ? (g->st_ell.empty() ? 1 : g->st_ell.back()) : r.L;
+  return GEDWALK_OK;
+}
+
+gedwalk_status gedwalk_maximize_lengths(gedwalk_graph_t h, int32_t* ell, int32_t cap, int32_t* count,
+                                        int64_t* separation_failures) {
+  if (!h) return fail(GEDWALK_ERR_INVALID, "graph is NULL");
+  if (cap < 0 || (cap > 0 && !ell)) return fail(GEDWALK_ERR_INVALID, "ell is NULL or cap < 0");
+  Graph* g = G(h);
+  std::lock_guard<std::mutex> lk(g->mu);
+  const int32_t m = static_cast<int32_t>(g->st_ell.size());
+  for (int32_t j = 0; j < std::min(m, cap); ++j) ell[j] = g->st_ell[j];
+  if (count) *count = m;
+  if (separation_failures) *separation_failures = g->st_sep_fail;
   return GEDWALK_OK;
 }
 

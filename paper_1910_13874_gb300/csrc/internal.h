@@ -87,7 +87,7 @@ constexpr int64_t kL1HubBytes = 160 * 1024;  // x rows per SM kept in L1 with hi
 struct Plan {
   int32_t num_units = 0;   // grid size: heavy slices first, then light units
   int32_t num_slices = 0;  // heavy slices (units [0, num_slices))
-  int32_t num_heavy = 0;   // heavy rows (new ids [0, num_heavy))
+  int32_t num_heavy = 0;   // heavy rows (degree > kHeavyDeg)
   int32_t num_slots = 0;   // num_units + num_heavy column-sum slots
   DevBuf units;            // int4[num_units]
   DevBuf heavy;            // int4[num_heavy]: {row, first slice, slice count, 0}
@@ -120,6 +120,8 @@ struct SweepGraph {
 struct Workspace {
   DevBuf x0, x1;     // walk vectors, [n][C]
   DevBuf mtab;       // phi^miss table, [(L+1)][n]
+  DevBuf ztab;       // directed graphs: psi^miss table (walks in the other orientation), [(L+1)][n]
+  DevBuf pvec;       // power iteration: three FP64 vectors and the statistics
   DevBuf partial;    // heavy-slice partial sums, [num_slices][C]
   DevBuf counters;   // heavy-row arrival counters, [num_heavy] (kept at 0 between launches)
   DevBuf slots;      // column-sum slots, [num_slots][C] doubles
@@ -131,7 +133,9 @@ struct Workspace {
   DevBuf members;    // batched scoring: member ids / group ids / accumulators
   DevBuf pinned_dummy;
   int64_t st_evals = 0, st_batches = 0, st_sweeps = 0, st_spec_miss = 0;  // last maximize
-  SweepGraph graphs[2];             // captured greedy sequences: fused, candidate batch
+  std::vector<int32_t> st_ell;  // last maximize: the walk length of each step
+  int64_t st_sep_fail = 0;      // last maximize: failed separation tests (l doublings)
+  SweepGraph graphs[4];             // captured greedy sequences: fused, candidate batch, reverse, lookahead
   cudaStream_t own_stream = nullptr;  // capturable stream used when the caller passes stream 0
   cudaEvent_t order_ev = nullptr;     // orders own_stream after the caller's stream
   std::vector<uint8_t> host_small;  // staging
@@ -149,6 +153,21 @@ struct Graph {
   int32_t dmax = 0;
   int32_t n_active = 0;     // rows with at least one entry; isolated rows are [n_active, n)
   double alpha_default = 0;
+  // Weighted walks (Section 5.4) with vertex-separable weights w(v,u) = s_v s_u: rs_* hold s by
+  // new id (empty for an unweighted graph). delta is the degree of the combinatorial bound:
+  // d_max, or the largest weighted degree max_v s_v sum_u s_u.
+  bool weighted = false;
+  double delta = 0;
+  DevBuf rs_f, rs_d;
+  // Directed graphs (Section 2): rp/ci/plan hold the successor lists; the reverse CSR (row v: the
+  // u with an arc u -> v) serves the sweeps that count walks in the other orientation (psi of
+  // Lemma initialize, the walk-total table of batched scoring).
+  bool directed = false;
+  DevBuf rp_r, ci_r;
+  Plan plan_r;
+  std::vector<int32_t> deg_r;
+  // certified upper bound of sigma_max (0: not computed) and the last Rayleigh estimate
+  double sigma_up = 0.0, sigma_lo = 0.0;
   DevBuf rp, ci;            // relabelled CSR (new ids), ci padded by 4 entries
   DevBuf perm_d;            // int32[n]: new -> caller id
   std::vector<int32_t> perm;  // new -> caller id
@@ -156,7 +175,8 @@ struct Graph {
   std::vector<int32_t> deg;   // degree by new id
   Plan plan;
 
-  // alpha-scaled walk totals t_r = alpha A t_{r-1}, t_0 = 1 (FP64, [rows][n]) and sums Wa[r]
+  // alpha-scaled walk totals t_r = alpha A t_{r-1}, t_0 = 1 (FP64, [rows][n]; on a weighted graph
+  // the rows hold s * t_r, the form the sweeps gather) and their sums Wa[r] = 1^T t_r
   double tt_alpha = -1.0;
   int32_t tt_rows = 0;
   DevBuf ttab;
@@ -168,6 +188,7 @@ struct Graph {
     double alpha, eps;
     int32_t L;
     double bound;
+    int32_t kind;  // the tail bound used
   };
   std::vector<Trunc> trunc_cache;
 
@@ -177,6 +198,8 @@ struct Graph {
 
   // statistics of the last maximize
   int64_t st_evals = 0, st_batches = 0, st_sweeps = 0, st_spec_miss = 0;
+  std::vector<int32_t> st_ell;
+  int64_t st_sep_fail = 0;
 
   Workspace ws;    // workspace of the synchronous API
   std::mutex mu;   // serialises calls on this handle
@@ -188,7 +211,8 @@ enum SweepMode : int {
   MODE_SCORE = 1,   // two-state hit/miss step, sums h
   MODE_FUSED = 2,   // greedy: column 0 = phi^miss under S, columns 1.. candidate columns
   MODE_CAND = 3,    // greedy: candidate columns only; candidate rows read phi^miss from a table
-  MODE_PLAIN = 4    // batched scoring: y = alpha A x, no mask
+  MODE_PLAIN = 4,   // batched scoring: y = alpha A x, no mask
+  MODE_LOOK = 5     // greedy lookahead: column pairs (phi^miss, candidate) under S + {c_1..c_d}
 };
 
 struct SweepArgs {
@@ -208,9 +232,15 @@ struct SweepArgs {
   double* slots;
   int32_t accumulate;
   void* Mout;
+  int64_t mout_stride;  // MODE_LOOK: elements between the phi^miss tables of consecutive levels
   const void* Min;
   const int32_t* cand;
   int32_t hub;  // rows [0, hub) of x are gathered with L1 retention priority (set by the launcher)
+  // Vertex scales s of a weighted graph (nullptr: unweighted). Vectors are then gathered in the
+  // scaled form x~ = s * x: (N x)(v) = s_v (A x~)(v) for N = diag(s) A diag(s), so the epilogue
+  // computes the true value alpha s_v (A x~)(v), sums it, and stores it times s_v.
+  const float* rs_f;
+  const double* rs_d;
 };
 
 // Profiling hooks around sweep launches (no-ops unless gedwalk_profile(1) was called).
@@ -223,7 +253,7 @@ void profile_add(double ms, double bytes, int key);
 void count_launches(int n);
 // Algorithmic bytes of one sweep launch: CSR once, x read once, y written once, plus the mask
 // and the phi^miss row where the mode reads or writes them.
-double sweep_bytes(int mode, bool fp64, int cols, int32_t n, int64_t nnz);
+double sweep_bytes(int mode, bool fp64, int cols, int32_t n, int64_t nnz, bool weighted = false);
 
 // Launches one sweep (instantiated for the supported (type, columns, mode) triples).
 gedwalk_status launch_sweep(int mode, bool fp64, int cols, const SweepArgs& a, cudaStream_t s, bool profile = true);
@@ -233,12 +263,14 @@ int sweep_sums(int mode, int cols);
 gedwalk_status launch_reduce_slots(const double* slots, int32_t num_slots, int32_t nsum, double* out,
                                    double* parts, cudaStream_t s);
 // The same over a workspace's slots after sweeps of width cols.
-gedwalk_status reduce_slots(Graph& g, Workspace& ws, int nsum, double* out, cudaStream_t s);
+gedwalk_status reduce_slots(Graph& g, Workspace& ws, int nsum, double* out, cudaStream_t s, bool rev = false);
 
 // Ensures workspace scratch for sweeps of width cols (partials, counters, slots).
 gedwalk_status ensure_sweep_scratch(Graph& g, Workspace& ws, int cols, bool fp64, cudaStream_t s);
 // Fills a SweepArgs with the graph/plan/scratch fields.
 SweepArgs base_args(Graph& g, Workspace& ws);
+// The same over the reverse CSR of a directed graph.
+SweepArgs base_args_rev(Graph& g, Workspace& ws);
 
 // ---------------------------------------------------------------- shared algorithm helpers
 struct Resolved {
@@ -249,13 +281,18 @@ struct Resolved {
   cudaStream_t stream;
   double eta = 0.1;    // stochastic greedy sample parameter
   uint64_t seed = 0;   // stochastic greedy seed
+  double eps = 0.0;    // the epsilon L was selected for (0 when L was forced)
+  int32_t bound_kind = 0;  // GEDWALK_BOUND_COMBINATORIAL or GEDWALK_BOUND_SPECTRAL
 };
 // Resolves alpha (0 -> default), L (from epsilon unless forced) for a given epsilon.
 gedwalk_status resolve(Graph& g, const gedwalk_params* p, double eps_override, Resolved* r);
 // Ensures the FP64 walk-total table holds rows 0..rows-1 for alpha.
 gedwalk_status ensure_totals(Graph& g, double alpha, int32_t rows, cudaStream_t s);
-// Truncation length from the combinatorial bound (device-side test); L=-1 if none <= Lcap.
-gedwalk_status truncation_length(Graph& g, double alpha, double eps, int32_t* L, double* bound, cudaStream_t s);
+// Truncation length from the chosen tail bound (device-side test).
+gedwalk_status truncation_length(Graph& g, double alpha, double eps, int32_t* L, double* bound, cudaStream_t s,
+                                 int32_t kind = 0);
+// Coefficient c of the tail bound B_l = c * Wa_l for (alpha, kind); NOT_CONVERGENT when it does not apply.
+gedwalk_status bound_coef(Graph& g, double alpha, int32_t kind, cudaStream_t s, double* coef);
 // Maps caller ids to internal ids with set semantics; INVALID on out-of-range ids.
 gedwalk_status map_group(const Graph& g, const int32_t* S, int32_t s_len, std::vector<int32_t>* out);
 // Uploads the S bitmask (internal ids) into ws.mask.

@@ -12,22 +12,25 @@ namespace {
 
 // X0[v] = (h_0(v), m_0(v)) = (1_S(v), 1_{V\S}(v))
 template <typename T>
-__global__ void init_two_state(T* __restrict__ X, const uint32_t* __restrict__ mask, int32_t n) {
+__global__ void init_two_state(T* __restrict__ X, const uint32_t* __restrict__ mask, int32_t n,
+                               const T* __restrict__ rs) {
   for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
     const bool inS = (mask[v >> 5] >> (v & 31)) & 1u;
-    X[2 * static_cast<size_t>(v)] = inS ? T(1) : T(0);
-    X[2 * static_cast<size_t>(v) + 1] = inS ? T(0) : T(1);
+    const T sv = rs ? rs[v] : T(1);  // weighted graph: the gathered vectors are scaled by s_v
+    X[2 * static_cast<size_t>(v)] = inS ? sv : T(0);
+    X[2 * static_cast<size_t>(v) + 1] = inS ? T(0) : sv;
   }
 }
 
 // Batched scoring, first-visit form. Column j of a block is m_0 = 1_{V \ S_j}.
 // Isolated rows (r >= n_active) hold 0: the sweeps never write them and nothing gathers them,
 // so they read as the (zero) first-visit counts of such vertices.
-__global__ void init_batch(float* __restrict__ X, int32_t n, int32_t n_active, int32_t cols, int32_t active) {
+__global__ void init_batch(float* __restrict__ X, int32_t n, int32_t n_active, int32_t cols, int32_t active,
+                           const float* __restrict__ rs) {
   const size_t total = static_cast<size_t>(n) * cols;
   const size_t live = static_cast<size_t>(n_active) * cols;
   for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < total; i += size_t(gridDim.x) * blockDim.x)
-    X[i] = (i < live && static_cast<int32_t>(i % cols) < active) ? 1.0f : 0.0f;
+    X[i] = (i < live && static_cast<int32_t>(i % cols) < active) ? (rs ? rs[i / cols] : 1.0f) : 0.0f;
 }
 
 __global__ void zero_members(float* __restrict__ X, int32_t cols, const int32_t* __restrict__ mrow,
@@ -39,9 +42,11 @@ __global__ void zero_members(float* __restrict__ X, int32_t cols, const int32_t*
 // After sweep p: Y_p(s, j) = alpha (A m_{p-1})(s) is alpha^p F_p(s), the weighted p-walks whose
 // first visit to S_j is their last vertex s. It meets every walk continuing from s:
 // acc += alpha^p F_p(s) * K_{L-p}(s), K_q(s) = sum_{r<=q} t_r(s). Then m_p(s) = 0.
+// On a weighted graph (rs = the vertex scales) Y and the table hold s times the true values.
 __global__ void batch_member_epilogue(float* __restrict__ Y, int32_t cols, const int32_t* __restrict__ mrow,
                                       const int32_t* __restrict__ mcol, double* __restrict__ acc, int32_t count,
-                                      const double* __restrict__ ttab, int32_t n, int32_t q) {
+                                      const double* __restrict__ ttab, int32_t n, int32_t q,
+                                      const double* __restrict__ rs) {
   const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= count) return;
   const int32_t s = mrow[i];
@@ -49,18 +54,24 @@ __global__ void batch_member_epilogue(float* __restrict__ Y, int32_t cols, const
   const double f = static_cast<double>(*y);
   double K = 0.0;
   for (int32_t r = 0; r <= q; ++r) K += ttab[static_cast<size_t>(r) * n + s];
+  if (rs) {
+    const double sv = rs[s];
+    K = sv > 0.0 ? K / (sv * sv) : 0.0;  // a vertex without edges starts and ends no walk
+  }
   acc[i] += f * K;
   *y = 0.0f;
 }
 
 // acc starts with the p = 0 term: every walk that starts at s (length 1..L) hits S_j at s.
 __global__ void batch_member_init(const int32_t* __restrict__ mrow, double* __restrict__ acc, int32_t count,
-                                  const double* __restrict__ ttab, int32_t n, int32_t L) {
+                                  const double* __restrict__ ttab, int32_t n, int32_t L,
+                                  const double* __restrict__ rs) {
   const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= count) return;
   const int32_t s = mrow[i];
   double K = 0.0;
   for (int32_t r = 1; r <= L; ++r) K += ttab[static_cast<size_t>(r) * n + s];
+  if (rs) K = rs[s] > 0.0 ? K / rs[s] : 0.0;
   acc[i] = K;
 }
 
@@ -93,9 +104,11 @@ gedwalk_status score_one(Graph& g, Workspace& ws, const std::vector<int32_t>& S_
   GW_TRY(ws.small.ensure(64, s));
   GW_TRY(upload_mask(g, ws, S_int, s));
   if (r.fp64)
-    init_two_state<double><<<blocks_for(g.n), 256, 0, s>>>(ws.x0.as<double>(), ws.mask.as<uint32_t>(), g.n);
+    init_two_state<double><<<blocks_for(g.n), 256, 0, s>>>(ws.x0.as<double>(), ws.mask.as<uint32_t>(), g.n,
+                                                            g.weighted ? g.rs_d.as<double>() : nullptr);
   else
-    init_two_state<float><<<blocks_for(g.n), 256, 0, s>>>(ws.x0.as<float>(), ws.mask.as<uint32_t>(), g.n);
+    init_two_state<float><<<blocks_for(g.n), 256, 0, s>>>(ws.x0.as<float>(), ws.mask.as<uint32_t>(), g.n,
+                                                           g.weighted ? g.rs_f.as<float>() : nullptr);
   GW_KCHECK();
   SweepArgs a = base_args(g, ws);
   a.alpha = r.alpha;
@@ -131,7 +144,8 @@ gedwalk_status autotune_batch(Graph& g, Workspace& ws, const Resolved& r) {
     const size_t vbytes = static_cast<size_t>(g.n) * c * 4;
     if (ws.x0.ensure(vbytes, s) != GEDWALK_OK || ws.x1.ensure(vbytes, s) != GEDWALK_OK) break;
     GW_TRY(ensure_sweep_scratch(g, ws, c, false, s));
-    init_batch<<<blocks_for(static_cast<int64_t>(g.n) * c), 256, 0, s>>>(ws.x0.as<float>(), g.n, g.n, c, c);
+    init_batch<<<blocks_for(static_cast<int64_t>(g.n) * c), 256, 0, s>>>(ws.x0.as<float>(), g.n, g.n, c, c,
+                                                                          nullptr);
     GW_KCHECK();
     SweepArgs a = base_args(g, ws);
     a.alpha = r.alpha;
@@ -191,13 +205,14 @@ gedwalk_status score_batch_impl(Graph& g, Workspace& ws, const int32_t* offsets,
   GW_TRY(ensure_sweep_scratch(g, ws, C, false, s));
   GW_TRY(ws.small.ensure(static_cast<size_t>(G) * sizeof(double) + 64, s));
   const double* T = g.ttab.as<double>();
+  const double* rsd = g.weighted ? g.rs_d.as<double>() : nullptr;
   SweepArgs a = base_args(g, ws);
   a.alpha = r.alpha;
   if (g.n_active < g.n)
     GW_CUDA(cudaMemsetAsync(ws.x1.as<float>() + static_cast<size_t>(g.n_active) * C, 0,
                             sizeof(float) * C * (static_cast<size_t>(g.n) - g.n_active), s));
   if (total > 0) {
-    batch_member_init<<<blocks_for(total), 256, 0, s>>>(mrow, acc, static_cast<int32_t>(total), T, g.n, r.L);
+    batch_member_init<<<blocks_for(total), 256, 0, s>>>(mrow, acc, static_cast<int32_t>(total), T, g.n, r.L, rsd);
     GW_KCHECK();
   }
   for (int32_t g0 = 0; g0 < G; g0 += C) {
@@ -205,7 +220,8 @@ gedwalk_status score_batch_impl(Graph& g, Workspace& ws, const int32_t* offsets,
     const int32_t m0 = offsets[g0], m1 = offsets[g1];
     const int32_t cnt = m1 - m0;
     init_batch<<<blocks_for(static_cast<int64_t>(g.n) * C), 256, 0, s>>>(ws.x0.as<float>(), g.n, g.n_active, C,
-                                                                          g1 - g0);
+                                                                          g1 - g0,
+                                                                          g.weighted ? g.rs_f.as<float>() : nullptr);
     GW_KCHECK();
     if (cnt > 0) {
       zero_members<<<blocks_for(cnt), 256, 0, s>>>(ws.x0.as<float>(), C, mrow + m0, mcol + m0, cnt);
@@ -219,7 +235,7 @@ gedwalk_status score_batch_impl(Graph& g, Workspace& ws, const int32_t* offsets,
       GW_TRY(launch_sweep(MODE_PLAIN, false, C, a, s));
       if (cnt > 0) {
         batch_member_epilogue<<<blocks_for(cnt), 256, 0, s>>>(static_cast<float*>(nxt), C, mrow + m0, mcol + m0,
-                                                               acc + m0, cnt, T, g.n, r.L - p);
+                                                               acc + m0, cnt, T, g.n, r.L - p, rsd);
         GW_KCHECK();
       }
       std::swap(cur, nxt);

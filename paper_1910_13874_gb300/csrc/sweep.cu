@@ -209,8 +209,13 @@ struct Scatter {
 template <int MODE, int C>
 struct Sums {
   static constexpr int N = MODE == MODE_TOTALS ? 1 : MODE == MODE_SCORE ? 1 : MODE == MODE_FUSED ? C - 1
-                           : MODE == MODE_CAND ? C : 0;
+                           : MODE == MODE_CAND ? C : MODE == MODE_LOOK ? C / 2 : 0;
   static constexpr int first = MODE == MODE_FUSED ? 1 : 0;
+  // the sum fed by column c, or -1 (MODE_LOOK: the odd columns, the candidates)
+  __device__ __forceinline__ static int slot(int c) {
+    if constexpr (MODE == MODE_LOOK) return (c & 1) ? c >> 1 : -1;
+    return c >= first && c - first < N ? c - first : -1;
+  }
 };
 
 // Column-parallel epilogue for row r. The calling lane holds the totals s[0..CPL) of
@@ -220,10 +225,14 @@ struct Sums {
 template <typename T, int C, int MODE, int CPL>
 __device__ __forceinline__ void epilogue(const SweepArgs& a, const int* __restrict__ s_cand, int r, bool valid,
                                          bool store, int c0, int base, T (&s)[CPL], double (&cs)[CPL]) {
-  const T alpha = static_cast<T>(a.alpha);
   T* Y = static_cast<T*>(a.Y);
-  constexpr bool kMasked = MODE == MODE_SCORE || MODE == MODE_FUSED || MODE == MODE_CAND;
+  constexpr bool kMasked = MODE == MODE_SCORE || MODE == MODE_FUSED || MODE == MODE_CAND || MODE == MODE_LOOK;
   const bool inS = kMasked && valid ? in_mask(a.mask, r) : false;
+  // weighted graph: the row's scale s_r turns the gathered sum into the true value
+  // alpha s_r (A x~)(r), which is summed, and the stored vector is x~ = s_r * value
+  const T* rs = sizeof(T) == 8 ? reinterpret_cast<const T*>(a.rs_d) : reinterpret_cast<const T*>(a.rs_f);
+  const T sv = rs && valid ? __ldg(rs + r) : T(1);
+  const T alpha = static_cast<T>(a.alpha) * sv;
   if constexpr (MODE == MODE_SCORE) {
     // Section 3.1.1: hit_i(v) = sum hit_{i-1}(u) + [v in S] sum miss_{i-1}(u);
     //                miss_i(v) = [v not in S] sum miss_{i-1}(u).  Columns: 0 = hit, 1 = miss.
@@ -239,8 +248,10 @@ __device__ __forceinline__ void epilogue(const SweepArgs& a, const int* __restri
       T out[2];
       out[0] = alpha * (inS ? sh + sm : sh);
       out[1] = inS ? T(0) : alpha * sm;
-      store_vec<T, 2>(Y + static_cast<size_t>(r) * C, out);
       cs[0] += static_cast<double>(out[0]);
+      out[0] *= sv;
+      out[1] *= sv;
+      store_vec<T, 2>(Y + static_cast<size_t>(r) * C, out);
     }
   } else {
     T y[CPL];
@@ -260,13 +271,35 @@ __device__ __forceinline__ void epilogue(const SweepArgs& a, const int* __restri
 #pragma unroll
       for (int k = 0; k < CPL; ++k)
         if (valid && s_cand[c0 + k] == r) y[k] = __ldg(static_cast<const T*>(a.Min) + r);
+    } else if constexpr (MODE == MODE_LOOK) {
+      // level d = c / 2 runs under S + {c_1..c_d}: column 2d is its phi^miss, column 2d+1 the
+      // walks through c_{d+1}, whose own row takes column 2d's value
+#pragma unroll
+      for (int k = 0; k < CPL; ++k) {
+        const int d = (c0 + k) >> 1;
+        for (int j = 0; j < d; ++j)
+          if (s_cand[j] == r) y[k] = T(0);
+      }
+      const T left = __shfl_up_sync(kFull, y[CPL - 1], 1);  // column 2d of a lane holding only 2d+1
+#pragma unroll
+      for (int k = 0; k < CPL; ++k) {
+        const int c = c0 + k;
+        if ((c & 1) && s_cand[c >> 1] == r) y[k] = CPL == 1 ? left : y[k > 0 ? k - 1 : 0];
+      }
+      if (store) {
+#pragma unroll
+        for (int k = 0; k < CPL; ++k)
+          if (((c0 + k) & 1) == 0) static_cast<T*>(a.Mout)[a.mout_stride * ((c0 + k) >> 1) + r] = y[k];
+      }
     }
     if (store) {
-      store_vec<T, CPL>(Y + static_cast<size_t>(r) * C + c0, y);
       if constexpr (Sums<MODE, C>::N > 0) {
 #pragma unroll
         for (int k = 0; k < CPL; ++k) cs[k] += static_cast<double>(y[k]);
       }
+#pragma unroll
+      for (int k = 0; k < CPL; ++k) y[k] *= sv;
+      store_vec<T, CPL>(Y + static_cast<size_t>(r) * C + c0, y);
     }
   }
 }
@@ -275,13 +308,12 @@ __device__ __forceinline__ void epilogue(const SweepArgs& a, const int* __restri
 template <int MODE, int C, int CPL>
 __device__ __forceinline__ void write_slot(const SweepArgs& a, size_t slot, int c0, const double (&cs)[CPL]) {
   constexpr int NS = Sums<MODE, C>::N;
-  constexpr int F = Sums<MODE, C>::first;
   if constexpr (NS > 0) {
     double* dst = a.slots + slot * NS;
 #pragma unroll
     for (int k = 0; k < CPL; ++k) {
-      const int c = c0 + k;
-      if (c >= F && c - F < NS) dst[c - F] = a.accumulate ? dst[c - F] + cs[k] : cs[k];
+      const int j = Sums<MODE, C>::slot(c0 + k);
+      if (j >= 0) dst[j] = a.accumulate ? dst[j] + cs[k] : cs[k];
     }
   }
 }
@@ -482,7 +514,7 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const SweepArgs a) {
   __shared__ int s_cand[kCandSlots];
   __shared__ int s_rp[kWarps][kUnitRowsMax + 1];
   if (threadIdx.x < kCandSlots)
-    s_cand[threadIdx.x] = (MODE == MODE_FUSED || MODE == MODE_CAND) && a.cand ? a.cand[threadIdx.x] : -1;
+    s_cand[threadIdx.x] = (MODE == MODE_FUSED || MODE == MODE_CAND || MODE == MODE_LOOK) && a.cand ? a.cand[threadIdx.x] : -1;
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int uidx = blockIdx.x * kWarps + warp;
@@ -548,7 +580,9 @@ gedwalk_status run(const SweepArgs& a, cudaStream_t s, bool profile) {
   b.hub = static_cast<int32_t>(std::min<int64_t>(a.n, kL1HubBytes / (sizeof(T) * C)));
   sweep_kernel<T, C, MODE><<<grid, kThreads, 0, s>>>(b);
   GW_KCHECK();
-  if (prof) profile_end(s, ev, sweep_bytes(MODE, sizeof(T) == 8, C, a.n, a.nnz), (MODE * 1000 + C) * 2 + (sizeof(T) == 8));
+  if (prof)
+    profile_end(s, ev, sweep_bytes(MODE, sizeof(T) == 8, C, a.n, a.nnz, a.rs_f != nullptr),
+                (MODE * 1000 + C) * 2 + (sizeof(T) == 8));
   return GEDWALK_OK;
 }
 
@@ -563,6 +597,8 @@ int sweep_sums(int mode, int cols) {
       return cols - 1;
     case MODE_CAND:
       return cols;
+    case MODE_LOOK:
+      return cols / 2;
     default:
       return 0;
   }
@@ -585,6 +621,9 @@ gedwalk_status launch_sweep(int mode, bool fp64, int cols, const SweepArgs& a, c
   GW_CASE(MODE_CAND, float, 16)
   GW_CASE(MODE_CAND, double, 4)
   GW_CASE(MODE_CAND, double, 8)
+  GW_CASE(MODE_LOOK, float, 4)
+  GW_CASE(MODE_LOOK, float, 8)
+  GW_CASE(MODE_LOOK, double, 4)
   GW_CASE(MODE_PLAIN, float, 4)
   GW_CASE(MODE_PLAIN, float, 8)
   GW_CASE(MODE_PLAIN, float, 16)

@@ -21,7 +21,10 @@ FP64, FP32 = 0, 1
 EPS_OVER_K, EPS_PLAIN = 0, 1
 GAINS_ALL = 1
 STOCHASTIC = 2
+ADAPTIVE_L = 4
+BOUND_COMBINATORIAL, BOUND_SPECTRAL = 0, 1
 UPLOAD_TRUSTED = 1
+UPLOAD_DIRECTED = 2
 REQ_SCORE, REQ_MAXIMIZE = 0, 1
 
 _STATUS_NAMES = {OK: "OK", ERR_INVALID: "INVALID", ERR_OOM: "OOM", ERR_NOT_CONVERGENT: "NOT_CONVERGENT",
@@ -29,9 +32,10 @@ _STATUS_NAMES = {OK: "OK", ERR_INVALID: "INVALID", ERR_OOM: "OOM", ERR_NOT_CONVE
 
 # every exported entry point of include/gedwalk.h
 EXPORTS = [
-    "gedwalk_params_default", "gedwalk_set_allocator", "gedwalk_graph_upload", "gedwalk_graph_free",
+    "gedwalk_params_default", "gedwalk_set_allocator", "gedwalk_graph_upload", "gedwalk_graph_upload_weighted",
+    "gedwalk_graph_info_weighted", "gedwalk_graph_free", "gedwalk_truncation_ex", "gedwalk_sigma_max",
     "gedwalk_graph_info", "gedwalk_truncation", "gedwalk_score", "gedwalk_score_batch", "gedwalk_gains",
-    "gedwalk_maximize", "gedwalk_maximize_stats", "gedwalk_serve_create", "gedwalk_serve_submit",
+    "gedwalk_maximize", "gedwalk_maximize_stats", "gedwalk_maximize_lengths", "gedwalk_serve_create", "gedwalk_serve_submit",
     "gedwalk_serve_poll", "gedwalk_serve_stats", "gedwalk_serve_destroy", "gedwalk_score_step_noalloc",
     "gedwalk_profile", "gedwalk_profile_read", "gedwalk_last_error",
 ]
@@ -70,6 +74,8 @@ class Params(ctypes.Structure):
         ("stream", ctypes.c_int64),
         ("eta", ctypes.c_double),
         ("seed", ctypes.c_uint64),
+        ("bound", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -101,6 +107,12 @@ def load(path: Optional[str] = None):
             "gedwalk_set_allocator": (ctypes.c_int, [_ALLOC_FN, _FREE_FN, vp]),
             "gedwalk_graph_upload": (ctypes.c_int, [_i32p, _i32p, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32,
                                                     ctypes.POINTER(vp)]),
+            "gedwalk_graph_upload_weighted": (ctypes.c_int, [_i32p, _i32p, ctypes.c_int32, ctypes.c_int64, _f64p,
+                                                             ctypes.c_int32, ctypes.POINTER(vp)]),
+            "gedwalk_graph_info_weighted": (ctypes.c_int, [vp, _i32p, _f64p]),
+            "gedwalk_truncation_ex": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_double, ctypes.c_int32, _i32p,
+                                                     _f64p]),
+            "gedwalk_sigma_max": (ctypes.c_int, [vp, ctypes.c_int32, _f64p, _f64p]),
             "gedwalk_graph_free": (ctypes.c_int, [vp]),
             "gedwalk_graph_info": (ctypes.c_int, [vp, _i32p, _i64p, _i32p, _f64p]),
             "gedwalk_truncation": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_double, _i32p, _f64p]),
@@ -112,6 +124,7 @@ def load(path: Optional[str] = None):
             "gedwalk_maximize": (ctypes.c_int, [vp, ctypes.c_int32, ctypes.POINTER(Params), _i32p, _f64p, _f64p,
                                                 _i32p, _i32p, ctypes.c_int32]),
             "gedwalk_maximize_stats": (ctypes.c_int, [vp, _i64p, _i64p, _i64p, _i64p]),
+            "gedwalk_maximize_lengths": (ctypes.c_int, [vp, _i32p, ctypes.c_int32, _i32p, _i64p]),
             "gedwalk_serve_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int32, ctypes.c_int64,
                                                     ctypes.c_int32, ctypes.POINTER(vp)]),
             "gedwalk_serve_submit": (ctypes.c_int, [vp, ctypes.c_int32, ctypes.c_int32, _i32p, ctypes.c_int32,
@@ -150,7 +163,7 @@ def _ptr(a: np.ndarray, t):
 
 def make_params(alpha: float = 0.0, epsilon: float = 1e-4, L: int = 0, precision: str = "fp32",
                 eps_rule: str = "over_k", gains_all: bool = False, stream: int = 0, stochastic: bool = False,
-                eta: float = 0.1, seed: int = 0) -> Params:
+                eta: float = 0.1, seed: int = 0, adaptive: bool = False, bound: str = "combinatorial") -> Params:
     p = Params()
     load().gedwalk_params_default(ctypes.byref(p))
     p.alpha = alpha
@@ -158,7 +171,8 @@ def make_params(alpha: float = 0.0, epsilon: float = 1e-4, L: int = 0, precision
     p.L = L
     p.precision = FP64 if precision in ("fp64", "f64", FP64) else FP32
     p.greedy_eps_rule = EPS_PLAIN if eps_rule == "plain" else EPS_OVER_K
-    p.flags = (GAINS_ALL if gains_all else 0) | (STOCHASTIC if stochastic else 0)
+    p.flags = (GAINS_ALL if gains_all else 0) | (STOCHASTIC if stochastic else 0) | (ADAPTIVE_L if adaptive else 0)
+    p.bound = {"combinatorial": BOUND_COMBINATORIAL, "spectral": BOUND_SPECTRAL}[bound]
     p.stream = int(stream)
     p.eta = eta
     p.seed = seed
@@ -213,24 +227,42 @@ def profile_read() -> dict:
 class Graph:
     """A device-resident graph (undirected CSR uploaded with gedwalk_graph_upload)."""
 
-    def __init__(self, row_ptr, col_idx, trusted: bool = False):
+    def __init__(self, row_ptr, col_idx, trusted: bool = False, weighted: bool = False, vertex_scale=None,
+                 directed: bool = False):
+        """weighted: walks weighted by w(v,u) = s_v s_u (gedwalk_graph_upload_weighted); vertex_scale
+        gives s (float64[n]), None the normalised adjacency D^{-1/2} A D^{-1/2}. directed: the rows
+        are successor lists of a directed graph."""
         lib = load()
         rp = _i32(row_ptr)
         ci = _i32(col_idx)
         n = rp.shape[0] - 1
         h = ctypes.c_void_p()
         ci_arg = ci if ci.size else np.zeros(1, np.int32)
-        _check(lib.gedwalk_graph_upload(_ptr(rp, _i32p), _ptr(ci_arg, _i32p), n, ci.size,
-                                        UPLOAD_TRUSTED if trusted else 0, ctypes.byref(h)))
+        fl = (UPLOAD_TRUSTED if trusted else 0) | (UPLOAD_DIRECTED if directed else 0)
+        if weighted or vertex_scale is not None:
+            sc = None
+            if vertex_scale is not None:
+                sc = np.ascontiguousarray(vertex_scale, dtype=np.float64)
+                if sc.shape != (n,):
+                    raise ValueError("vertex_scale must hold n values")
+            _check(lib.gedwalk_graph_upload_weighted(_ptr(rp, _i32p), _ptr(ci_arg, _i32p), n, ci.size,
+                                                     None if sc is None else _ptr(sc, _f64p), fl, ctypes.byref(h)))
+        else:
+            _check(lib.gedwalk_graph_upload(_ptr(rp, _i32p), _ptr(ci_arg, _i32p), n, ci.size, fl, ctypes.byref(h)))
         self._h = h
         n_, nnz, dmax, alpha = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_double()
         _check(lib.gedwalk_graph_info(h, ctypes.byref(n_), ctypes.byref(nnz), ctypes.byref(dmax),
                                       ctypes.byref(alpha)))
         self.n, self.nnz, self.dmax, self.alpha_default = n_.value, nnz.value, dmax.value, alpha.value
+        wt, dl = ctypes.c_int32(), ctypes.c_double()
+        _check(lib.gedwalk_graph_info_weighted(h, ctypes.byref(wt), ctypes.byref(dl)))
+        self.weighted, self.delta = bool(wt.value), dl.value
+        self.directed = bool(directed)
 
     @classmethod
-    def from_host(cls, g, trusted: bool = False):
-        return cls(g.row_ptr, g.col_idx, trusted=trusted)
+    def from_host(cls, g, trusted: bool = False, weighted: bool = False, vertex_scale=None, directed: bool = False):
+        return cls(g.row_ptr, g.col_idx, trusted=trusted, weighted=weighted, vertex_scale=vertex_scale,
+                   directed=directed)
 
     @property
     def handle(self):
@@ -247,10 +279,21 @@ class Graph:
         except Exception:
             pass
 
-    def truncation(self, alpha: float = 0.0, epsilon: float = 1e-4):
+    def truncation(self, alpha: float = 0.0, epsilon: float = 1e-4, bound: str = "combinatorial"):
+        """(L, B_L) for (alpha, epsilon) with the combinatorial or the spectral tail bound."""
         L, b = ctypes.c_int32(), ctypes.c_double()
-        _check(load().gedwalk_truncation(self._h, alpha, epsilon, ctypes.byref(L), ctypes.byref(b)))
+        if bound == "combinatorial":
+            _check(load().gedwalk_truncation(self._h, alpha, epsilon, ctypes.byref(L), ctypes.byref(b)))
+        else:
+            kind = {"spectral": BOUND_SPECTRAL}[bound]
+            _check(load().gedwalk_truncation_ex(self._h, alpha, epsilon, kind, ctypes.byref(L), ctypes.byref(b)))
         return L.value, b.value
+
+    def sigma_max(self, iters: int = 300):
+        """(upper, lower) bounds of the largest singular value of A (gedwalk_sigma_max)."""
+        up, lo = ctypes.c_double(), ctypes.c_double()
+        _check(load().gedwalk_sigma_max(self._h, iters, ctypes.byref(up), ctypes.byref(lo)))
+        return up.value, lo.value
 
     def score(self, S: Sequence[int], params: Optional[Params] = None, **kw):
         """(score, L, tail_bound) of one group."""
@@ -302,6 +345,16 @@ class Graph:
         vals = [ctypes.c_int64() for _ in range(4)]
         _check(load().gedwalk_maximize_stats(self._h, *[ctypes.byref(v) for v in vals]))
         return dict(zip(("evaluations", "batches", "sweeps", "spec_misses"), (v.value for v in vals)))
+
+    def maximize_lengths(self):
+        """(ell, separation_failures): the walk length of each step of the last maximize."""
+        cnt = ctypes.c_int32()
+        fails = ctypes.c_int64()
+        _check(load().gedwalk_maximize_lengths(self._h, None, 0, ctypes.byref(cnt), None))
+        ell = np.zeros(max(cnt.value, 1), dtype=np.int32)
+        _check(load().gedwalk_maximize_lengths(self._h, ell.ctypes.data_as(_i32p), cnt.value, ctypes.byref(cnt),
+                                               ctypes.byref(fails)))
+        return ell[:cnt.value].copy(), int(fails.value)
 
 
 class Server:

@@ -314,3 +314,81 @@ def test_stochastic_maximize_matches_oracle(cuda_device, name, k, eta, seed, pre
         if p < 1.0:
             assert oracle.sample_hash(seed, j, int(grp[j])) < int(p * 2.0 ** 64)
     assert rel(score, oracle.score(g, grp, alpha, L)) < tol
+
+
+# ------------------------------------------------------------------ lazy greedy with l-doubling (Algorithm 2)
+@pytest.mark.parametrize("name,k,eps", [("er1000", 5, 1e-6), ("er1000", 12, 1e-4), ("ba5000", 20, 1e-4),
+                                        ("rmat14", 16, 1e-4), ("star", 4, 1e-4), ("isolated", 6, 1e-3)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_adaptive_maximize_matches_oracle(cuda_device, name, k, eps, prec):
+    # Identical picks, walk lengths and separation failures as long as no separation test of the
+    # oracle lies within the tolerance of its threshold; after such a test only validity is checked.
+    g = host_graph(name)
+    G = dev_graph(name)
+    alpha = oracle.default_alpha(g)
+    sep = eps / k
+    ref = oracle.greedy_adaptive(g, k, alpha, sep)
+    grp, gains, score, L = G.maximize(k, precision=prec, epsilon=eps, adaptive=True)
+    ell, fails = G.maximize_lengths()
+    tol = TOL[prec]
+    assert len(ell) == k and L == ell[-1]
+    assert all(int(l) & (int(l) - 1) == 0 for l in ell) and np.all(np.diff(ell) >= 0)
+    gu, gv, B = ref["att_gu"], ref["att_gv"], ref["att_B"]
+    close = np.abs(gu - (gv + B - sep)) <= 10 * tol * np.maximum(np.maximum(gu, B), 1e-300)
+    close &= gv >= 0
+    upto = int(ref["att_step"][np.argmax(close)]) if close.any() else k  # steps decided far from the threshold
+    for j in range(upto):
+        assert ell[j] == ref["ell"][j], (j, list(ell), list(ref["ell"]))
+        if grp[j] != ref["group"][j]:  # an exact tie of gains (symmetric vertices) may part the sequences
+            assert abs(gains[j] - ref["gains"][j]) <= tol * max(ref["gains"][j], 1e-300), j
+            upto = j
+            break
+        assert gains[j] == ref["gains"][j] == 0.0 or rel(gains[j], ref["gains"][j]) < tol, j
+    if upto == k:
+        n_fail = int(np.sum((gv >= 0) & ~(gu > gv + B - sep)))
+        assert fails == n_fail
+    # every pick is the exact gain of that vertex at its step's length
+    for j in range(k):
+        want = oracle.gain(g, list(grp[:j]), int(grp[j]), alpha, int(ell[j]))
+        assert gains[j] == want == 0.0 or rel(gains[j], want) < tol, j
+    L_fixed = oracle.select_L(g, alpha, sep)[0]
+    assert rel(score, oracle.score(g, grp, alpha, L_fixed)) < tol
+    assert ell[-1] < 2 * L_fixed
+
+
+def test_adaptive_maximize_rejects_bad_combinations(cuda_device):
+    from paper_1910_13874_gb300 import gedwalk
+
+    G = dev_graph("er1000")
+    for kw in ({"L": 8}, {"gains_all": True}, {"stochastic": True}):
+        with pytest.raises(gedwalk.GedWalkError):
+            G.maximize(3, adaptive=True, **kw)
+    with pytest.raises(gedwalk.GedWalkError):
+        G.maximize(3, adaptive=True, init=[1, 2])
+    # the fixed-length run reports its L for every step
+    grp, gains, score, L = G.maximize(3)
+    ell, fails = G.maximize_lengths()
+    assert list(ell) == [L] * 3 and fails == 0
+
+
+# ------------------------------------------------------------------ lookahead sweeps (several steps per run)
+@pytest.mark.parametrize("name,k", [("ba5000", 24), ("rmat14", 24), ("er1000", 10)])
+@pytest.mark.parametrize("levels", ["1", "2", "4"])
+def test_lookahead_levels_match_oracle(cuda_device, monkeypatch, name, k, levels):
+    # Level d of a lookahead run holds phi^miss and the guessed winner's column under S + {c_1..c_d};
+    # whatever the number of levels, every pick is certified against the bounds of the current S.
+    g = host_graph(name)
+    G = dev_graph(name)
+    alpha = oracle.default_alpha(g)
+    monkeypatch.setenv("GEDWALK_LOOKAHEAD", levels)
+    grp, gains, score, L = G.maximize(k, precision="fp32", epsilon=1e-4)
+    ogrp, ogains, _ = oracle.greedy(g, k, alpha, L, "lazy")
+    for j in range(k):
+        if grp[j] != ogrp[j]:  # only a tie inside the tolerance may part the sequences
+            assert abs(gains[j] - ogains[j]) <= 1e-5 * ogains[j], (j, grp[j], ogrp[j])
+            break
+        assert gains[j] == ogains[j] == 0.0 or rel(gains[j], ogains[j]) < 1e-5, j
+    assert rel(score, oracle.score(g, grp, alpha, L)) < 1e-5
+    st = G.maximize_stats()
+    if levels != "1":  # steps whose winner was guessed run no sweep of their own
+        assert st["sweeps"] < (k + 1) * L
