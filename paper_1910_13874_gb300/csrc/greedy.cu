@@ -573,13 +573,15 @@ gedwalk_status maximize_impl(Graph& g, Workspace& ws, int32_t k, const Resolved&
   }
   // Lookahead (plain greedy on an undirected graph): one run of sweeps carries `levels` steps,
   // level d under S + {c_1..c_d} with the guessed winners c_d; a step whose winner was guessed
-  // needs no sweep of its own. GEDWALK_LOOKAHEAD (1 = off, 2, 4) overrides the default of 2.
+  // needs no sweep of its own. A gather costs one L2 sector request whatever the row width up to
+  // 32 bytes, so 4 FP32 levels (2 FP64) cost little more per sweep than one.
+  // GEDWALK_LOOKAHEAD (1 = off, 2, 4, 8 in FP32) overrides the default.
   int levels = 1;
   if (!(flags & (GEDWALK_ADAPTIVE_L | GEDWALK_STOCHASTIC | GEDWALK_GAINS_ALL)) && !g.directed) {
-    levels = 2;
+    levels = r.fp64 ? 2 : 4;
     if (const char* e = getenv("GEDWALK_LOOKAHEAD")) {
       const int v = atoi(e);
-      if (v == 1 || v == 2 || (v == 4 && !r.fp64)) levels = v;
+      if (v == 1 || v == 2 || (!r.fp64 && (v == 4 || v == 8))) levels = v;
     }
   }
   const bool look = levels > 1;

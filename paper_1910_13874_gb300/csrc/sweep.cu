@@ -205,16 +205,20 @@ struct Scatter {
   }
 };
 
-// Number of FP64 column sums a mode keeps; column c feeds sum (c - first).
+// Number of FP64 column sums a mode keeps.
 template <int MODE, int C>
 struct Sums {
   static constexpr int N = MODE == MODE_TOTALS ? 1 : MODE == MODE_SCORE ? 1 : MODE == MODE_FUSED ? C - 1
                            : MODE == MODE_CAND ? C : MODE == MODE_LOOK ? C / 2 : 0;
-  static constexpr int first = MODE == MODE_FUSED ? 1 : 0;
-  // the sum fed by column c, or -1 (MODE_LOOK: the odd columns, the candidates)
+  // the sum fed by column c, or -1 (MODE_FUSED: columns 1..; MODE_LOOK: the odd columns, the
+  // candidates)
   __device__ __forceinline__ static int slot(int c) {
-    if constexpr (MODE == MODE_LOOK) return (c & 1) ? c >> 1 : -1;
-    return c >= first && c - first < N ? c - first : -1;
+    if constexpr (MODE == MODE_LOOK) {
+      return (c & 1) ? c >> 1 : -1;
+    } else {
+      constexpr int first = MODE == MODE_FUSED ? 1 : 0;
+      return c >= first && c - first < N ? c - first : -1;
+    }
   }
 };
 
@@ -623,6 +627,7 @@ gedwalk_status launch_sweep(int mode, bool fp64, int cols, const SweepArgs& a, c
   GW_CASE(MODE_CAND, double, 8)
   GW_CASE(MODE_LOOK, float, 4)
   GW_CASE(MODE_LOOK, float, 8)
+  GW_CASE(MODE_LOOK, float, 16)
   GW_CASE(MODE_LOOK, double, 4)
   GW_CASE(MODE_PLAIN, float, 4)
   GW_CASE(MODE_PLAIN, float, 8)

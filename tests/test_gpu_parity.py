@@ -373,7 +373,7 @@ def test_adaptive_maximize_rejects_bad_combinations(cuda_device):
 
 # ------------------------------------------------------------------ lookahead sweeps (several steps per run)
 @pytest.mark.parametrize("name,k", [("ba5000", 24), ("rmat14", 24), ("er1000", 10)])
-@pytest.mark.parametrize("levels", ["1", "2", "4"])
+@pytest.mark.parametrize("levels", ["1", "2", "4", "8"])
 def test_lookahead_levels_match_oracle(cuda_device, monkeypatch, name, k, levels):
     # Level d of a lookahead run holds phi^miss and the guessed winner's column under S + {c_1..c_d};
     # whatever the number of levels, every pick is certified against the bounds of the current S.
