@@ -155,7 +155,7 @@ def recorded_traffic(top, workload_key):
     """
     from paper_1910_13874_gb300.kernel_hash import sweep_kernel_hash
 
-    files = {("rmat22", 2, 2, 0): "sweep_fused_f2_rmat22.md"}
+    files = {("rmat22", 2, 2, 0): "sweep_fused_f2_rmat22.md", ("rmat22", 5, 8, 0): "sweep_look_f8_rmat22.md"}
     name = files.get((workload_key, top["top_mode"], top["top_cols"], top["top_fp64"]))
     if not name:
         return None

@@ -179,33 +179,107 @@ gedwalk_status Workspace::ensure_pinned(size_t need) {
   return GEDWALK_OK;
 }
 
-// ---------------------------------------------------------------- host parallel helpers
-template <class F>
-static void parallel_rows(int64_t n, F&& f) {
-  unsigned hw = std::thread::hardware_concurrency();
-  unsigned T = std::max(1u, std::min(hw == 0 ? 1u : hw, 64u));
-  if (n < (1 << 15) || T == 1) {
-    f(int64_t(0), n);
-    return;
-  }
-  // dynamic chunks: heavy rows sit at the front after relabelling
-  const int64_t chunk = 4096;
-  std::atomic<int64_t> next(0);
-  std::vector<std::thread> th;
-  for (unsigned t = 0; t < T; ++t)
-    th.emplace_back([&]() {
-      for (;;) {
-        const int64_t b = next.fetch_add(chunk);
-        if (b >= n) break;
-        f(b, std::min(n, b + chunk));
-      }
-    });
-  for (auto& x : th) x.join();
-}
 
 // First malformed row (or -1) and a reason.
-static int64_t validate_csr(const int32_t* rp, const int32_t* ci, int32_t n, int64_t nnz, bool full,
-                            std::string* why, bool symmetric = true) {
+// Entry checks of an uploaded CSR, one warp per row: column in range, and (full) no self-loop,
+// strictly increasing rows and (symmetric) the reverse entry present, by binary search in the
+// other row. The smallest offending (row << 3 | kind) wins.
+__global__ void validate_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, int32_t n,
+                                int full, int symmetric, unsigned long long* __restrict__ bad) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t v = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+    const int32_t b = rp[v], e = rp[v + 1];
+    for (int32_t j = b + lane; j < e; j += 32) {
+      const int32_t u = ci[j];
+      int k = 0;
+      if (u < 0 || u >= n) {
+        k = 1;
+      } else if (full) {
+        if (u == v) {
+          k = 2;
+        } else if (j > b && ci[j - 1] >= u) {
+          k = 3;
+        } else if (symmetric) {
+          int32_t lo = rp[u], hi = rp[u + 1];
+          while (lo < hi) {  // first entry of row u that is >= v
+            const int32_t mid = lo + ((hi - lo) >> 1);
+            if (ci[mid] < v) lo = mid + 1;
+            else hi = mid;
+          }
+          if (lo == rp[u + 1] || ci[lo] != v) k = 4;
+        }
+      }
+      if (k) atomicMin(bad, (static_cast<unsigned long long>(v) << 3) | static_cast<unsigned long long>(k));
+    }
+  }
+}
+
+// Relabelled CSR, one warp per new row i: the entries of old row perm[i], each mapped to its new
+// id, in their old order.
+__global__ void relabel_kernel(const int32_t* __restrict__ raw_rp, const int32_t* __restrict__ raw_ci,
+                               const int32_t* __restrict__ rp, const int32_t* __restrict__ perm,
+                               const int32_t* __restrict__ inv, int32_t n, int32_t* __restrict__ ci) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
+    const int32_t src = raw_rp[perm[i]], dst = rp[i], len = rp[i + 1] - rp[i];
+    for (int32_t j = lane; j < len; j += 32) ci[dst + j] = inv[raw_ci[src + j]];
+  }
+}
+
+// Sorts segments of the relabelled CSR (one warp per segment of at most 1024 entries): whole rows
+// up to 1024 entries, and 1024-entry pieces of longer rows (those are summed slice by slice
+// anyway). Ascending neighbour ids put the high-degree neighbours, the most gathered rows, first
+// in every row. A bitonic network: in registers up to 32 entries, in the warp's shared memory above.
+constexpr int kSortSeg = 1024;
+__global__ void __launch_bounds__(256) sort_segments_kernel(const int2* __restrict__ seg, int64_t nseg,
+                                                            int32_t* __restrict__ ci) {
+  __shared__ int32_t buf[8][kSortSeg];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t warps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t sidx = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; sidx < nseg; sidx += warps) {
+    const int2 sg = seg[sidx];
+    int32_t* p = ci + sg.x;
+    const int len = sg.y;
+    if (len <= 32) {
+      int32_t x = lane < len ? p[lane] : INT_MAX;
+      for (int k = 2; k <= 32; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+          const int32_t y = __shfl_xor_sync(0xffffffffu, x, j);
+          const bool up = (lane & k) == 0, low = (lane & j) == 0;
+          x = (low == up) ? min(x, y) : max(x, y);
+        }
+      if (lane < len) p[lane] = x;
+      continue;
+    }
+    int P = 64;
+    while (P < len) P <<= 1;
+    int32_t* b = buf[w];
+    for (int i = lane; i < P; i += 32) b[i] = i < len ? p[i] : INT_MAX;
+    __syncwarp();
+    for (int k = 2; k <= P; k <<= 1)
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int t = lane; t < P / 2; t += 32) {
+          const int i = 2 * j * (t / j) + (t % j), q = i + j;
+          const int32_t a = b[i], c = b[q];
+          if (((i & k) == 0) == (a > c)) {
+            b[i] = c;
+            b[q] = a;
+          }
+        }
+        __syncwarp();
+      }
+    for (int i = lane; i < len; i += 32) p[i] = b[i];
+    __syncwarp();
+  }
+}
+
+// Validates a CSR: row_ptr on the host (the kernels index with it), the entries on the device
+// (drp/dci: copies of the same arrays). Returns the first offending row or -1.
+static int64_t validate_csr(const int32_t* rp, const int32_t* drp, const int32_t* dci, int32_t n, int64_t nnz,
+                            bool full, std::string* why, bool symmetric, gedwalk_status* st) {
+  *st = GEDWALK_OK;
   if (rp[0] != 0) {
     *why = "row_ptr[0] != 0";
     return 0;
@@ -219,34 +293,27 @@ static int64_t validate_csr(const int32_t* rp, const int32_t* ci, int32_t n, int
       *why = "row_ptr decreases";
       return v;
     }
-  std::atomic<int64_t> bad(INT64_MAX);
-  std::atomic<int> kind(0);
-  parallel_rows(n, [&](int64_t b, int64_t e) {
-    for (int64_t v = b; v < e; ++v) {
-      if (v >= bad.load(std::memory_order_relaxed)) return;
-      int k = 0;
-      for (int32_t j = rp[v]; j < rp[v + 1] && !k; ++j) {
-        const int32_t u = ci[j];
-        if (u < 0 || u >= n) k = 1;
-        else if (!full) continue;
-        else if (u == v) k = 2;
-        else if (j > rp[v] && ci[j - 1] >= u) k = 3;
-        else if (symmetric && !std::binary_search(ci + rp[u], ci + rp[u + 1], static_cast<int32_t>(v))) k = 4;
-      }
-      if (k) {
-        int64_t cur = bad.load();
-        while (v < cur && !bad.compare_exchange_weak(cur, v)) {
-        }
-        if (v <= bad.load()) kind.store(k);
-        return;
-      }
-    }
-  });
+  if (nnz == 0) return -1;
+  DevBuf dbad;
+  unsigned long long hbad = ~0ull;
+  if ((*st = dbad.ensure(sizeof(hbad), 0)) != GEDWALK_OK) return -1;
+  cudaError_t e = cudaMemcpy(dbad.p, &hbad, sizeof(hbad), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    const int64_t blocks = std::min<int64_t>((static_cast<int64_t>(n) * 32 + 255) / 256, 152 * 32);
+    validate_kernel<<<static_cast<int>(blocks), 256>>>(drp, dci, n, full ? 1 : 0, symmetric ? 1 : 0,
+                                                       dbad.as<unsigned long long>());
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(&hbad, dbad.p, sizeof(hbad), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    *st = fail(GEDWALK_ERR_DEVICE, "CSR validation: %s", cudaGetErrorString(e));
+    return -1;
+  }
   static const char* reasons[] = {"", "column index out of range", "self-loop", "row not strictly increasing",
                                   "graph is not symmetric (undirected graphs only)"};
-  if (bad.load() != INT64_MAX) {
-    *why = reasons[kind.load()];
-    return bad.load();
+  if (hbad != ~0ull) {
+    *why = reasons[hbad & 7];
+    return static_cast<int64_t>(hbad >> 3);
   }
   return -1;
 }
@@ -809,10 +876,20 @@ static gedwalk_status upload_impl(const int32_t* row_ptr, const int32_t* col_idx
   if (directed && weighted) return fail(GEDWALK_ERR_INVALID, "weighted directed graphs are not supported");
   std::string why;
   const bool trusted = (flags & GEDWALK_UPLOAD_TRUSTED) != 0;
+  // the caller's CSR on the device: validated there, then relabelled there
+  DevBuf raw_rp, raw_ci;
+  GW_TRY(raw_rp.ensure((static_cast<size_t>(n) + 1) * sizeof(int32_t), 0));
+  GW_TRY(raw_ci.ensure(std::max<size_t>(static_cast<size_t>(nnz), 1) * sizeof(int32_t), 0));
+  GW_CUDA(cudaMemcpy(raw_rp.p, row_ptr, (static_cast<size_t>(n) + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
+  if (nnz > 0)
+    GW_CUDA(cudaMemcpy(raw_ci.p, col_idx, static_cast<size_t>(nnz) * sizeof(int32_t), cudaMemcpyHostToDevice));
   {
     // row_ptr and index ranges are always checked (the plan and the kernels index with
     // them); TRUSTED skips the sortedness, self-loop and symmetry checks
-    const int64_t bad = validate_csr(row_ptr, col_idx, n, nnz, !trusted, &why, !directed);
+    gedwalk_status vst = GEDWALK_OK;
+    const int64_t bad = validate_csr(row_ptr, raw_rp.as<int32_t>(), raw_ci.as<int32_t>(), n, nnz, !trusted, &why,
+                                     !directed, &vst);
+    if (vst != GEDWALK_OK) return vst;
     if (bad >= 0)
       return fail(GEDWALK_ERR_INVALID, "malformed graph at row %lld: %s", static_cast<long long>(bad), why.c_str());
   }
@@ -887,17 +964,6 @@ static gedwalk_status upload_impl(const int32_t* row_ptr, const int32_t* col_idx
     g->deg[i] = deg_old[g->perm[i]];
     rp[i + 1] = rp[i] + g->deg[i];
   }
-  std::vector<int32_t> ci(static_cast<size_t>(nnz) + 4, 0);
-  const Graph* gp = g.get();
-  parallel_rows(n, [&](int64_t b, int64_t e) {
-    for (int64_t i = b; i < e; ++i) {
-      const int32_t v = gp->perm[i];
-      int32_t* dst = ci.data() + rp[i];
-      const int32_t len = rp[i + 1] - rp[i];
-      for (int32_t j = 0; j < len; ++j) dst[j] = gp->inv[col_idx[row_ptr[v] + j]];
-      std::sort(dst, dst + len);
-    }
-  });
   // rows from n_active on are isolated: no entry in either direction
   g->n_active = n;
   if (!directed) {
@@ -906,11 +972,43 @@ static gedwalk_status upload_impl(const int32_t* row_ptr, const int32_t* col_idx
     while (g->n_active > 0 && g->deg[g->n_active - 1] == 0 && rdeg_old[g->perm[g->n_active - 1]] == 0) --g->n_active;
   }
   GW_TRY(g->rp.ensure(rp.size() * sizeof(int32_t), 0));
-  GW_TRY(g->ci.ensure(ci.size() * sizeof(int32_t), 0));
+  const size_t ci_len = static_cast<size_t>(nnz) + 4;  // 4 zero pad entries for the vector loads at the end
+  GW_TRY(g->ci.ensure(ci_len * sizeof(int32_t), 0));
   GW_TRY(g->perm_d.ensure(static_cast<size_t>(n) * sizeof(int32_t), 0));
   GW_CUDA(cudaMemcpy(g->rp.p, rp.data(), rp.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-  GW_CUDA(cudaMemcpy(g->ci.p, ci.data(), ci.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
   GW_CUDA(cudaMemcpy(g->perm_d.p, g->perm.data(), static_cast<size_t>(n) * sizeof(int32_t), cudaMemcpyHostToDevice));
+  {
+    DevBuf inv_d;
+    GW_TRY(inv_d.ensure(static_cast<size_t>(n) * sizeof(int32_t), 0));
+    GW_CUDA(cudaMemcpy(inv_d.p, g->inv.data(), static_cast<size_t>(n) * sizeof(int32_t), cudaMemcpyHostToDevice));
+    GW_CUDA(cudaMemset(g->ci.as<int32_t>() + nnz, 0, 4 * sizeof(int32_t)));
+    const int64_t blocks = std::min<int64_t>((static_cast<int64_t>(n) * 32 + 255) / 256, 152 * 32);
+    relabel_kernel<<<static_cast<int>(blocks), 256>>>(raw_rp.as<int32_t>(), raw_ci.as<int32_t>(), g->rp.as<int32_t>(),
+                                                      g->perm_d.as<int32_t>(), inv_d.as<int32_t>(), n,
+                                                      g->ci.as<int32_t>());
+    GW_KCHECK();
+    // sort each row (each 1024-entry piece of a longer row) by new id
+    std::vector<int2> seg;
+    seg.reserve(static_cast<size_t>(g->n_active));
+    for (int32_t i = 0; i < n; ++i)
+      for (int32_t b = rp[i]; b < rp[i + 1]; b += kSortSeg) {
+        const int32_t len = std::min(kSortSeg, rp[i + 1] - b);
+        if (len > 1) seg.push_back(make_int2(b, len));
+      }
+    if (!seg.empty()) {
+      DevBuf seg_d;
+      GW_TRY(seg_d.ensure(seg.size() * sizeof(int2), 0));
+      GW_CUDA(cudaMemcpy(seg_d.p, seg.data(), seg.size() * sizeof(int2), cudaMemcpyHostToDevice));
+      const int64_t sblocks = std::min<int64_t>((static_cast<int64_t>(seg.size()) * 32 + 255) / 256, 152 * 32);
+      sort_segments_kernel<<<static_cast<int>(sblocks), 256>>>(seg_d.as<int2>(), static_cast<int64_t>(seg.size()),
+                                                               g->ci.as<int32_t>());
+      GW_KCHECK();
+      GW_CUDA(cudaDeviceSynchronize());
+    }
+    GW_CUDA(cudaDeviceSynchronize());
+  }
+  raw_ci.release();
+  raw_rp.release();
   if (weighted) {
     std::vector<double> sd(n);
     std::vector<float> sf(n);
@@ -932,8 +1030,10 @@ static gedwalk_status upload_impl(const int32_t* row_ptr, const int32_t* col_idx
     for (int32_t i = 0; i < n; ++i) rpr[i + 1] = rpr[i] + g->deg_r[i];
     std::vector<int32_t> cir(static_cast<size_t>(nnz) + 4, 0);
     std::vector<int32_t> fill(rpr.begin(), rpr.end() - 1);
-    for (int32_t i = 0; i < n; ++i)  // rows i in increasing order: every reverse row comes out sorted
-      for (int32_t j = rp[i]; j < rp[i + 1]; ++j) cir[fill[ci[j]]++] = i;
+    for (int32_t i = 0; i < n; ++i) {  // rows i in increasing order: every reverse row comes out sorted
+      const int32_t v = g->perm[i];
+      for (int32_t j = row_ptr[v]; j < row_ptr[v + 1]; ++j) cir[fill[g->inv[col_idx[j]]]++] = i;
+    }
     GW_TRY(g->rp_r.ensure(rpr.size() * sizeof(int32_t), 0));
     GW_TRY(g->ci_r.ensure(cir.size() * sizeof(int32_t), 0));
     GW_CUDA(cudaMemcpy(g->rp_r.p, rpr.data(), rpr.size() * sizeof(int32_t), cudaMemcpyHostToDevice));

@@ -586,7 +586,9 @@ gedwalk_status maximize_impl(Graph& g, Workspace& ws, int32_t k, const Resolved&
   }
   const bool look = levels > 1;
   const int n_spec = look ? levels : cols_fused - 1;
-  const int cols_cand = r.fp64 ? 4 : 8;
+  // Candidate batches run when the evaluated guess is not certified; the winner is nearly always
+  // among the best few bounds, and a narrower batch is a cheaper sweep.
+  const int cols_cand = 4;
   const int cols_all = r.fp64 ? 8 : 16;
   const double tol = r.fp64 ? 1e-11 : 1e-5;  // relative inflation of bounds against rounding
   const bool gains_all = (flags & GEDWALK_GAINS_ALL) != 0;
@@ -725,7 +727,13 @@ gedwalk_status maximize_impl(Graph& g, Workspace& ws, int32_t k, const Resolved&
           GW_KCHECK();
           E.push_back(Cand{look_g[look_lvl], cl, g.perm[cl]});
           sc.push_back(cl);
-        } else if (look && !spec.empty()) {
+        } else if (look && (!spec.empty() || step == 0)) {
+          if (spec.empty()) {
+            // the first step has no bounds yet: guess the highest-degree vertices outside S (new
+            // ids run by decreasing degree), GED-Walk's leading order for small alpha
+            for (int32_t v = 0; v < g.n && static_cast<int>(spec.size()) < levels; ++v)
+              if (!inS[v]) spec.push_back(Cand{0.0, v, g.perm[v]});
+          }
           sc.assign(levels, -1);
           for (size_t j = 0; j < spec.size() && j < static_cast<size_t>(levels); ++j) sc[j] = spec[j].v;
           c.tab_off = 0;

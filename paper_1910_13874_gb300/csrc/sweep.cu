@@ -512,9 +512,13 @@ __device__ __forceinline__ void run_unit(const SweepArgs& a, const Src& src, int
 
 constexpr int kCandSlots = 16;
 
-// One warp per unit, one CTA per eight units.
+// One warp per unit, one CTA per eight units. The 8-column lookahead sweep is held to 48
+// registers (five CTAs per SM) and the 4-column candidate batch to 64 (four CTAs): their gathers
+// wait on memory, and the extra resident warps hide more latency than the few spilled registers
+// cost (measured on R-MAT scale 22).
 template <typename T, int C, int MODE>
-__global__ void __launch_bounds__(kThreads) sweep_kernel(const SweepArgs a) {
+__global__ void __launch_bounds__(kThreads, (MODE == MODE_LOOK && C == 8) ? 5 : (MODE == MODE_CAND && C == 4) ? 4 : 1)
+    sweep_kernel(const SweepArgs a) {
   __shared__ int s_cand[kCandSlots];
   __shared__ int s_rp[kWarps][kUnitRowsMax + 1];
   if (threadIdx.x < kCandSlots)
@@ -621,6 +625,7 @@ gedwalk_status launch_sweep(int mode, bool fp64, int cols, const SweepArgs& a, c
   GW_CASE(MODE_FUSED, double, 1)
   GW_CASE(MODE_FUSED, double, 2)
   GW_CASE(MODE_FUSED, double, 4)
+  GW_CASE(MODE_CAND, float, 4)
   GW_CASE(MODE_CAND, float, 8)
   GW_CASE(MODE_CAND, float, 16)
   GW_CASE(MODE_CAND, double, 4)
