@@ -181,36 +181,51 @@ gedwalk_status Workspace::ensure_pinned(size_t need) {
 
 
 // First malformed row (or -1) and a reason.
-// Entry checks of an uploaded CSR, one warp per row: column in range, and (full) no self-loop,
-// strictly increasing rows and (symmetric) the reverse entry present, by binary search in the
-// other row. The smallest offending (row << 3 | kind) wins.
+// Entry checks of an uploaded CSR: column in range, and (full) no self-loop, strictly increasing
+// rows and (symmetric) the reverse entry present, by binary search in the other row. The smallest
+// offending (row << 3 | kind) wins. Entries [b, e) of row v, whose row starts at r0.
+__device__ __forceinline__ void check_entries(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                              int32_t n, int full, int symmetric, int64_t v, int32_t r0, int32_t b,
+                                              int32_t e, int lane, unsigned long long* __restrict__ bad) {
+  for (int32_t j = b + lane; j < e; j += 32) {
+    const int32_t u = ci[j];
+    int k = 0;
+    if (u < 0 || u >= n) {
+      k = 1;
+    } else if (full) {
+      if (u == v) {
+        k = 2;
+      } else if (j > r0 && ci[j - 1] >= u) {
+        k = 3;
+      } else if (symmetric) {
+        int32_t lo = rp[u], hi = rp[u + 1];
+        while (lo < hi) {  // first entry of row u that is >= v
+          const int32_t mid = lo + ((hi - lo) >> 1);
+          if (ci[mid] < v) lo = mid + 1;
+          else hi = mid;
+        }
+        if (lo == rp[u + 1] || ci[lo] != v) k = 4;
+      }
+    }
+    if (k) atomicMin(bad, (static_cast<unsigned long long>(v) << 3) | static_cast<unsigned long long>(k));
+  }
+}
+
+// One warp per row of at most kCheckPiece entries; longer rows come as pieces in `pieces`
+// ({row, first entry, end}), so that no warp walks a hub row alone.
+constexpr int32_t kCheckPiece = 1024;
 __global__ void validate_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, int32_t n,
-                                int full, int symmetric, unsigned long long* __restrict__ bad) {
+                                int full, int symmetric, const int4* __restrict__ pieces, int64_t npieces,
+                                unsigned long long* __restrict__ bad) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t(gridDim.x) * blockDim.x) >> 5;
-  for (int64_t v = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
-    const int32_t b = rp[v], e = rp[v + 1];
-    for (int32_t j = b + lane; j < e; j += 32) {
-      const int32_t u = ci[j];
-      int k = 0;
-      if (u < 0 || u >= n) {
-        k = 1;
-      } else if (full) {
-        if (u == v) {
-          k = 2;
-        } else if (j > b && ci[j - 1] >= u) {
-          k = 3;
-        } else if (symmetric) {
-          int32_t lo = rp[u], hi = rp[u + 1];
-          while (lo < hi) {  // first entry of row u that is >= v
-            const int32_t mid = lo + ((hi - lo) >> 1);
-            if (ci[mid] < v) lo = mid + 1;
-            else hi = mid;
-          }
-          if (lo == rp[u + 1] || ci[lo] != v) k = 4;
-        }
-      }
-      if (k) atomicMin(bad, (static_cast<unsigned long long>(v) << 3) | static_cast<unsigned long long>(k));
+  for (int64_t w = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; w < n + npieces; w += warps) {
+    if (w < n) {
+      const int32_t b = rp[w], e = rp[w + 1];
+      if (e - b <= kCheckPiece) check_entries(rp, ci, n, full, symmetric, w, b, b, e, lane, bad);
+    } else {
+      const int4 pc = pieces[w - n];
+      check_entries(rp, ci, n, full, symmetric, pc.x, rp[pc.x], pc.y, pc.z, lane, bad);
     }
   }
 }
@@ -294,13 +309,23 @@ static int64_t validate_csr(const int32_t* rp, const int32_t* drp, const int32_t
       return v;
     }
   if (nnz == 0) return -1;
-  DevBuf dbad;
+  std::vector<int4> pieces;  // rows above kCheckPiece entries, cut into pieces
+  for (int32_t v = 0; v < n; ++v)
+    if (rp[v + 1] - rp[v] > kCheckPiece)
+      for (int32_t b = rp[v]; b < rp[v + 1]; b += kCheckPiece)
+        pieces.push_back(make_int4(v, b, std::min(rp[v + 1], b + kCheckPiece), 0));
+  DevBuf dbad, dpieces;
   unsigned long long hbad = ~0ull;
   if ((*st = dbad.ensure(sizeof(hbad), 0)) != GEDWALK_OK) return -1;
+  if ((*st = dpieces.ensure(std::max<size_t>(pieces.size(), 1) * sizeof(int4), 0)) != GEDWALK_OK) return -1;
   cudaError_t e = cudaMemcpy(dbad.p, &hbad, sizeof(hbad), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !pieces.empty())
+    e = cudaMemcpy(dpieces.p, pieces.data(), pieces.size() * sizeof(int4), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) {
-    const int64_t blocks = std::min<int64_t>((static_cast<int64_t>(n) * 32 + 255) / 256, 152 * 32);
+    const int64_t work = static_cast<int64_t>(n) + static_cast<int64_t>(pieces.size());
+    const int64_t blocks = std::min<int64_t>((work * 32 + 255) / 256, 152 * 32);
     validate_kernel<<<static_cast<int>(blocks), 256>>>(drp, dci, n, full ? 1 : 0, symmetric ? 1 : 0,
+                                                       dpieces.as<int4>(), static_cast<int64_t>(pieces.size()),
                                                        dbad.as<unsigned long long>());
     e = cudaGetLastError();
   }

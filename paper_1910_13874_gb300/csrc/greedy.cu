@@ -82,13 +82,16 @@ __device__ __forceinline__ void topk_push(float (&v)[kTopK], int (&id)[kTopK], f
   }
 }
 
-// Block-wide top-K of the threads' sorted lists (NT threads); thread 0 writes out[0..K).
+// Block-wide top-K of the threads' sorted lists (NT threads); out[0..K) is written (by thread 0)
+// before the closing barrier. First every warp draws its own top K (K rounds of a warp-wide argmax
+// over the lanes' list heads, the winning lane popping its head), then warp 0 merges the NT/32
+// sorted warp lists the same way. Ids are distinct across the lists, so one lane pops per round.
 template <int NT>
 __device__ void block_topk(float (&v)[kTopK], int (&id)[kTopK], float* out_v, int* out_id) {
-  __shared__ float sv[NT / 32];
-  __shared__ int sid[NT / 32];
-  __shared__ float bv_s;
-  __shared__ int bi_s;
+  constexpr int NW = NT / 32;
+  static_assert(NW <= 32, "one lane per warp list in the merge");
+  __shared__ float wv[NW][kTopK];
+  __shared__ int wi[NW][kTopK];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int round = 0; round < kTopK; ++round) {
     float bv = v[0];
@@ -103,25 +106,10 @@ __device__ void block_topk(float (&v)[kTopK], int (&id)[kTopK], float* out_v, in
       }
     }
     if (lane == 0) {
-      sv[warp] = bv;
-      sid[warp] = bi;
+      wv[warp][round] = bv;
+      wi[warp][round] = bi;
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      float b = sv[0];
-      int i0 = sid[0];
-      for (int w = 1; w < NT / 32; ++w)
-        if (better(sv[w], sid[w], b, i0)) {
-          b = sv[w];
-          i0 = sid[w];
-        }
-      bv_s = b;
-      bi_s = i0;
-      out_v[round] = b;
-      out_id[round] = i0;
-    }
-    __syncthreads();
-    if (bi_s != INT_MAX && id[0] == bi_s && v[0] == bv_s) {
+    if (bi != INT_MAX && id[0] == bi && v[0] == bv) {
 #pragma unroll
       for (int i = 0; i < kTopK - 1; ++i) {
         v[i] = v[i + 1];
@@ -130,8 +118,36 @@ __device__ void block_topk(float (&v)[kTopK], int (&id)[kTopK], float* out_v, in
       v[kTopK - 1] = -1.0f;
       id[kTopK - 1] = INT_MAX;
     }
-    __syncthreads();
   }
+  __syncthreads();
+  if (warp == 0) {
+    int p = 0;  // lane w: the next entry of warp w's list
+    for (int round = 0; round < kTopK; ++round) {
+      float hv = -1.0f;
+      int hi = INT_MAX;
+      if (lane < NW && p < kTopK) {
+        hv = wv[lane][p];
+        hi = wi[lane][p];
+      }
+      float bv = hv;
+      int bi = hi;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (better(ov, oi, bv, bi)) {
+          bv = ov;
+          bi = oi;
+        }
+      }
+      if (lane == 0) {
+        out_v[round] = bv;
+        out_id[round] = bi;
+      }
+      if (bi != INT_MAX && hi == bi && hv == bv) ++p;
+    }
+  }
+  __syncthreads();
 }
 
 // mtab row 0 = phi^miss_0 = 1_{V\S}; X column 0 (fused) = the same; candidate columns = e_c.
