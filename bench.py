@@ -7,12 +7,14 @@ b=c=0.19, d=0.05; symmetrised, deduplicated, self-loops removed, labels permuted
 alpha = 1/(1+d_max), epsilon = 1e-4 (L from the bound at epsilon/k). One "step" is one
 whole maximisation with the graph resident in HBM. It prints ONE JSON line.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload rmat|ba|ba64|batch|serve|small]
+  python bench.py [--gpus N] [--steps K] [--warmup W]
+                  [--workload rmat|rmat_s|rmat_a|rmat_w|ba|ba64|batch|serve|small]
   python bench.py --impl reference ...   # the CPU oracle on this host's cores, same metric
 
-Metric: GTEPS = k * 2L * nnz / seconds (per greedy step the method must at least
-recompute the L walk vectors for the new group and the L walk columns of the chosen
-vertex; each such sweep traverses every directed entry once).
+Metric: GTEPS = sum over the k steps of 2 l * nnz / seconds (= k * 2L * nnz at a fixed L: per
+greedy step the method must at least recompute the L walk vectors for the new group and the L
+walk columns of the chosen vertex; each such sweep traverses every directed entry once). The
+library's lookahead sweeps carry several steps per run, so it does fewer sweeps than that.
 Multi-GPU: the path does not shard; every rank runs an independent replica (weak scaling).
 """
 from __future__ import annotations
@@ -189,9 +191,9 @@ def roofline(prof, workload_key):
 
 
 def l2_note(n, nnz):
-    """How the timed region avoids a warm L2: inputs larger than the 126 MB L2, or say they fit."""
+    """How the timed region avoids a warm L2: inputs larger than the L2, or say that they fit."""
     mb = (nnz + n) * 4 / 1e6
-    if mb > 126:
+    if (nnz + n) * 4 > L2_BYTES:
         return "inputs larger than L2 (CSR %.0f MB)" % mb
     return "inputs fit in L2 (CSR %.1f MB), not flushed: a latency-bound small case" % mb
 
