@@ -125,7 +125,12 @@ GEDWALK_API gedwalk_status gedwalk_set_allocator(gedwalk_alloc_fn alloc, gedwalk
  *  flags: GEDWALK_UPLOAD_TRUSTED skips validation (a malformed graph then gives
  *  unspecified results, never a device fault: indices are still range-checked).
  * The library relabels vertices by decreasing degree internally (ties by id) for
- * gather locality; results are always reported in the caller's ids.
+ * gather locality; results are always reported in the caller's ids. The arrays
+ * are copied to the device once; the checks, the relabelling and the sorting of
+ * every row run there (the upload briefly holds a second copy of col_idx on the
+ * device). The call returns after the device work is done.
+ * GEDWALK_UPLOAD_DIRECTED: the rows are successor lists of a directed graph (see
+ * the flag); no symmetry is required.
  * On success *out receives a handle to release with gedwalk_graph_free.
  * Errors: INVALID (malformed input, with the first offending row named in
  * gedwalk_last_error), OOM, DEVICE.
@@ -266,6 +271,12 @@ GEDWALK_API gedwalk_status gedwalk_gains(gedwalk_graph_t g, const int32_t* S, in
  * where splitmix64(x) is the first output of that generator started from state x;
  * an empty sample falls back to all of V \ S. The argmax within the sample is exact.
  * It cannot be combined with GEDWALK_GAINS_ALL or an init group.
+ * Without a flag, on an undirected graph, each run of sweeps also computes the
+ * next steps' phi^miss vectors and exact gains for guessed winners (lookahead):
+ * a step whose winner was guessed needs no sweep. Every pick is still certified
+ * against the bounds of the actual group, so the results do not depend on it.
+ * The environment variable GEDWALK_LOOKAHEAD (1 = off, 2, 4; 8 in FP32) sets
+ * the number of steps per run (default 4 in FP32, 2 in FP64).
  * GEDWALK_ADAPTIVE_L runs the lazy greedy of Algorithm 2 (Section 3.2.3): the
  * walk length l starts at 1 and only doubles. At each step u, the vertex with the
  * largest L_l(S, u) = GED_{<=l}(S, u), is taken when it is separated from v, the
