@@ -60,6 +60,30 @@ def test_reference_arm_small_config():
     assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "GTEPS"
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0
+    # the same keys as the GPU arm's line, so that the two lines compare one to one
+    for key in ("metric", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling", "dtype", "data"):
+        assert key in d, key
+    assert set(d["config"]) == {"workload", "n", "nnz", "d_max", "alpha", "epsilon", "L", "k", "parallelism", "l2"}
+    assert d["ms_per_step"] > 0 and d["config"]["L"] == 34
+
+
+def test_reference_arm_declines_sampled_and_adaptive_workloads():
+    for wl in ("rmat_s", "rmat_a", "batch"):
+        out = subprocess.run([sys.executable, "-c", "import sys, bench; sys.argv=['bench.py','--impl','reference',"
+                              f"'--workload','{wl}']; import json; a=bench.parse(); print(json.dumps(bench.run_reference(a)))"],
+                             cwd=ROOT, capture_output=True, text=True, timeout=120)
+        assert out.returncode == 0, out.stderr
+        d = json.loads(out.stdout.strip().splitlines()[-1])
+        assert d["impl"] == "reference" and "unavailable" in d
+
+
+def test_l2_note():
+    import importlib
+
+    sys.path.insert(0, ROOT)
+    bench = importlib.import_module("bench")
+    assert bench.l2_note(4_194_304, 128_309_616).startswith("inputs larger than L2")
+    assert bench.l2_note(1000, 10_206).startswith("inputs fit in L2")
 
 
 def test_reference_arm_other_ranks_print_nothing():
