@@ -181,8 +181,12 @@ def roofline(prof, workload_key):
     all_ach = prof["sweep_bytes"] / (prof["sweep_ms"] / 1e3) / 1e9 if prof["sweep_ms"] > 0 else 0.0
     kname = (f"sweep_kernel<{'double' if prof['top_fp64'] else 'float'}, {prof['top_cols']}, "
              f"{prof['top_mode']}> ({MODE_NAMES.get(prof['top_mode'], '?')})")
+    traffic = recorded_traffic(prof, workload_key)
+    avg_s = ms / max(n, 1) / 1e3
     return {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-            "frac": round(achieved / hbm, 4), "traffic": recorded_traffic(prof, workload_key),
+            "frac": round(achieved / hbm, 4), "traffic": traffic,
+            # DRAM bytes actually moved per launch (the ncu counters) over the measured launch time
+            "dram_gbs": round(traffic / avg_s / 1e9, 1) if traffic and avg_s > 0 else None,
             "peak_kind": peak_kind, "kernel": kname, "launches_timed": n,
             "avg_launch_us": round(ms / max(n, 1) * 1e3, 1),
             "algorithmic_bytes_per_launch": round(by / max(n, 1)),
@@ -313,6 +317,8 @@ def run_greedy(args, spec, rank, world, local):
                    "sweeps_per_run": stats["sweeps"], "spec_misses": stats["spec_misses"],
                    "ell_per_step": {int(v): int(c) for v, c in zip(*np.unique(ell, return_counts=True))},
                    "separation_failures": sep_fail,
+                   # every sweep launched, whatever its columns, traverses each entry once
+                   "gteps_sweeps": round(stats["sweeps"] * G.nnz / t_step / 1e9, 3),
                    "group_head": [int(x) for x in grp[:10]], "score": score},
         "upload_s": round(upload_s, 3),
     }

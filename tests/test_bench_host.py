@@ -92,3 +92,22 @@ def test_reference_arm_other_ranks_print_nothing():
                           "--warmup", "0"], cwd=ROOT, capture_output=True, text=True, timeout=300, env=env)
     assert out.returncode == 0, out.stderr
     assert out.stdout.strip() == ""
+
+
+def test_roofline_fields_from_profiler_counters():
+    # the dominant kernel's algorithmic bytes over its measured time, against the measured peak;
+    # DRAM GB/s only when a committed ncu summary matches the kernel and its source hash
+    import importlib
+
+    sys.path.insert(0, ROOT)
+    bench = importlib.import_module("bench")
+    prof = {"top_ms": 600.0, "top_bytes": 866_084_292 * 1000, "top_launches": 1000, "sweep_bytes": 1e12,
+            "sweep_ms": 700.0, "sweep_launches": 1200, "top_fp64": 0, "top_cols": 8, "top_mode": 5}
+    r = bench.roofline(prof, "rmat22")
+    assert r["unit"] == "GB/s" and r["bound"] == "hbm"
+    assert abs(r["achieved"] - 866_084_292 / 600e-6 / 1e9) < 0.1
+    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-4
+    assert r["kernel"].startswith("sweep_kernel<float, 8, 5>")
+    if r["traffic"] is not None:
+        assert abs(r["dram_gbs"] - r["traffic"] / 600e-6 / 1e9) < 0.1
+    assert bench.roofline(dict(prof, top_mode=4), "rmat22")["traffic"] is None  # no summary for that kernel
