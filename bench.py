@@ -255,7 +255,7 @@ def oracle_greedy_sample(g, spec, L, budget_s=20.0, w=None):
             break
     t = time.perf_counter() - t0
     gteps = steps * 2 * L * g.nnz / t / 1e9
-    return {"value": gteps, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+    return {"value": gteps, "unit": "GTEPS", "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
             "sample": f"{steps} of {spec['k']} greedy steps (lazy oracle, FP64, single thread) on the same graph, "
                       f"{t:.1f} s"}
 
@@ -408,7 +408,7 @@ def run_batch(args, spec, rank, world, local):
             oracle.score(g, mem[off[cnt]:off[cnt + 1]], alpha, L)
             cnt += 1
         tc = time.perf_counter() - t0
-        out["cpu_baseline"] = {"value": round(cnt / tc, 3), "unit": "queries/s", "cores": 1, "kind": "oracle",
+        out["cpu_baseline"] = {"value": round(cnt / tc, 3), "unit": "queries/s", "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
                                "sample": f"{cnt} of {spec['groups']} groups scored by the FP64 oracle, {tc:.1f} s"}
     del np
     return out
@@ -508,7 +508,7 @@ def run_reference(args):
             "config": {"workload": spec["name"], "n": g.n, "nnz": g.nnz, "d_max": oracle.dmax(g), "alpha": alpha,
                        "epsilon": spec["eps"], "L": L, "k": spec["k"], "parallelism": f"replicas x{world}",
                        "l2": l2_note(g.n, g.nnz)},
-            "cpu_baseline": {"value": round(v, 6), "unit": "GTEPS", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": round(v, 6), "unit": "GTEPS", "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
                              "sample": timed[-1]["sample"]},
             "e2e": {"value": round(v, 6), "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
