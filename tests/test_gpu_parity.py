@@ -80,6 +80,32 @@ def test_truncation_length_matches_oracle(cuda_device, name, eps):
     assert rel(B, Bo) < 1e-12
 
 
+def _golden_truncations():
+    import os
+
+    path = os.path.join(os.path.dirname(__file__), "golden", "comb_bound.txt")
+    return [tuple(x.strip() for x in ln.split(";")) for ln in open(path)
+            if ln.strip() and not ln.startswith("#") and ln.startswith("L ")]
+
+
+@pytest.mark.parametrize("rec", _golden_truncations(), ids=lambda r: "-".join(r[1:4]))
+def test_truncation_length_matches_hand_values(cuda_device, rec):
+    # Eq. comb-bound and Algorithm 1's strict stop test against values derived by hand
+    # (tests/golden/comb_bound.txt), independent of the oracle: the device's walk totals and
+    # its first-crossing test must give the same L and B_L.
+    from fractions import Fraction
+
+    from paper_1910_13874_gb300 import gedwalk
+
+    cube = gg.from_edges(8, [(u, v) for u in range(8) for v in range(u + 1, 8) if bin(u ^ v).count("1") == 1])
+    g = {"K4": gg.complete(4), "C5": gg.cycle(5), "star3": gg.star(3), "Q3": cube}[rec[1]]
+    G = gedwalk.Graph.from_host(g)
+    L, B = G.truncation(float(Fraction(rec[2])), float(rec[3]))
+    assert L == int(rec[4])
+    assert rel(B, float(Fraction(rec[5]))) < 1e-14
+    G.free()
+
+
 # ------------------------------------------------------------------ scoring one group
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_score_small_config_16_groups(cuda_device, prec):

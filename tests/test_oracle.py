@@ -257,6 +257,109 @@ def test_select_L_is_first_crossing_and_monotone():
     assert oracle.select_L(g, 1.0 / g.d_max, 1e-4)[0] == -1
 
 
+BOUND_GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "comb_bound.txt")
+
+
+def _cube3():
+    return gg.from_edges(8, [(u, v) for u in range(8) for v in range(u + 1, 8) if bin(u ^ v).count("1") == 1])
+
+
+def _petersen():
+    outer = [(i, (i + 1) % 5) for i in range(5)]
+    inner = [(5 + i, 5 + (i + 2) % 5) for i in range(5)]
+    spokes = [(i, i + 5) for i in range(5)]
+    return gg.from_edges(10, outer + inner + spokes)
+
+
+_NAMED = {"K4": lambda: gg.complete(4), "C5": lambda: gg.cycle(5), "star3": lambda: gg.star(3), "Q3": _cube3}
+
+
+def _parse_bound_golden():
+    recs = []
+    for line in open(BOUND_GOLDEN):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        f = [x.strip() for x in line.split(";")]
+        recs.append(tuple(f))
+    return recs
+
+
+@pytest.mark.parametrize("rec", _parse_bound_golden(), ids=lambda r: "-".join(r[:4]))
+def test_comb_bound_hand_values(rec):
+    # Eq. comb-bound and Algorithm 1's stop test against values derived by hand
+    # (tests/golden/comb_bound.txt): a dropped alpha, alpha^l for alpha^{l+1}, a wrong
+    # d/(1 - alpha d), an average degree for d_max or an off-by-one in l all change them.
+    from fractions import Fraction
+
+    g = _NAMED[rec[1]]()
+    alpha = float(Fraction(rec[2]))
+    if rec[0] == "B":
+        l, want = int(rec[3]), float(Fraction(rec[4]))
+        _, Wa = oracle.walk_totals(g, alpha, l)
+        assert _rel(oracle.comb_bound(g, alpha, Wa[l]), want) < 1e-14
+    else:
+        L, B = oracle.select_L(g, alpha, float(rec[3]))
+        assert L == int(rec[4])
+        assert _rel(B, float(Fraction(rec[5]))) < 1e-14
+
+
+def _dense_tail(g, alpha, upto=4000):
+    """alpha^i W_i for i = 1..upto from dense powers of the adjacency matrix (numpy)."""
+    A = g.to_dense().astype(float)
+    v, terms = np.ones(g.n), [0.0]
+    for _ in range(upto):
+        v = alpha * (A @ v)
+        terms.append(float(v.sum()))
+        if terms[-1] < 1e-30 * max(terms):
+            break
+    return np.array(terms)
+
+
+@pytest.mark.parametrize("name,d", [("C7", 2), ("K6", 5), ("Q3", 3), ("petersen", 3)])
+@pytest.mark.parametrize("frac", [None, 0.5, 0.9])
+def test_comb_bound_is_tight_on_regular_graphs(name, d, frac):
+    # On a d-regular graph W_{l+j} = d^j W_l, so the whole-graph tail sum_{i>l} alpha^i W_i equals
+    # the bound of Eq. comb-bound exactly: the pin holds from both sides, not only tail <= B_l.
+    g = {"C7": lambda: gg.cycle(7), "K6": lambda: gg.complete(6), "Q3": _cube3, "petersen": _petersen}[name]()
+    assert oracle.dmax(g) == d and np.all(np.diff(g.row_ptr) == d)
+    alpha = 1.0 / (d + 1) if frac is None else frac / d
+    terms = _dense_tail(g, alpha)
+    _, Wa = oracle.walk_totals(g, alpha, 8)
+    for l in range(1, 9):
+        tail = terms[l + 1:].sum()
+        closed = g.n * (alpha * d) ** (l + 1) / (1.0 - alpha * d)  # geometric series of n (alpha d)^i
+        assert _rel(tail, closed) < 1e-11
+        assert _rel(oracle.comb_bound(g, alpha, Wa[l]), tail) < 1e-11
+        # the oracle's own two-state score at S = V gives the same tail (GED_{>l}(V))
+        if frac is None:
+            fullV = oracle.score(g, list(range(g.n)), alpha, 600)
+            partV = oracle.score(g, list(range(g.n)), alpha, l)
+            assert _rel(fullV - partV, tail) < 1e-9
+        # Lemma spectral-bound with sigma_max = d is sqrt(|V|) times the true tail
+        assert _rel(oracle.spectral_bound(g, alpha, Wa[l], float(d)), math.sqrt(g.n) * tail) < 1e-11
+
+
+@pytest.mark.parametrize("name,d", [("C7", 2), ("K6", 5), ("Q3", 3)])
+@pytest.mark.parametrize("eps", [1e-2, 1e-4, 1e-7])
+def test_select_L_matches_closed_form_on_regular_graphs(name, d, eps):
+    # L = min{l >= 1 : n (alpha d)^{l+1} / (1 - alpha d) < eps}, evaluated in exact rationals
+    from fractions import Fraction
+
+    g = {"C7": lambda: gg.cycle(7), "K6": lambda: gg.complete(6), "Q3": _cube3}[name]()
+    a = Fraction(1, d + 1)
+    e = Fraction(eps)
+    l = 1
+    while g.n * (a * d) ** (l + 1) / (1 - a * d) >= e:
+        l += 1
+    B = g.n * (a * d) ** (l + 1) / (1 - a * d)
+    # the crossing is far from a rounding boundary at these parameters
+    assert abs(float(B / e) - 1) > 1e-6 and abs(float(B / (a * d) / e) - 1) > 1e-6
+    L, BL = oracle.select_L(g, float(a), eps)
+    assert L == l
+    assert _rel(BL, float(B)) < 1e-13
+
+
 @pytest.mark.parametrize("kind,seed", [("er", 1), ("er", 2), ("ba", 3), ("ba", 4), ("rmat", 5)])
 def test_greedy_all_vertex_equals_lazy(kind, seed):
     if kind == "er":
