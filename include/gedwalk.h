@@ -118,7 +118,9 @@ typedef void (*gedwalk_free_fn)(void* ptr, size_t bytes, int64_t stream, void* c
 GEDWALK_API gedwalk_status gedwalk_set_allocator(gedwalk_alloc_fn alloc, gedwalk_free_fn release, void* ctx);
 
 /*
- * Uploads a graph to the current CUDA device.
+ * Uploads a graph to the current CUDA device (Section 2: an undirected,
+ * unweighted graph G = (V, E); each edge {u, v} is stored as the two entries
+ * (u, v) and (v, u), the two 1-walks it carries).
  *  row_ptr: host int32[n+1], row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz.
  *  col_idx: host int32[nnz], see the conventions above.
  *  n >= 1; nnz >= 0 and < 2^31.
@@ -376,8 +378,9 @@ GEDWALK_API gedwalk_status gedwalk_serve_destroy(gedwalk_server_t srv);
  *    next length. Both 8-byte aligned; they must not overlap. A score starts from
  *    x = (1_S, 1_{V\S}) and applies the step L times, swapping x and y.
  *  alpha: the damping factor (> 0).
- *  d_hit_sum: device double[1], receives sum_v hit'(v), i.e. alpha^i phi_i(S) of
- *    this step (Eq. phisum); the score is the sum over the L steps.
+ *  d_hit_sum: device double[1] (8-byte aligned), receives sum_v hit'(v), the
+ *    alpha^i-weighted count of the i-walks that hit S; the score is the sum over
+ *    the L steps.
  *  stream: cudaStream_t (0 = default). The call is asynchronous.
  * Scratch: a fixed 512 KiB device array inside the library (per GPU, held until
  * the process exits) limits n to 16,777,216; larger n returns

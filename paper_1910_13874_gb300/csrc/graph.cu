@@ -484,7 +484,10 @@ gedwalk_status reduce_slots(Graph& g, Workspace& ws, int nsum, double* out, cuda
 
 // ---------------------------------------------------------------- walk totals
 gedwalk_status ensure_totals(Graph& g, double alpha, int32_t rows, cudaStream_t s) {
-  if (g.tt_alpha == alpha && rows <= g.tt_rows) return GEDWALK_OK;
+  {
+    std::shared_lock<std::shared_mutex> rl(g.tt_lock);
+    if (g.tt_alpha == alpha && rows <= g.tt_rows) return GEDWALK_OK;
+  }
   std::unique_lock<std::shared_mutex> wl(g.tt_lock);
   if (g.tt_alpha != alpha) {
     g.tt_alpha = alpha;

@@ -227,16 +227,19 @@ __device__ __forceinline__ float to_f32_up(double v) { return __double2float_ru(
 // in FP32 with every operation rounded toward +infinity on non-negative inputs (FP64 inputs are
 // first rounded up), so the result never falls below the bound of the stored vectors.
 template <typename T, int L>
-__device__ __forceinline__ float ub_fixed(const T* __restrict__ col, const T* __restrict__ zcol, int32_t n) {
+__device__ __forceinline__ float ub_fixed(const T* __restrict__ col, const T* __restrict__ zcol, int32_t n, float m0) {
+  // row 0 is phi^miss_0 = psi^miss_0 = 1_{V\S}: m0, not read from the tables
   float y[L + 1], z[L + 1];
+  y[0] = m0;
 #pragma unroll
-  for (int a = 0; a <= L; ++a) y[a] = to_f32_up(__ldcs(col + static_cast<size_t>(a) * n));
+  for (int a = 1; a <= L; ++a) y[a] = to_f32_up(__ldcs(col + static_cast<size_t>(a) * n));
   if (zcol == col) {
 #pragma unroll
     for (int a = 0; a <= L; ++a) z[a] = y[a];
   } else {
+    z[0] = m0;
 #pragma unroll
-    for (int a = 0; a <= L; ++a) z[a] = to_f32_up(__ldcs(zcol + static_cast<size_t>(a) * n));
+    for (int a = 1; a <= L; ++a) z[a] = to_f32_up(__ldcs(zcol + static_cast<size_t>(a) * n));
   }
   float Q[L + 1];
   Q[0] = z[0];
@@ -253,18 +256,20 @@ __device__ __forceinline__ float ub_fixed(const T* __restrict__ col, const T* __
 }
 
 template <typename T>
-__device__ float ub_any(const T* __restrict__ col, const T* __restrict__ zcol, int32_t n, int32_t L) {
+__device__ float ub_any(const T* __restrict__ col, const T* __restrict__ zcol, int32_t n, int32_t L, float m0) {
+  auto yv = [&](int a) { return a == 0 ? m0 : to_f32_up(col[static_cast<size_t>(a) * n]); };
+  auto zv = [&](int b) { return b == 0 ? m0 : to_f32_up(zcol[static_cast<size_t>(b) * n]); };
   float ub = 0.0f;
   for (int i = 1; i <= L; ++i)
-    for (int j = 0; j <= i; ++j)
-      ub = __fmaf_ru(to_f32_up(col[static_cast<size_t>(i - j) * n]), to_f32_up(zcol[static_cast<size_t>(j) * n]), ub);
+    for (int j = 0; j <= i; ++j) ub = __fmaf_ru(yv(i - j), zv(j), ub);
   return ub;
 }
 
-// Lemma-initialize bound + selection over all vertices. LF = L when L <= 16, else 0 (any L).
+// Lemma-initialize bound + selection over vertices [0, n_scan) (the tables have n rows apart).
+// LF = L when L <= 16, else 0 (any L).
 template <typename T, int LF>
 __global__ void __launch_bounds__(kThreads) ub_select(const T* __restrict__ mtab, const T* __restrict__ ztab,
-                                                     int32_t L, int32_t n,
+                                                     int32_t L, int32_t n, int32_t n_scan,
                                                      const uint32_t* __restrict__ mask,
                                                      const Stale* __restrict__ stale, int32_t step,
                                                      const int32_t* __restrict__ perm, float* __restrict__ sel_v,
@@ -280,24 +285,26 @@ __global__ void __launch_bounds__(kThreads) ub_select(const T* __restrict__ mtab
   }
   // four vertices per iteration, all of their loads issued before any decision
   const int32_t stride = gridDim.x * blockDim.x;
-  for (int32_t base = blockIdx.x * blockDim.x + threadIdx.x; base < n; base += 4 * stride) {
+  for (int32_t base = blockIdx.x * blockDim.x + threadIdx.x; base < n_scan; base += 4 * stride) {
     float b[4];
     bool live[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int32_t xr = base + k * stride;
-      const int32_t x = xr < n ? xr : n - 1;
+      const int32_t x = xr < n_scan ? xr : n_scan - 1;
       const bool inS = (__ldg(mask + (x >> 5)) >> (x & 31)) & 1u;
       const Stale st = stale[x];
-      float ub = LF > 0 ? ub_fixed<T, (LF > 0 ? LF : 1)>(mtab + x, ztab + x, n) : ub_any<T>(mtab + x, ztab + x, n, L);
+      const float m0 = inS ? 0.0f : 1.0f;
+      float ub = LF > 0 ? ub_fixed<T, (LF > 0 ? LF : 1)>(mtab + x, ztab + x, n, m0)
+                        : ub_any<T>(mtab + x, ztab + x, n, L, m0);
       if (st.step >= 0 && st.ub < ub) ub = st.ub;
       b[k] = ub;
       bool in_sample = true;
-      if (smp.thr != ~0ull && xr < n && !inS)
+      if (smp.thr != ~0ull && xr < n_scan && !inS)
         in_sample = sample_hash(smp.seed, smp.step, static_cast<uint32_t>(__ldg(perm + x))) < smp.thr;
-      if (xr < n && !inS && in_sample) ++nsampled;
+      if (xr < n_scan && !inS && in_sample) ++nsampled;
       // evaluated with the current S: its exact gain is known
-      live[k] = xr < n && !inS && in_sample && st.step != step;
+      live[k] = xr < n_scan && !inS && in_sample && st.step != step;
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -326,19 +333,19 @@ __global__ void __launch_bounds__(kThreads) ub_select(const T* __restrict__ mtab
 
 template <typename T>
 cudaError_t launch_ub_select(int nb, cudaStream_t s, const T* mtab, const T* ztab, int32_t L, int32_t n,
-                             const uint32_t* mask,
+                             int32_t n_scan, const uint32_t* mask,
                              const Stale* stale, int32_t step, const int32_t* perm, float* sel_v, int* sel_id,
                              int32_t* zero_min, const Sampling& smp, int32_t* sampled) {
 #define GW_UB(LL)                                                                                          \
   case LL:                                                                                                 \
-    ub_select<T, LL><<<nb, kThreads, 0, s>>>(mtab, ztab, L, n, mask, stale, step, perm, sel_v, sel_id, zero_min, smp, \
+    ub_select<T, LL><<<nb, kThreads, 0, s>>>(mtab, ztab, L, n, n_scan, mask, stale, step, perm, sel_v, sel_id, zero_min, smp, \
                                              sampled);                                                     \
     break;
   switch (L) {
     GW_UB(1) GW_UB(2) GW_UB(3) GW_UB(4) GW_UB(5) GW_UB(6) GW_UB(7) GW_UB(8)
     GW_UB(9) GW_UB(10) GW_UB(11) GW_UB(12) GW_UB(13) GW_UB(14) GW_UB(15) GW_UB(16)
     default:
-      ub_select<T, 0><<<nb, kThreads, 0, s>>>(mtab, ztab, L, n, mask, stale, step, perm, sel_v, sel_id, zero_min, smp,
+      ub_select<T, 0><<<nb, kThreads, 0, s>>>(mtab, ztab, L, n, n_scan, mask, stale, step, perm, sel_v, sel_id, zero_min, smp,
                                               sampled);
   }
 #undef GW_UB
@@ -625,11 +632,16 @@ gedwalk_status maximize_impl(Graph& g, Workspace& ws, int32_t k, const Resolved&
   while (adaptive && ell_max < r.L) ell_max *= 2;
   const int32_t L = adaptive ? ell_max : r.L;  // rows of the miss table
   double coef = 0.0;  // B_l = coef * Wa_l (Eq. comb-bound, or Lemma spectral-bound)
+  std::vector<double> Wa;  // the walk totals this run needs, copied under the table's lock
   if (adaptive) {
     GW_TRY(bound_coef(g, r.alpha, r.bound_kind, s, &coef));
     GW_TRY(ensure_totals(g, r.alpha, ell_max + 1, s));
+    std::shared_lock<std::shared_mutex> rl(g.tt_lock);
+    if (g.tt_alpha != r.alpha || g.tt_rows < ell_max + 1)
+      return fail(GEDWALK_ERR_INVALID, "the walk-total table was replaced for another alpha during the call");
+    Wa.assign(g.Wa.begin(), g.Wa.begin() + ell_max + 1);
   }
-  auto bound_at = [&](int32_t l) { return coef * g.Wa[l]; };
+  auto bound_at = [&](int32_t l) { return coef * Wa[l]; };
   ws.st_evals = ws.st_batches = ws.st_sweeps = ws.st_spec_miss = ws.st_sep_fail = 0;
   ws.st_ell.clear();
 
@@ -680,26 +692,35 @@ gedwalk_status maximize_impl(Graph& g, Workspace& ws, int32_t k, const Resolved&
     }
     return smp;
   };
-  const int nb_sel = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(kSelBlocks, (int64_t(g.n) + 1023) / 1024)));
+  // Isolated vertices (rows [n_active, n)) start and end no walk: their bound and gain are exactly
+  // 0. The bound pass skips them, and the smallest caller id among those outside S stands for
+  // them among the zero gains. Stochastic greedy scans them all: they belong to its samples.
+  // The relabelling is a stable sort by degree, so the isolated rows hold increasing caller ids.
+  const int32_t n_scan = stochastic ? g.n : g.n_active;
+  int32_t iso_next = stochastic ? g.n : g.n_active;  // first isolated row not in S
+  const int nb_sel =
+      static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(kSelBlocks, (int64_t(n_scan) + 1023) / 1024)));
   // One bound + selection pass into c.d_out / c.h_out; `step` decides which stale gains are exact.
   auto select_pass = [&](int32_t st, const Sampling& smp) -> gedwalk_status {
     reset_selection<<<1, 1, 0, s>>>(c.d_out);
     if (r.fp64)
       GW_CUDA(launch_ub_select<double>(nb_sel, s, ws.mtab.as<double>() + c.tab_off,
-                                       g.directed ? ws.ztab.as<double>() : ws.mtab.as<double>() + c.tab_off, c.L, g.n, ws.mask.as<uint32_t>(), stale, st,
-                                       g.perm_d.as<int32_t>(), sel_v, sel_id, &c.d_out->zero_min_caller, smp,
-                                       &c.d_out->sampled));
+                                       g.directed ? ws.ztab.as<double>() : ws.mtab.as<double>() + c.tab_off, c.L, g.n,
+                                       n_scan, ws.mask.as<uint32_t>(), stale, st, g.perm_d.as<int32_t>(), sel_v,
+                                       sel_id, &c.d_out->zero_min_caller, smp, &c.d_out->sampled));
     else
       GW_CUDA(launch_ub_select<float>(nb_sel, s, ws.mtab.as<float>() + c.tab_off,
-                                      g.directed ? ws.ztab.as<float>() : ws.mtab.as<float>() + c.tab_off, c.L, g.n, ws.mask.as<uint32_t>(), stale, st,
-                                      g.perm_d.as<int32_t>(), sel_v, sel_id, &c.d_out->zero_min_caller, smp,
-                                      &c.d_out->sampled));
+                                      g.directed ? ws.ztab.as<float>() : ws.mtab.as<float>() + c.tab_off, c.L, g.n,
+                                      n_scan, ws.mask.as<uint32_t>(), stale, st, g.perm_d.as<int32_t>(), sel_v,
+                                      sel_id, &c.d_out->zero_min_caller, smp, &c.d_out->sampled));
     count_launch();
     select_merge<<<1, kMergeThreads, 0, s>>>(sel_v, sel_id, nb_sel * kTopK, c.d_out);
     GW_KCHECK();
     GW_CUDA(cudaMemcpyAsync(c.h_out, c.d_out, sizeof(SelOut), cudaMemcpyDeviceToHost, s));
     GW_CUDA(cudaStreamSynchronize(s));
     read_graph_timing(ws);
+    while (iso_next < g.n && inS[iso_next]) ++iso_next;
+    if (iso_next < g.n) c.h_out->zero_min_caller = std::min(c.h_out->zero_min_caller, g.perm[iso_next]);
     return GEDWALK_OK;
   };
 

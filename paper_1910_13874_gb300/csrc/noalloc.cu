@@ -115,8 +115,9 @@ extern "C" gedwalk_status gedwalk_score_step_noalloc(const int32_t* d_row_ptr, c
                 "at most %lld rows",
                 n, static_cast<long long>(kNaMaxRows), static_cast<long long>(kNaMaxRows));
   if (!(alpha > 0.0)) return fail(GEDWALK_ERR_INVALID, "gedwalk_score_step_noalloc: alpha must be positive");
-  if ((reinterpret_cast<uintptr_t>(d_x) | reinterpret_cast<uintptr_t>(d_y)) & 7u)
-    return fail(GEDWALK_ERR_INVALID, "gedwalk_score_step_noalloc: x and y must be 8-byte aligned");
+  if ((reinterpret_cast<uintptr_t>(d_x) | reinterpret_cast<uintptr_t>(d_y) | reinterpret_cast<uintptr_t>(d_hit_sum)) &
+      7u)
+    return fail(GEDWALK_ERR_INVALID, "gedwalk_score_step_noalloc: x, y and hit_sum must be 8-byte aligned");
   double* slots = nullptr;
   GW_TRY(na_scratch(&slots));
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

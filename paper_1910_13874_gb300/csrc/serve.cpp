@@ -16,6 +16,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <deque>
 #include <thread>
@@ -265,12 +266,21 @@ gedwalk_status gedwalk_serve_submit(gedwalk_server_t h, int32_t graph, int32_t k
   {
     // resolving may extend the graph's walk-total table: serialise with its other users
     std::lock_guard<std::mutex> lk(g.mu);
+    // The walk-total table holds one alpha, the one the server prepared at creation; scoring
+    // lanes read it while other requests are submitted, so a request with another alpha is
+    // rejected before anything could replace the table under them.
+    if (p.alpha < 0.0 || std::isnan(p.alpha)) return fail(GEDWALK_ERR_INVALID, "alpha must be positive (0 = default)");
+    const double alpha = p.alpha > 0.0 ? p.alpha : g.alpha_default;
+    {
+      std::shared_lock<std::shared_mutex> rl(g.tt_lock);
+      if (g.tt_rows > 0 && alpha != g.tt_alpha)
+        return fail(GEDWALK_ERR_INVALID, "served requests use one alpha per graph (%.17g), not %.17g", g.tt_alpha,
+                    alpha);
+    }
     if (kind == GEDWALK_REQ_SCORE) {
       GW_TRY(map_group(g, S, s_len_or_k, &q->S));
       GW_TRY(resolve(g, &p, 0.0, &q->r));
       GW_TRY(ensure_totals(g, q->r.alpha, q->r.L + 1, nullptr));
-      if (q->r.alpha != g.tt_alpha)
-        return fail(GEDWALK_ERR_INVALID, "served scoring uses one alpha per graph (the first one requested)");
     } else {
       if (s_len_or_k < 0 || s_len_or_k > g.n) return fail(GEDWALK_ERR_INVALID, "k out of range");
       q->k = s_len_or_k;

@@ -22,9 +22,9 @@
 //    the row. No warp ever waits for another.
 // A row's C-wide sum is reduce-scattered across its lanes (halving the columns
 // at every shuffle step), so each lane ends with its own columns and the
-// epilogue runs column-parallel. Column sums (sum_v y(v), FP64) are reduced per
-// warp in a fixed order into per-unit slots: every result is bitwise
-// reproducible.
+// epilogue runs column-parallel. Column sums (sum_v y(v)) are accumulated per lane
+// (compensated FP32 for FP32 vectors), reduced per warp in FP64 in a fixed order
+// into per-unit slots: every result is bitwise reproducible.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -222,13 +222,86 @@ struct Sums {
   }
 };
 
+// Number of candidate ids a mode reads (the only rows whose epilogue differs from y = alpha s).
+template <int MODE, int C>
+struct Cands {
+  static constexpr int N = MODE == MODE_FUSED ? C - 1 : MODE == MODE_CAND ? C : MODE == MODE_LOOK ? C / 2 : 0;
+};
+
+// Per-lane column sums over the rows of one unit. FP64 vectors sum in FP64. FP32 vectors sum with
+// compensated FP32 additions (Kahan: the error is at most 2u * sum |y| + O(m u^2), u = 2^-24, over
+// m <= 128 rows) and convert once per unit to FP64, in which every later sum (over lanes, units and
+// sweeps) is taken. On a GB300 an FP64 addition costs about 64 FP32 ones, and one conversion and
+// one FP64 addition per row and column cost more than the rest of the epilogue.
+template <typename T, int N>
+struct ColAcc {
+  double s[N];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int k = 0; k < N; ++k) s[k] = 0.0;
+  }
+  __device__ __forceinline__ void add(int k, double y) { s[k] += y; }
+  __device__ __forceinline__ double get(int k) const { return s[k]; }
+};
+template <int N>
+struct ColAcc<float, N> {
+  float s[N], c[N];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int k = 0; k < N; ++k) s[k] = c[k] = 0.0f;
+  }
+  __device__ __forceinline__ void add(int k, float y) {
+    const float t1 = __fsub_rn(y, c[k]);
+    const float t = __fadd_rn(s[k], t1);
+    c[k] = __fsub_rn(__fsub_rn(t, s[k]), t1);
+    s[k] = t;
+  }
+  __device__ __forceinline__ double get(int k) const { return static_cast<double>(s[k]) - static_cast<double>(c[k]); }
+};
+
+// The epilogue of the rows whose warp holds a candidate row (at most kCandSlots rows of the graph;
+// every lane of the warp calls it, shuffles inside). y holds alpha * s, zeroed on S.
+template <typename T, int C, int MODE, int CPL>
+__device__ __noinline__ void candidate_rows(const SweepArgs& a, const int* __restrict__ s_cand, int r, bool valid,
+                                            int c0, int base, T (&y)[CPL]) {
+  if constexpr (MODE == MODE_FUSED) {
+    // column 0 is phi^miss under S; candidate column j >= 1 takes it at the candidate's row
+    // (every S-avoiding walk ending at c_j visits c_j)
+    const T m = __shfl_sync(kFull, y[0], base);
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) {
+      const int c = c0 + k;
+      if (valid && c >= 1 && s_cand[c - 1] == r) y[k] = m;
+    }
+  } else if constexpr (MODE == MODE_CAND) {
+#pragma unroll
+    for (int k = 0; k < CPL; ++k)
+      if (valid && s_cand[c0 + k] == r) y[k] = __ldg(static_cast<const T*>(a.Min) + r);
+  } else if constexpr (MODE == MODE_LOOK) {
+    // level d = c / 2 runs under S + {c_1..c_d}: column 2d is its phi^miss, column 2d+1 the
+    // walks through c_{d+1}, whose own row takes column 2d's value
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) {
+      const int d = (c0 + k) >> 1;
+      for (int j = 0; j < d; ++j)
+        if (valid && s_cand[j] == r) y[k] = T(0);
+    }
+    const T left = __shfl_up_sync(kFull, y[CPL - 1], 1);  // column 2d of a lane holding only 2d+1
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) {
+      const int c = c0 + k;
+      if (valid && (c & 1) && s_cand[c >> 1] == r) y[k] = CPL == 1 ? left : y[k > 0 ? k - 1 : 0];
+    }
+  }
+}
+
 // Column-parallel epilogue for row r. The calling lane holds the totals s[0..CPL) of
 // columns c0 .. c0+CPL-1; base is the first lane of the row's group. Every lane of the
 // warp calls it (shuffles inside); `store` marks the lanes that own distinct columns of a
-// valid row. cs accumulates this lane's column sums (FP64).
+// valid row. acc accumulates this lane's column sums.
 template <typename T, int C, int MODE, int CPL>
 __device__ __forceinline__ void epilogue(const SweepArgs& a, const int* __restrict__ s_cand, int r, bool valid,
-                                         bool store, int c0, int base, T (&s)[CPL], double (&cs)[CPL]) {
+                                         bool store, int c0, int base, T (&s)[CPL], ColAcc<T, CPL>& acc) {
   T* Y = static_cast<T*>(a.Y);
   constexpr bool kMasked = MODE == MODE_SCORE || MODE == MODE_FUSED || MODE == MODE_CAND || MODE == MODE_LOOK;
   const bool inS = kMasked && valid ? in_mask(a.mask, r) : false;
@@ -252,7 +325,7 @@ __device__ __forceinline__ void epilogue(const SweepArgs& a, const int* __restri
       T out[2];
       out[0] = alpha * (inS ? sh + sm : sh);
       out[1] = inS ? T(0) : alpha * sm;
-      cs[0] += static_cast<double>(out[0]);
+      acc.add(0, out[0]);
       out[0] *= sv;
       out[1] *= sv;
       store_vec<T, 2>(Y + static_cast<size_t>(r) * C, out);
@@ -261,35 +334,15 @@ __device__ __forceinline__ void epilogue(const SweepArgs& a, const int* __restri
     T y[CPL];
 #pragma unroll
     for (int k = 0; k < CPL; ++k) y[k] = inS ? T(0) : alpha * s[k];
+    if constexpr (Cands<MODE, C>::N > 0) {
+      bool special = false;
+#pragma unroll
+      for (int j = 0; j < Cands<MODE, C>::N; ++j) special |= s_cand[j] == r;
+      if (__any_sync(kFull, valid && special)) candidate_rows<T, C, MODE, CPL>(a, s_cand, r, valid, c0, base, y);
+    }
     if constexpr (MODE == MODE_FUSED) {
-      // column 0 is phi^miss under S; candidate column j >= 1 takes it at the candidate's row
-      // (every S-avoiding walk ending at c_j visits c_j)
-      const T m = __shfl_sync(kFull, y[0], base);
-#pragma unroll
-      for (int k = 0; k < CPL; ++k) {
-        const int c = c0 + k;
-        if (c >= 1 && s_cand[c - 1] == r) y[k] = m;
-      }
       if (store && c0 == 0) static_cast<T*>(a.Mout)[r] = y[0];
-    } else if constexpr (MODE == MODE_CAND) {
-#pragma unroll
-      for (int k = 0; k < CPL; ++k)
-        if (valid && s_cand[c0 + k] == r) y[k] = __ldg(static_cast<const T*>(a.Min) + r);
     } else if constexpr (MODE == MODE_LOOK) {
-      // level d = c / 2 runs under S + {c_1..c_d}: column 2d is its phi^miss, column 2d+1 the
-      // walks through c_{d+1}, whose own row takes column 2d's value
-#pragma unroll
-      for (int k = 0; k < CPL; ++k) {
-        const int d = (c0 + k) >> 1;
-        for (int j = 0; j < d; ++j)
-          if (s_cand[j] == r) y[k] = T(0);
-      }
-      const T left = __shfl_up_sync(kFull, y[CPL - 1], 1);  // column 2d of a lane holding only 2d+1
-#pragma unroll
-      for (int k = 0; k < CPL; ++k) {
-        const int c = c0 + k;
-        if ((c & 1) && s_cand[c >> 1] == r) y[k] = CPL == 1 ? left : y[k > 0 ? k - 1 : 0];
-      }
       if (store) {
 #pragma unroll
         for (int k = 0; k < CPL; ++k)
@@ -299,7 +352,8 @@ __device__ __forceinline__ void epilogue(const SweepArgs& a, const int* __restri
     if (store) {
       if constexpr (Sums<MODE, C>::N > 0) {
 #pragma unroll
-        for (int k = 0; k < CPL; ++k) cs[k] += static_cast<double>(y[k]);
+        for (int k = 0; k < CPL; ++k)
+          if (Sums<MODE, C>::slot(c0 + k) >= 0) acc.add(k, y[k]);
       }
 #pragma unroll
       for (int k = 0; k < CPL; ++k) y[k] *= sv;
@@ -340,9 +394,8 @@ __device__ __forceinline__ void short_rows(const SweepArgs& a, const Src& src, c
   const int c0 = blk * CPL;
   const int32_t* __restrict__ ci = a.ci;
   const uint64_t pol = stream_policy();
-  double cs[CPL];
-#pragma unroll
-  for (int k = 0; k < CPL; ++k) cs[k] = 0.0;
+  ColAcc<T, CPL> acc;
+  acc.zero();
   for (int it = 0; it < nrows; it += 2 * NG) {
     const int ra = it + g, rb = it + NG + g;
     const bool va = ra < nrows, vb = rb < nrows;
@@ -379,10 +432,13 @@ __device__ __forceinline__ void short_rows(const SweepArgs& a, const Src& src, c
       sa[k] = acca[k];
       sb[k] = accb[k];
     }
-    epilogue<T, C, MODE, CPL>(a, s_cand, r0 + ra, va, va && owner, c0, base, sa, cs);
-    epilogue<T, C, MODE, CPL>(a, s_cand, r0 + rb, vb, vb && owner, c0, base, sb, cs);
+    epilogue<T, C, MODE, CPL>(a, s_cand, r0 + ra, va, va && owner, c0, base, sa, acc);
+    epilogue<T, C, MODE, CPL>(a, s_cand, r0 + rb, vb, vb && owner, c0, base, sb, acc);
   }
-  // sum the groups' copies of each column (non-owners hold zeros)
+  // sum the groups' copies of each column (non-owners hold zeros), in FP64
+  double cs[CPL];
+#pragma unroll
+  for (int k = 0; k < CPL; ++k) cs[k] = acc.get(k);
 #pragma unroll
   for (int o = W; o < 32; o <<= 1)
 #pragma unroll
@@ -404,9 +460,8 @@ __device__ __forceinline__ void long_rows(const SweepArgs& a, const Src& src, co
   const int c0 = blk * CPL;
   const int32_t* __restrict__ ci = a.ci;
   const uint64_t pol = stream_policy();
-  double cs[CPL];
-#pragma unroll
-  for (int k = 0; k < CPL; ++k) cs[k] = 0.0;
+  ColAcc<T, CPL> cacc;
+  cacc.zero();
   for (int rr = 0; rr < nrows; ++rr) {
     const int e0 = s_rp[rr], e1 = s_rp[rr + 1];
     T acc[C];
@@ -426,8 +481,11 @@ __device__ __forceinline__ void long_rows(const SweepArgs& a, const Src& src, co
     T s[CPL];
 #pragma unroll
     for (int k = 0; k < CPL; ++k) s[k] = acc[k];
-    epilogue<T, C, MODE, CPL>(a, s_cand, r0 + rr, true, owner, c0, 0, s, cs);
+    epilogue<T, C, MODE, CPL>(a, s_cand, r0 + rr, true, owner, c0, 0, s, cacc);
   }
+  double cs[CPL];
+#pragma unroll
+  for (int k = 0; k < CPL; ++k) cs[k] = cacc.get(k);
   if (owner) write_slot<MODE, C, CPL>(a, static_cast<size_t>(uidx), c0, cs);
 }
 
@@ -482,10 +540,12 @@ __device__ __forceinline__ void heavy_slice(const SweepArgs& a, const Src& src, 
   for (int s = hr.y; s < hr.y + hr.z; ++s)
 #pragma unroll
     for (int k = 0; k < CPL; ++k) tot[k] += __ldcg(part + static_cast<size_t>(s) * C + c0 + k);
+  ColAcc<T, CPL> cacc;
+  cacc.zero();
+  epilogue<T, C, MODE, CPL>(a, s_cand, hr.x, true, owner, c0, 0, tot, cacc);
   double cs[CPL];
 #pragma unroll
-  for (int k = 0; k < CPL; ++k) cs[k] = 0.0;
-  epilogue<T, C, MODE, CPL>(a, s_cand, hr.x, true, owner, c0, 0, tot, cs);
+  for (int k = 0; k < CPL; ++k) cs[k] = cacc.get(k);
   if (owner) write_slot<MODE, C, CPL>(a, static_cast<size_t>(a.num_units + u.x), c0, cs);
   if (lane == 0) a.counters[u.x] = 0u;  // ready for the next launch
 }

@@ -1,18 +1,24 @@
 """Parity at the configured sizes, in the launch configuration bench.py times.
 
-The oracle cannot replay a whole k=100 maximisation on a 128M-entry graph within a test, so at
-full size the GPU results are checked on sampled outputs the oracle computes one by one (the
-first greedy picks, the exact gains of sampled steps, scores of sampled groups) and through
-properties that hold at any size (gains never increase by more than the tolerance, by
-submodularity; the gains add up to the score of the group).
+The whole k = 100 greedy sequences of the benchmarked configurations (R-MAT scale 22 in FP32; the
+Barabasi-Albert graph with n = 10^6 in FP32 and FP64) are compared pick by pick and gain by gain
+with the oracle's sequences in tests/golden/, written once by tests/golden/make_greedy_goldens.py
+from the CPU oracle alone. A pick may differ only where the two gains tie within the tolerance;
+the oracle then continues from the GPU's own prefix (here, on the CPU) and the comparison goes on
+(tests/seqcheck.py). FP64 gains at n = 10^6 are compared with the long-double oracle: the FP64
+oracle's own sequential sums carry rounding near the FP64 tolerance there. Batched scoring is
+checked on sampled groups the oracle scores one by one.
 """
 import functools
+import importlib.util
+import os
 
 import numpy as np
 import pytest
 
 import graphgen as gg
 import oracle
+from seqcheck import check_sequence, oracle_greedy_checker
 
 pytestmark = pytest.mark.gpu
 
@@ -34,25 +40,26 @@ def ba1m():
     return gg.barabasi_albert(1_000_000, 8, seed=1)
 
 
+def golden(name):
+    """(alpha, L, group, gains, long-double gains or None) of the oracle's k = 100 sequence."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "make_greedy_goldens.py")
+    spec = importlib.util.spec_from_file_location("make_greedy_goldens", path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod.read(name)
+
+
 def test_rmat22_greedy_k100_fp32(cuda_device):
     from paper_1910_13874_gb300 import gedwalk
 
     g = rmat22()
+    alpha, Lg, ref_grp, ref_gains, _ = golden("rmat22")
+    assert alpha == oracle.default_alpha(g)
     G = gedwalk.Graph.from_host(g)
-    alpha = oracle.default_alpha(g)
     grp, gains, score, L = G.maximize(100, precision="fp32", epsilon=1e-4)  # the bench configuration
-    assert L == oracle.select_L(g, alpha, 1e-4 / 100)[0]
+    assert L == Lg
     assert len(set(grp.tolist())) == 100
-    # submodularity: the truncated gain of the chosen vertex never grows from one step to the next
-    assert np.all(gains[1:] <= gains[:-1] * (1 + TOL32))
-    # the first picks are the oracle's greedy picks
-    ogrp, ogains, _ = oracle.greedy(g, 2, alpha, L, "lazy")
-    assert list(grp[:2]) == list(ogrp)
-    assert np.all([rel(gains[j], ogains[j]) < TOL32 for j in range(2)])
-    # sampled steps: the GPU gain equals the oracle's exact gain of that vertex for that prefix
-    for step in (5, 50, 99):
-        want = oracle.gain(g, grp[:step], int(grp[step]), alpha, L)
-        assert rel(gains[step], want) < TOL32, (step, gains[step], want)
+    check_sequence(grp, gains, TOL32, ref_grp, ref_gains, *oracle_greedy_checker(oracle, g, alpha, L))
     # the gains add up to the score of the final group (FP64 oracle, same L)
     want = oracle.score(g, grp, alpha, L)
     assert rel(score, want) < TOL32
@@ -60,10 +67,26 @@ def test_rmat22_greedy_k100_fp32(cuda_device):
     G.free()
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_ba1m_greedy_k100(cuda_device, prec):
+    from paper_1910_13874_gb300 import gedwalk
+
+    g = ba1m()
+    alpha, Lg, ref_grp, ref_gains, ref_ld = golden("ba1m")
+    assert alpha == oracle.default_alpha(g) and ref_ld is not None
+    G = gedwalk.Graph.from_host(g)
+    grp, gains, score, L = G.maximize(100, precision=prec, epsilon=1e-4)
+    assert L == Lg
+    fp64 = prec == "fp64"
+    tol = TOL64 if fp64 else TOL32
+    check_sequence(grp, gains, tol, ref_grp, ref_ld if fp64 else ref_gains,
+                   *oracle_greedy_checker(oracle, g, alpha, L, long_double=fp64))
+    assert rel(score, oracle.score(g, grp, alpha, L, long_double=fp64)) < tol
+    G.free()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_ba1m_greedy_k10(cuda_device, prec):
-    # At n = 10^6 the FP64 oracle's own sequential sums carry ~1e-12 relative rounding, the size of
-    # the FP64 tolerance itself, so FP64 values are compared with the long-double oracle.
     from paper_1910_13874_gb300 import gedwalk
 
     g = ba1m()
@@ -71,13 +94,10 @@ def test_ba1m_greedy_k10(cuda_device, prec):
     alpha = oracle.default_alpha(g)
     grp, gains, score, L = G.maximize(10, precision=prec, epsilon=1e-4)
     tol = TOL64 if prec == "fp64" else TOL32
-    ogrp, ogains, _ = oracle.greedy(g, 10, alpha, L, "lazy")
-    for j in range(10):
-        ref = oracle.gain(g, list(grp[:j]), int(grp[j]), alpha, L, long_double=True)
-        assert rel(gains[j], ref) < tol, (j, gains[j], ref)
-        if grp[j] != ogrp[j]:  # only a tie inside the tolerance may part the sequences
-            assert abs(ref - ogains[j]) <= tol * ogains[j]
-            break
+    fp64 = prec == "fp64"
+    ogrp, _, _ = oracle.greedy(g, 10, alpha, L, "lazy")
+    ref = [oracle.gain(g, list(ogrp[:j]), int(ogrp[j]), alpha, L, long_double=fp64) for j in range(10)]
+    check_sequence(grp, gains, tol, ogrp, ref, *oracle_greedy_checker(oracle, g, alpha, L, long_double=fp64))
     assert rel(score, oracle.score(g, grp, alpha, L, long_double=True)) < tol
     G.free()
 

@@ -18,6 +18,7 @@ import pytest
 
 import graphgen as gg
 import oracle
+from seqcheck import check_sequence, oracle_greedy_checker, oracle_stochastic_checker
 
 pytestmark = pytest.mark.gpu
 
@@ -316,6 +317,24 @@ def test_score_batch(cuda_device, name):
     assert s2[0] == 0.0 and rel(s2[1], oracle.score(g, [5, 6], alpha, L)) < 1e-5
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_maximize_past_the_positive_gains(cuda_device, prec):
+    # 7 vertices have edges, 23 are isolated (caller ids 3, 4, 9..29). After 4 picks every gain is
+    # exactly 0 (vertex 2's neighbours are both in S) and the picks go by increasing caller id,
+    # isolated or not (the bound pass leaves the isolated rows to the host, which tracks the
+    # smallest such id outside S)
+    g = host_graph("isolated")
+    G = dev_graph("isolated")
+    alpha = oracle.default_alpha(g)
+    grp, gains, score, L = G.maximize(12, precision=prec, epsilon=1e-4)
+    ogrp, ogains, _ = oracle.greedy(g, 12, alpha, L, "all")
+    check_sequence(grp, gains, TOL[prec], ogrp, ogains, *oracle_greedy_checker(oracle, g, alpha, L))
+    assert list(grp[4:]) == [2, 3, 4, 6, 8, 9, 10, 11] and np.all(gains[4:] == 0.0)
+    # resuming from a prefix that already holds isolated vertices skips them
+    grp2, gains2, _, _ = G.maximize(3, precision=prec, epsilon=1e-4, init=[0, 1, 2, 5, 6, 7, 8, 3, 9])
+    assert list(grp2) == [4, 10, 11] and np.all(gains2 == 0.0)
+
+
 # ------------------------------------------------------------------ stochastic greedy (Appendix D)
 @pytest.mark.parametrize("name,k,eta,seed", [("ba5000", 20, 0.1, 1), ("rmat14", 20, 0.2, 5), ("er1000", 8, 0.3, 9)])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
@@ -326,11 +345,10 @@ def test_stochastic_maximize_matches_oracle(cuda_device, name, k, eta, seed, pre
     grp, gains, score, L = G.maximize(k, precision=prec, epsilon=1e-4, stochastic=True, eta=eta, seed=seed)
     ogrp, ogains, _ = oracle.greedy_stochastic(g, k, alpha, L, eta, seed)
     tol = TOL[prec]
-    for j in range(k):
-        if grp[j] != ogrp[j]:  # sequences may part only at a tie inside the tolerance
-            assert abs(gains[j] - ogains[j]) <= tol * ogains[j], (j, grp[j], ogrp[j])
-            break
-        assert gains[j] == ogains[j] == 0.0 or rel(gains[j], ogains[j]) < tol
+    # sequences may part only at a tie inside the tolerance; the oracle then continues from the
+    # GPU's own prefix with the same draws
+    check_sequence(grp, gains, tol, ogrp, ogains,
+                   *oracle_stochastic_checker(oracle, g, alpha, L, k, eta, seed))
     # every pick lies in its step's sample (the oracle's own draw)
     import math
 
@@ -409,11 +427,9 @@ def test_lookahead_levels_match_oracle(cuda_device, monkeypatch, name, k, levels
     monkeypatch.setenv("GEDWALK_LOOKAHEAD", levels)
     grp, gains, score, L = G.maximize(k, precision="fp32", epsilon=1e-4)
     ogrp, ogains, _ = oracle.greedy(g, k, alpha, L, "lazy")
-    for j in range(k):
-        if grp[j] != ogrp[j]:  # only a tie inside the tolerance may part the sequences
-            assert abs(gains[j] - ogains[j]) <= 1e-5 * ogains[j], (j, grp[j], ogrp[j])
-            break
-        assert gains[j] == ogains[j] == 0.0 or rel(gains[j], ogains[j]) < 1e-5, j
+    # only a tie inside the tolerance may part the sequences; after one the oracle continues from
+    # the GPU's own prefix
+    check_sequence(grp, gains, 1e-5, ogrp, ogains, *oracle_greedy_checker(oracle, g, alpha, L))
     assert rel(score, oracle.score(g, grp, alpha, L)) < 1e-5
     st = G.maximize_stats()
     if levels != "1":  # steps whose winner was guessed run no sweep of their own

@@ -13,6 +13,7 @@ import pytest
 
 import graphgen as gg
 import oracle
+from seqcheck import check_sequence, oracle_greedy_checker
 
 pytestmark = pytest.mark.gpu
 
@@ -123,8 +124,5 @@ def test_spectral_score_and_maximize_match_oracle(cuda_device, name, prec):
     k = 5
     grp, gains, score, L = G.maximize(k, alpha=alpha, precision=prec, epsilon=1e-3, bound="spectral")
     ogrp, ogains, _ = oracle.greedy(g, k, alpha, L, "lazy", w=w, directed=directed)
-    for j in range(k):
-        if grp[j] != ogrp[j]:
-            assert abs(gains[j] - ogains[j]) <= TOL[prec] * ogains[j], j
-            break
-        assert rel(gains[j], ogains[j]) < TOL[prec], j
+    check_sequence(grp, gains, TOL[prec], ogrp, ogains,
+                   *oracle_greedy_checker(oracle, g, alpha, L, w=w, directed=directed))

@@ -14,6 +14,7 @@ import pytest
 
 import graphgen as gg
 import oracle
+from seqcheck import check_sequence, oracle_greedy_checker, oracle_stochastic_checker
 
 pytestmark = pytest.mark.gpu
 
@@ -126,11 +127,9 @@ def test_weighted_maximize_matches_oracle(cuda_device, name, k, prec):
     grp, gains, score, L = G.maximize(k, alpha=alpha, precision=prec, epsilon=1e-4)
     ogrp, ogains, _ = oracle.greedy(g, k, alpha, L, "lazy", w=w)
     tol = TOL[prec]
-    for j in range(k):
-        if grp[j] != ogrp[j]:  # only a tie inside the tolerance may part the sequences
-            assert abs(gains[j] - ogains[j]) <= tol * ogains[j], (j, grp[j], ogrp[j])
-            break
-        assert gains[j] == ogains[j] == 0.0 or rel(gains[j], ogains[j]) < tol, j
+    # only a tie inside the tolerance may part the sequences; the oracle then continues from the
+    # GPU's own prefix
+    check_sequence(grp, gains, tol, ogrp, ogains, *oracle_greedy_checker(oracle, g, alpha, L, w=w))
     assert rel(score, oracle.score(g, grp, alpha, L, w=w)) < tol
 
 
@@ -150,11 +149,8 @@ def test_weighted_adaptive_and_stochastic(cuda_device, prec):
     assert grp[0] == ref["group"][0] and ell[0] == ref["ell"][0]
     grp, gains, score, L = G.maximize(k, alpha=alpha, precision=prec, epsilon=eps, stochastic=True, eta=0.2, seed=3)
     ogrp, ogains, _ = oracle.greedy_stochastic(g, k, alpha, L, 0.2, 3, w=w)
-    for j in range(k):
-        if grp[j] != ogrp[j]:
-            assert abs(gains[j] - ogains[j]) <= tol * ogains[j], j
-            break
-        assert rel(gains[j], ogains[j]) < tol, j
+    check_sequence(grp, gains, tol, ogrp, ogains,
+                   *oracle_stochastic_checker(oracle, g, alpha, L, k, 0.2, 3, w=w))
 
 
 def test_weighted_rejects_bad_scales(cuda_device):

@@ -3,8 +3,9 @@
 Callers that cannot allocate device memory (a framework that has pooled the whole GPU, a
 service that forbids allocation while serving) use gedwalk_score_step_noalloc with buffers
 they already own. This test owns its buffers through PyTorch, runs the step repeatedly and
-compares every partial sum with the regular scoring entry point (gedwalk_score, FP32), within
-the FP32 tolerance of the other parity tests (1e-5 relative). It runs two scorings in a row so
+compares every partial sum with the regular scoring entry point (gedwalk_score, FP32) and the
+whole score with the CPU oracle's two-state recurrence, within the FP32 tolerance of the other
+parity tests (1e-5 relative). It runs two scorings in a row so
 that the scratch kept from the previous call cannot leak into the next one, and it must pass
 alone in a fresh process as well as after the other tests.
 """
@@ -14,6 +15,7 @@ import numpy as np
 import pytest
 
 import graphgen as gg
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -70,6 +72,8 @@ def test_noalloc_step_matches_score_two_calls_in_a_row(cuda_device):
             x, y = y, x
         want, _, _ = G.score(S, precision="fp32", L=L)
         assert _rel(total, want) < TOL, (trial, total, want)
+        want_oracle = oracle.score(g, S, alpha, L)  # independent of the library: the CPU oracle
+        assert _rel(total, want_oracle) < TOL, (trial, total, want_oracle)
     G.free()
 
 
