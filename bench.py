@@ -392,6 +392,7 @@ def run_batch(args, spec, rank, world, local):
                    "member_total": int(off[-1]), "parallelism": f"replicas x{world}",
                    "l2": l2_note(G.n, G.nnz)},
         "fp64_per_group_queries_s": round(1.0 / t64, 1), "speedup_vs_fp64_per_group": round(qps / world * t64, 2),
+        "autotuner": dict(zip(("widths", "us_per_column", "chosen"), G.batch_tuning())),
         "roofline": roofline(prof, "batch"),
         "gpu_launches": prof["launches"], "clocks": clk,
         "e2e": {"value": round(qps, 1), "unit": "queries/s", "h2d_bytes_per_step": int(mem.nbytes + off.nbytes),
@@ -429,11 +430,23 @@ def run_serve(args, spec, rank, world, local):
     devs = [gedwalk.Graph.from_host(h) for h in hosts]
     srv = gedwalk.Server(devs, mem_budget=8 << 30, max_batch=256)
     rng = np.random.default_rng(42)
+    # service times without load: one maximise (k = 27, the mean of U{5..50}) and one score of
+    # 100 members per graph, each alone on the server (after one warm-up request)
+    alone = []
+    for gi, h in enumerate(hosts):
+        S = rng.choice(h.n, size=100, replace=False)
+        srv.poll(srv.submit_maximize(gi, 27), -1)
+        srv.poll(srv.submit_score(gi, S), -1)
+        tm = srv.poll(srv.submit_maximize(gi, 27), -1)["latency_us"] / 1e3
+        ts = srv.poll(srv.submit_score(gi, S), -1)["latency_us"] / 1e3
+        alone.append({"graph": f"n={devs[gi].n} nnz={devs[gi].nnz}", "maximize_k27_ms": round(tm, 3),
+                      "score_100_ms": round(ts, 3)})
     # the configured mix (90% score, 10% maximise) and score-only traffic, Poisson arrivals
     plan = [(1000, 0.9), (5000, 0.9), (20000, 0.9), (5000, 1.0), (20000, 1.0), (50000, 1.0)]
     per_rate = max(1.0, min(3.0, args.steps))
     results = []
     for rate, score_frac in plan:
+        c0 = srv.stats()
         n_req = int(rate * per_rate)
         gaps = rng.exponential(1.0 / rate, size=n_req)
         kinds = rng.random(n_req) < score_frac
@@ -455,9 +468,15 @@ def run_serve(args, spec, rank, world, local):
         lat = [srv.poll(t, -1)["latency_us"] for t in tickets]
         wall = time.perf_counter() - t0
         lat = np.array(lat) / 1e3
+        c1 = srv.stats()
         res = {"offered_req_s": rate, "score_fraction": score_frac, "achieved_req_s": round(n_req / wall, 1),
                "p50_ms": round(float(np.percentile(lat, 50)), 3),
-               "p99_ms": round(float(np.percentile(lat, 99)), 3), "requests": n_req}
+               "p99_ms": round(float(np.percentile(lat, 99)), 3), "requests": n_req,
+               "admitted_at_submit": c1["admitted_at_submit"] - c0["admitted_at_submit"],
+               "admitted_after_wait": c1["admitted_after_wait"] - c0["admitted_after_wait"],
+               "batches": c1["batches"] - c0["batches"],
+               "mean_batch": round((c1["batched_requests"] - c0["batched_requests"]) / max(1, c1["batches"] - c0["batches"]), 2),
+               "peak_maximize_running": c1["peak_maximize_running"]}
         for flag, name in ((True, "score"), (False, "maximize")):
             sel = lat[kinds == flag]
             if sel.size:
@@ -475,7 +494,7 @@ def run_serve(args, spec, rank, world, local):
             "config": {"workload": spec["name"], "graphs": [f"n={d.n} nnz={d.nnz}" for d in devs],
                        "mix": "90% score |S|~U{1..200}, 10% maximize k~U{5..50}; plus score-only rates",
                        "epsilon": spec["eps"], "value_is": "best achieved rate of the configured mix"},
-            "rates": results, "server": st,
+            "rates": results, "server": st, "alone": alone,
             "e2e": {"value": best["achieved_req_s"], "unit": "queries/s", "h2d_bytes_per_step": None,
                     "d2h_bytes_per_step": None, "note": "requests submitted from host memory through the C ABI"}}
 

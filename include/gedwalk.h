@@ -93,6 +93,11 @@ typedef struct {
   double eta;              /* stochastic greedy: sample (n/k) ln(1/eta) vertices per step, 0 < eta < 1 */
   uint64_t seed;           /* stochastic greedy: seed of the counter-based sample draws */
   int32_t bound;           /* GEDWALK_BOUND_COMBINATORIAL (default) or GEDWALK_BOUND_SPECTRAL */
+  int32_t lookahead;       /* maximize: greedy steps carried by one run of sweeps (see gedwalk_maximize):
+                              0 = default (4 in FP32, 2 in FP64), 1 = off, 2, 4 or (FP32) 8 */
+  int32_t spec_cols;       /* maximize without lookahead: columns of the fused sweep (phi^miss plus
+                              speculative candidates): 0 = default (2; 4 with GEDWALK_ADAPTIVE_L), 2, 4
+                              or (FP32) 8 */
   int32_t reserved;        /* 0 */
 } gedwalk_params;
 
@@ -103,15 +108,19 @@ enum {
 };
 
 /* Fills *p with the defaults: alpha 0, epsilon 1e-4, L 0, FP32, EPS_OVER_K, no flags, stream 0,
- * eta 0.1, seed 0, the combinatorial bound. */
+ * eta 0.1, seed 0, the combinatorial bound, lookahead 0, spec_cols 0. */
 GEDWALK_API void gedwalk_params_default(gedwalk_params* p);
 
 /*
  * Device memory hook. alloc(bytes, stream, ctx) returns device memory or NULL;
  * release(ptr, bytes, stream, ctx) frees it. Passing NULL restores the
  * built-in cudaMalloc/cudaFree. The Python binding installs PyTorch's caching
- * allocator here. Set it before the first upload; it applies to every later
- * allocation of the process.
+ * allocator here when it loads the library. The hook applies to every later
+ * allocation of the process; each block is freed through the allocator that
+ * allocated it, so the functions of a replaced hook must stay callable while
+ * blocks they allocated are alive. Before calling a hook's release the library
+ * waits for the device (as cudaFree does), since a caching allocator may hand
+ * the block to another stream at once. Set it while no other call is running.
  */
 typedef void* (*gedwalk_alloc_fn)(size_t bytes, int64_t stream, void* ctx);
 typedef void (*gedwalk_free_fn)(void* ptr, size_t bytes, int64_t stream, void* ctx);
@@ -240,6 +249,17 @@ GEDWALK_API gedwalk_status gedwalk_score_batch(gedwalk_graph_t g, const int32_t*
                                    const gedwalk_params* params, double* scores, int32_t* L_used);
 
 /*
+ * The batched-scoring autotuner's record for this graph (empty before the first
+ * gedwalk_score_batch): for each column-block width tried, cols[j] and the
+ * measured sweep time per column us_per_col[j] (microseconds, one unmasked
+ * FP32 sweep of that width divided by its columns); *chosen the width in use
+ * (0 before tuning). Up to cap entries are written; *count receives how many
+ * exist. count and chosen may be NULL.
+ */
+GEDWALK_API gedwalk_status gedwalk_batch_tuning(gedwalk_graph_t g, int32_t* cols, double* us_per_col, int32_t cap,
+                                    int32_t* count, int32_t* chosen);
+
+/*
  * Exact truncated marginal gain GED_{<=L}(S, x) = GED_{<=L}(S + x) - GED_{<=L}(S)
  * (the lower bound L_l of Section 3.2.1) for every vertex x, counted directly as
  * the alpha-weighted walks of length 1..L that visit x and avoid S (proof of
@@ -277,8 +297,9 @@ GEDWALK_API gedwalk_status gedwalk_gains(gedwalk_graph_t g, const int32_t* S, in
  * next steps' phi^miss vectors and exact gains for guessed winners (lookahead):
  * a step whose winner was guessed needs no sweep. Every pick is still certified
  * against the bounds of the actual group, so the results do not depend on it.
- * The environment variable GEDWALK_LOOKAHEAD (1 = off, 2, 4; 8 in FP32) sets
- * the number of steps per run (default 4 in FP32, 2 in FP64).
+ * params->lookahead (1 = off, 2, 4; 8 in FP32) sets the number of steps per run
+ * (0: 4 in FP32, 2 in FP64); params->spec_cols the width of the one-step fused
+ * sweep when the lookahead is off. Other values return INVALID.
  * GEDWALK_ADAPTIVE_L runs the lazy greedy of Algorithm 2 (Section 3.2.3): the
  * walk length l starts at 1 and only doubles. At each step u, the vertex with the
  * largest L_l(S, u) = GED_{<=l}(S, u), is taken when it is separated from v, the
@@ -328,10 +349,12 @@ enum { GEDWALK_REQ_SCORE = 0, GEDWALK_REQ_MAXIMIZE = 1 };
 
 /*
  * graphs: n_graphs uploaded handles, referenced by index in submit; they must
- * outlive the server. mem_budget: bytes of device working memory the server
- * may hold for requests in flight (0 = 1 GiB). max_batch: the most score
- * requests packed into one SpMM (0 = 256). The server starts one scheduler
- * thread.
+ * outlive the server, and while it runs other calls on them must use the alpha
+ * the server serves (the graph's default unless a request set another first).
+ * mem_budget: bytes of device working memory the server may hold (0 = 1 GiB;
+ * see gedwalk_serve_counters). max_batch: the most score requests packed into
+ * one SpMM (0 = 256). The server starts one scoring thread per graph and 8
+ * maximise worker threads, each with its own CUDA stream.
  */
 GEDWALK_API gedwalk_status gedwalk_serve_create(const gedwalk_graph_t* graphs, int32_t n_graphs, int64_t mem_budget,
                                     int32_t max_batch, gedwalk_server_t* out);
@@ -340,7 +363,9 @@ GEDWALK_API gedwalk_status gedwalk_serve_create(const gedwalk_graph_t* graphs, i
  * Queues a request. kind GEDWALK_REQ_SCORE scores S (s_len members);
  * GEDWALK_REQ_MAXIMIZE runs gedwalk_maximize with k = s_len_or_k (S ignored).
  * params: NULL = defaults (its stream field is ignored). *ticket identifies the
- * request. BUSY when the queue holds 1<<20 requests already.
+ * request. BUSY when the queue holds 1<<20 requests already. INVALID when the
+ * request's alpha differs from the one its graph serves: the graph's walk-total
+ * table, which queued score requests read, holds one alpha.
  */
 GEDWALK_API gedwalk_status gedwalk_serve_submit(gedwalk_server_t srv, int32_t graph, int32_t kind, const int32_t* S,
                                     int32_t s_len_or_k, const gedwalk_params* params, uint64_t* ticket);
@@ -356,9 +381,37 @@ GEDWALK_API gedwalk_status gedwalk_serve_submit(gedwalk_server_t srv, int32_t gr
 GEDWALK_API gedwalk_status gedwalk_serve_poll(gedwalk_server_t srv, uint64_t ticket, int32_t wait_us, double* score,
                                   int32_t* group, double* gains, double* latency_us, int32_t* done);
 
-/* Counters: requests completed, batched SpMM launches, score requests packed into them, peak bytes in flight. */
+/* Counters: requests completed, batched SpMM launches, score requests packed into them, and the
+ * peak of the charged device bytes (see gedwalk_serve_counters). */
 GEDWALK_API gedwalk_status gedwalk_serve_stats(gedwalk_server_t srv, int64_t* completed, int64_t* batches, int64_t* batched_requests,
                                    int64_t* peak_bytes);
+
+/*
+ * Memory admission in detail. Each scoring lane and maximise worker owns a workspace whose device
+ * buffers grow to its largest request and stay allocated. The server charges each workspace the
+ * bytes it holds or, while it has work, the larger of those and the exact footprint of that work.
+ * A request is admitted while the total charge stays within mem_budget; otherwise idle workspaces
+ * are released (largest first, counted in releases / released_bytes) and, if that is not enough,
+ * the request waits. A request larger than the budget runs when nothing else holds memory. The
+ * graphs themselves (their CSR and walk-total tables) are not charged.
+ */
+typedef struct {
+  int64_t completed;             /* requests finished */
+  int64_t batches;               /* batched SpMM launches of the scoring lanes */
+  int64_t batched_requests;      /* score requests packed into them */
+  int64_t peak_bytes;            /* largest total charge seen */
+  int64_t budget;                /* mem_budget */
+  int64_t charged_bytes;         /* total charge now */
+  int64_t idle_held_bytes;       /* device bytes the idle workspaces hold now (measured) */
+  int64_t admitted_at_submit;    /* requests admitted by their own submit call */
+  int64_t admitted_after_wait;   /* requests that waited in a queue for memory or a worker */
+  int64_t peak_maximize_running; /* most maximise requests running at once */
+  int64_t releases;              /* idle workspaces released to make room */
+  int64_t released_bytes;        /* device bytes they held */
+  int64_t pending;               /* requests waiting for admission now */
+} gedwalk_serve_counters;
+
+GEDWALK_API gedwalk_status gedwalk_serve_counters_read(gedwalk_server_t srv, gedwalk_serve_counters* out);
 
 /* Stops the scheduler after the requests in flight finish; pending requests are dropped. */
 GEDWALK_API gedwalk_status gedwalk_serve_destroy(gedwalk_server_t srv);

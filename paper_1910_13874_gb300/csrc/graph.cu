@@ -117,9 +117,15 @@ static gedwalk_alloc_fn g_alloc = nullptr;
 static gedwalk_free_fn g_free = nullptr;
 static void* g_alloc_ctx = nullptr;
 
-void* dalloc(size_t bytes, cudaStream_t s) {
+void* dalloc(size_t bytes, cudaStream_t s, Allocator* from) {
   if (bytes == 0) bytes = 16;
-  if (g_alloc) return g_alloc(bytes, reinterpret_cast<int64_t>(s), g_alloc_ctx);
+  if (g_alloc) {
+    from->release = g_free;
+    from->ctx = g_alloc_ctx;
+    return g_alloc(bytes, reinterpret_cast<int64_t>(s), g_alloc_ctx);
+  }
+  from->release = nullptr;
+  from->ctx = nullptr;
   void* p = nullptr;
   if (cudaMalloc(&p, bytes) != cudaSuccess) {
     cudaGetLastError();  // clear the sticky-free error state of a failed allocation
@@ -128,20 +134,26 @@ void* dalloc(size_t bytes, cudaStream_t s) {
   return p;
 }
 
-void dfree(void* p, size_t bytes, cudaStream_t s) {
+void dfree(void* p, size_t bytes, cudaStream_t s, const Allocator& from) {
   if (!p) return;
-  if (g_free) {
-    g_free(p, bytes, reinterpret_cast<int64_t>(s), g_alloc_ctx);
+  if (from.release) {
+    // A caching allocator (PyTorch's) may hand the block to its next user at once, while cudaFree
+    // would first wait for the device. The library frees only blocks no kernel uses any more:
+    // every call synchronises the stream it ran on before it returns (on success and on error),
+    // the walk-total table grows only after its readers have finished, and a graph is freed after
+    // the whole device has. (No device-wide wait here: it would break a CUDA graph capture that
+    // another thread has in progress.)
+    from.release(p, bytes, reinterpret_cast<int64_t>(s), from.ctx);
     return;
   }
-  cudaFree(p);
+  if (cudaFree(p) != cudaSuccess) cudaGetLastError();  // leave no error behind for the next check
 }
 
 gedwalk_status DevBuf::ensure(size_t need, cudaStream_t s, bool zero) {
   if (need == 0) need = 16;
   if (p && bytes >= need) return GEDWALK_OK;
   release();
-  p = dalloc(need, s);
+  p = dalloc(need, s, &from);
   if (!p) return fail(GEDWALK_ERR_OOM, "device allocation of %zu bytes failed", need);
   bytes = need;
   if (zero) GW_CUDA(cudaMemsetAsync(p, 0, need, s));
@@ -156,6 +168,21 @@ void SweepGraph::reset() {
   key = 0;
   uses = 0;
   timing_pending = false;
+}
+
+int64_t Workspace::device_bytes() const {
+  int64_t b = 0;
+  for (const DevBuf* d : {&x0, &x1, &mtab, &ztab, &pvec, &partial, &counters, &slots, &parts, &mask, &stale, &sel,
+                          &small, &members})
+    b += static_cast<int64_t>(d->bytes);
+  return b;
+}
+
+void Workspace::release_device() {
+  for (SweepGraph& sg : graphs) sg.reset();
+  for (DevBuf* d : {&x0, &x1, &mtab, &ztab, &pvec, &partial, &counters, &slots, &parts, &mask, &stale, &sel, &small,
+                    &members})
+    d->release();
 }
 
 Workspace::~Workspace() {
@@ -505,8 +532,7 @@ gedwalk_status ensure_totals(Graph& g, double alpha, int32_t rows, cudaStream_t 
     if (g.tt_rows > 0)
       GW_CUDA(cudaMemcpyAsync(fresh.p, g.ttab.p, static_cast<size_t>(g.tt_rows) * n * sizeof(double),
                               cudaMemcpyDeviceToDevice, s));
-    std::swap(g.ttab.p, fresh.p);
-    std::swap(g.ttab.bytes, fresh.bytes);
+    g.ttab.swap(fresh);
     GW_CUDA(cudaStreamSynchronize(s));
   }
   Workspace& ws = g.ws;
@@ -754,6 +780,8 @@ gedwalk_status resolve(Graph& g, const gedwalk_params* p, double eps_override, R
   r->stream = reinterpret_cast<cudaStream_t>(p->stream);
   r->eta = p->eta;
   r->seed = p->seed;
+  r->lookahead = p->lookahead;
+  r->spec_cols = p->spec_cols;
   if (p->bound != GEDWALK_BOUND_COMBINATORIAL && p->bound != GEDWALK_BOUND_SPECTRAL)
     return fail(GEDWALK_ERR_INVALID, "bound must be GEDWALK_BOUND_COMBINATORIAL or GEDWALK_BOUND_SPECTRAL");
   r->bound_kind = p->bound;
@@ -817,6 +845,8 @@ void gedwalk_params_default(gedwalk_params* p) {
   p->eta = 0.1;
   p->seed = 0;
   p->bound = GEDWALK_BOUND_COMBINATORIAL;
+  p->lookahead = 0;
+  p->spec_cols = 0;
   p->reserved = 0;
 }
 

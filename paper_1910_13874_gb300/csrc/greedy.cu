@@ -494,7 +494,6 @@ gedwalk_status run_sweeps(GreedyCtx& c, int mode, int cols, const std::vector<in
   GW_TRY(ensure_sweep_scratch(g, ws, cols, fp64, c.s));
   c.sweeps += c.L;
   if (c.s == nullptr || g.plan.num_units == 0) return issue_sweeps(c, mode, cols, true, nullptr, rev);
-  SweepGraph& sg = ws.graphs[rev ? 2 : mode == MODE_LOOK ? 3 : mode == MODE_FUSED ? 0 : 1];
   uint64_t key = 0;
   for (uint64_t v : {uint64_t(mode), uint64_t(cols), uint64_t(fp64), uint64_t(c.L), uint64_t(g.n), uint64_t(rev),
                      uint64_t(c.tab_off),
@@ -510,10 +509,21 @@ gedwalk_status run_sweeps(GreedyCtx& c, int mode, int cols, const std::vector<in
   uint64_t abits;
   memcpy(&abits, &c.r.alpha, 8);
   key = mix_key(key, abits);
-  if (sg.key != key) {
-    sg.reset();
-    sg.key = key;
+  if (key == 0) key = 1;  // 0 marks a free cache entry
+  // the workspace's entry for this configuration, else the least recently used one
+  SweepGraph* hit = nullptr;
+  SweepGraph* lru = &ws.graphs[0];
+  for (SweepGraph& e : ws.graphs) {
+    if (e.key == key) hit = &e;
+    if (e.last_use < lru->last_use) lru = &e;
   }
+  if (!hit) {
+    lru->reset();
+    lru->key = key;
+    hit = lru;
+  }
+  SweepGraph& sg = *hit;
+  sg.last_use = ++ws.graph_clock;
   if (!sg.exec) {
     if (sg.uses++ < 1) return issue_sweeps(c, mode, cols, true, nullptr, rev);  // set-up happens outside capture
     sg.ev.assign(2, nullptr);
@@ -523,10 +533,13 @@ gedwalk_status run_sweeps(GreedyCtx& c, int mode, int cols, const std::vector<in
     cudaGraph_t graph = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(c.s, &graph);
     if (st != GEDWALK_OK || ce != cudaSuccess || !graph) {
+      // Nothing captured has run. Another thread can invalidate a capture (a call that waits for
+      // the whole device, such as cudaFree); the sequence then runs directly, and a genuine error
+      // shows up again there.
       if (graph) cudaGraphDestroy(graph);
       cudaGetLastError();
       sg.reset();
-      return st != GEDWALK_OK ? st : fail(GEDWALK_ERR_DEVICE, "stream capture failed: %s", cudaGetErrorString(ce));
+      return issue_sweeps(c, mode, cols, true, nullptr, rev);
     }
     const cudaError_t ie = cudaGraphInstantiate(&sg.exec, graph, 0);
     cudaGraphDestroy(graph);
@@ -577,42 +590,94 @@ gedwalk_status greedy_stream(Workspace& ws, cudaStream_t caller, cudaStream_t* o
 
 }  // namespace
 
-gedwalk_status maximize_impl(Graph& g, Workspace& ws, int32_t k, const Resolved& r_in, int32_t flags,
-                             const std::vector<int32_t>& init_int, int32_t* group, double* gains, double* score) {
-  Resolved r = r_in;
-  GW_TRY(greedy_stream(ws, r_in.stream, &r.stream));
-  cudaStream_t s = r.stream;
-  const size_t es = r.fp64 ? 8 : 4;
-  // phi^miss + speculative candidates. Every gather costs one L2 sector whatever the row
-  // width, so narrow rows are cheapest; one speculative candidate certifies most steps (a
-  // miss costs one extra candidate batch). GEDWALK_SPEC_COLS (2, 4 or 8) overrides.
+gedwalk_status greedy_shape(const Graph& g, const Resolved& r, int32_t flags, GreedyShape* out) {
+  GreedyShape sh{};
   const bool adaptive = (flags & GEDWALK_ADAPTIVE_L) != 0;
-  // The adaptive variant certifies the best two exact gains (u and v of its separation test),
-  // so it speculates on three candidates.
-  int cols_fused = adaptive ? 4 : 2;
-  if (const char* e = getenv("GEDWALK_SPEC_COLS")) {
-    const int v = atoi(e);
-    if (v == 2 || v == 4 || (v == 8 && !r.fp64)) cols_fused = v;
+  // phi^miss + speculative candidates. Every gather costs one L2 sector whatever the row width,
+  // so narrow rows are cheapest; one speculative candidate certifies most steps (a miss costs one
+  // extra candidate batch). The adaptive variant certifies the best two exact gains (u and v of
+  // its separation test), so it speculates on three candidates.
+  sh.cols_fused = adaptive ? 4 : 2;
+  if (r.spec_cols != 0) {
+    if (!(r.spec_cols == 2 || r.spec_cols == 4 || (r.spec_cols == 8 && !r.fp64)))
+      return fail(GEDWALK_ERR_INVALID, "spec_cols must be 0, 2, 4 or (FP32) 8");
+    sh.cols_fused = r.spec_cols;
   }
   // Lookahead (plain greedy on an undirected graph): one run of sweeps carries `levels` steps,
   // level d under S + {c_1..c_d} with the guessed winners c_d; a step whose winner was guessed
   // needs no sweep of its own. A gather costs one L2 sector request whatever the row width up to
   // 32 bytes, so 4 FP32 levels (2 FP64) cost little more per sweep than one.
-  // GEDWALK_LOOKAHEAD (1 = off, 2, 4, 8 in FP32) overrides the default.
-  int levels = 1;
+  sh.levels = 1;
   if (!(flags & (GEDWALK_ADAPTIVE_L | GEDWALK_STOCHASTIC | GEDWALK_GAINS_ALL)) && !g.directed) {
-    levels = r.fp64 ? 2 : 4;
-    if (const char* e = getenv("GEDWALK_LOOKAHEAD")) {
-      const int v = atoi(e);
-      if (v == 1 || v == 2 || (!r.fp64 && (v == 4 || v == 8))) levels = v;
+    sh.levels = r.fp64 ? 2 : 4;
+    if (r.lookahead != 0) {
+      if (!(r.lookahead == 1 || r.lookahead == 2 || (!r.fp64 && (r.lookahead == 4 || r.lookahead == 8))))
+        return fail(GEDWALK_ERR_INVALID, "lookahead must be 0, 1, 2 or (FP32) 4 or 8");
+      sh.levels = r.lookahead;
     }
   }
-  const bool look = levels > 1;
-  const int n_spec = look ? levels : cols_fused - 1;
   // Candidate batches run when the evaluated guess is not certified; the winner is nearly always
   // among the best few bounds, and a narrower batch is a cheaper sweep.
-  const int cols_cand = 4;
-  const int cols_all = r.fp64 ? 8 : 16;
+  sh.cols_cand = 4;
+  sh.cols_all = r.fp64 ? 8 : 16;
+  sh.ell_max = 1;
+  while (adaptive && sh.ell_max < r.L) sh.ell_max *= 2;
+  sh.tab_L = adaptive ? sh.ell_max : r.L;
+  sh.cols_max = std::max({sh.levels > 1 ? 2 * sh.levels : sh.cols_fused, sh.cols_cand,
+                          (flags & GEDWALK_GAINS_ALL) ? sh.cols_all : 0, 2});
+  *out = sh;
+  return GEDWALK_OK;
+}
+
+int64_t maximize_footprint(const Graph& g, const Resolved& r, int32_t flags) {
+  GreedyShape sh{};
+  if (greedy_shape(g, r, flags, &sh) != GEDWALK_OK) return 0;
+  const int64_t n = g.n, es = r.fp64 ? 8 : 4;
+  const int64_t slices = std::max(std::max(g.plan.num_slices, g.directed ? g.plan_r.num_slices : 0), 1);
+  const int64_t heavy = std::max(std::max(g.plan.num_heavy, g.directed ? g.plan_r.num_heavy : 0), 1);
+  const int64_t slots = std::max(std::max(g.plan.num_slots, g.directed ? g.plan_r.num_slots : 0), 1);
+  int64_t b = 0;
+  b += static_cast<int64_t>(sh.tab_L + 1) * n * es * sh.levels;  // phi^miss tables
+  if (g.directed) b += static_cast<int64_t>(sh.tab_L + 1) * n * es;  // psi^miss table
+  b += 2 * n * sh.cols_max * es;                                    // walk vectors x0, x1
+  b += slices * sh.cols_max * es + heavy * 4 + slots * sh.cols_max * 8 + sh.cols_max * kReduceParts * 8;
+  b += (n + 31) / 32 * 4;                                           // S bitmask
+  b += n * static_cast<int64_t>(sizeof(Stale)) + static_cast<int64_t>(kSelBlocks) * kTopK * 8;
+  b += static_cast<int64_t>(sizeof(SelOut)) + 16 * 4 + 16 * 8 + 256;
+  return b;
+}
+
+namespace {
+// Waits for a stream when a call leaves early with an error, so that nothing it launched still
+// runs when its buffers are reused or freed.
+struct SyncOnError {
+  cudaStream_t s = nullptr;
+  bool ok = false;
+  ~SyncOnError() {
+    if (!ok && s) {
+      cudaStreamSynchronize(s);
+      cudaGetLastError();
+    }
+  }
+};
+}  // namespace
+
+gedwalk_status maximize_impl(Graph& g, Workspace& ws, int32_t k, const Resolved& r_in, int32_t flags,
+                             const std::vector<int32_t>& init_int, int32_t* group, double* gains, double* score) {
+  Resolved r = r_in;
+  GW_TRY(greedy_stream(ws, r_in.stream, &r.stream));
+  SyncOnError guard{r.stream};
+  cudaStream_t s = r.stream;
+  const size_t es = r.fp64 ? 8 : 4;
+  const bool adaptive = (flags & GEDWALK_ADAPTIVE_L) != 0;
+  GreedyShape shape{};
+  GW_TRY(greedy_shape(g, r, flags, &shape));
+  const int cols_fused = shape.cols_fused;
+  const int levels = shape.levels;
+  const bool look = levels > 1;
+  const int n_spec = look ? levels : cols_fused - 1;
+  const int cols_cand = shape.cols_cand;
+  const int cols_all = shape.cols_all;
   const double tol = r.fp64 ? 1e-11 : 1e-5;  // relative inflation of bounds against rounding
   const bool gains_all = (flags & GEDWALK_GAINS_ALL) != 0;
   const bool stochastic = (flags & GEDWALK_STOCHASTIC) != 0;
@@ -628,9 +693,8 @@ gedwalk_status maximize_impl(Graph& g, Workspace& ws, int32_t k, const Resolved&
   // adaptive: l runs through the powers of two from 1; B_l < eps_sep separates any pair, and r.L
   // (the first l with B_l < eps_sep) bounds the largest power reached.
   const double eps_sep = r.eps;
-  int32_t ell_max = 1;
-  while (adaptive && ell_max < r.L) ell_max *= 2;
-  const int32_t L = adaptive ? ell_max : r.L;  // rows of the miss table
+  const int32_t ell_max = shape.ell_max;
+  const int32_t L = shape.tab_L;  // rows of the miss table
   double coef = 0.0;  // B_l = coef * Wa_l (Eq. comb-bound, or Lemma spectral-bound)
   std::vector<double> Wa;  // the walk totals this run needs, copied under the table's lock
   if (adaptive) {
@@ -901,6 +965,7 @@ gedwalk_status maximize_impl(Graph& g, Workspace& ws, int32_t k, const Resolved&
     *score = v;
   }
   GW_CUDA(cudaStreamSynchronize(s));
+  guard.ok = true;
   return GEDWALK_OK;
 }
 
@@ -908,6 +973,7 @@ gedwalk_status gains_impl(Graph& g, Workspace& ws, const std::vector<int32_t>& S
                           double* gains_caller) {
   Resolved r = r_in;
   GW_TRY(greedy_stream(ws, r_in.stream, &r.stream));
+  SyncOnError guard{r.stream};
   cudaStream_t s = r.stream;
   const size_t es = r.fp64 ? 8 : 4;
   const int cols_all = r.fp64 ? 8 : 16;
@@ -936,6 +1002,7 @@ gedwalk_status gains_impl(Graph& g, Workspace& ws, const std::vector<int32_t>& S
       batch.clear();
     }
   }
+  guard.ok = true;
   return GEDWALK_OK;
 }
 

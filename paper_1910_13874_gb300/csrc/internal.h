@@ -10,6 +10,7 @@
 #include <mutex>
 #include <shared_mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "gedwalk.h"
@@ -43,21 +44,35 @@ void count_launch();
   } while (0)
 
 // ---------------------------------------------------------------- device memory
-void* dalloc(size_t bytes, cudaStream_t s);
-void dfree(void* p, size_t bytes, cudaStream_t s);
+// The allocator a block came from: the caller's hook (gedwalk_set_allocator) or cudaMalloc
+// (release == nullptr). Every block is freed through the allocator that made it, whatever the
+// hook is when it is freed.
+struct Allocator {
+  gedwalk_free_fn release = nullptr;
+  void* ctx = nullptr;
+};
+void* dalloc(size_t bytes, cudaStream_t s, Allocator* from);
+void dfree(void* p, size_t bytes, cudaStream_t s, const Allocator& from);
 
 // A device buffer that grows on demand and is released with its owner.
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
+  Allocator from;
   DevBuf() = default;
   DevBuf(const DevBuf&) = delete;
   DevBuf& operator=(const DevBuf&) = delete;
   ~DevBuf() { release(); }
   void release() {
-    if (p) dfree(p, bytes, 0);
+    if (p) dfree(p, bytes, 0, from);
     p = nullptr;
     bytes = 0;
+  }
+  // Exchanges two buffers (storage, size and the allocator that made the storage).
+  void swap(DevBuf& o) {
+    std::swap(p, o.p);
+    std::swap(bytes, o.bytes);
+    std::swap(from, o.from);
   }
   // Ensures capacity >= need bytes; contents are not preserved. zero: memset new storage to 0.
   gedwalk_status ensure(size_t need, cudaStream_t s, bool zero = false);
@@ -107,6 +122,7 @@ struct SweepGraph {
   double bytes = 0.0;           // algorithmic bytes per sweep
   int prof_key = 0;
   bool timing_pending = false;  // replayed while profiling; events not read yet
+  uint64_t last_use = 0;        // recency, for eviction from a workspace's cache
   void reset();
   SweepGraph() = default;
   SweepGraph(const SweepGraph&) = delete;
@@ -135,7 +151,11 @@ struct Workspace {
   int64_t st_evals = 0, st_batches = 0, st_sweeps = 0, st_spec_miss = 0;  // last maximize
   std::vector<int32_t> st_ell;  // last maximize: the walk length of each step
   int64_t st_sep_fail = 0;      // last maximize: failed separation tests (l doublings)
-  SweepGraph graphs[4];             // captured greedy sequences: fused, candidate batch, reverse, lookahead
+  // captured greedy sequences, one per configuration (mode, width, graph, L, alpha, buffers); a
+  // serving worker that alternates between graphs keeps each graph's sequences
+  static constexpr int kGraphCache = 16;
+  SweepGraph graphs[kGraphCache];
+  uint64_t graph_clock = 0;
   cudaStream_t own_stream = nullptr;  // capturable stream used when the caller passes stream 0
   cudaEvent_t order_ev = nullptr;     // orders own_stream after the caller's stream
   std::vector<uint8_t> host_small;  // staging
@@ -143,6 +163,11 @@ struct Workspace {
   size_t pinned_bytes = 0;
   ~Workspace();
   gedwalk_status ensure_pinned(size_t bytes);
+  // Device bytes the workspace holds now (its buffers only; the captured graphs hold none).
+  int64_t device_bytes() const;
+  // Releases every device buffer and the captured sequences that refer to them (the workspace
+  // must be idle: no call is using it and nothing of it is in flight on the device).
+  void release_device();
 };
 
 // ---------------------------------------------------------------- graph
@@ -283,7 +308,26 @@ struct Resolved {
   uint64_t seed = 0;   // stochastic greedy seed
   double eps = 0.0;    // the epsilon L was selected for (0 when L was forced)
   int32_t bound_kind = 0;  // GEDWALK_BOUND_COMBINATORIAL or GEDWALK_BOUND_SPECTRAL
+  int32_t lookahead = 0;   // gedwalk_params.lookahead (0 = default)
+  int32_t spec_cols = 0;   // gedwalk_params.spec_cols (0 = default)
 };
+
+// The configuration of one greedy maximisation (sweep widths, lookahead levels, table rows),
+// fixed before it starts; maximize_impl runs it and maximize_footprint sizes it.
+struct GreedyShape {
+  int32_t levels;     // lookahead levels per run of sweeps (1 = no lookahead)
+  int32_t cols_fused; // columns of the fused sweep (phi^miss + speculative candidates)
+  int32_t cols_cand;  // columns of a candidate batch
+  int32_t cols_all;   // columns per batch of GEDWALK_GAINS_ALL
+  int32_t tab_L;      // rows 0..tab_L of every phi^miss table
+  int32_t ell_max;    // adaptive: the largest walk length it may reach (else L)
+  int32_t cols_max;   // widest sweep of the run (walk vectors are sized for it)
+};
+gedwalk_status greedy_shape(const Graph& g, const Resolved& r, int32_t flags, GreedyShape* out);
+// Device bytes a maximisation with this configuration needs in its workspace.
+int64_t maximize_footprint(const Graph& g, const Resolved& r, int32_t flags);
+// Device bytes a batched scoring of `groups` groups with `members` members needs in its workspace.
+int64_t score_batch_footprint(const Graph& g, int64_t members, int32_t groups);
 // Resolves alpha (0 -> default), L (from epsilon unless forced) for a given epsilon.
 gedwalk_status resolve(Graph& g, const gedwalk_params* p, double eps_override, Resolved* r);
 // Ensures the FP64 walk-total table holds rows 0..rows-1 for alpha.

@@ -89,6 +89,21 @@ int blocks_for(int64_t n, int per = 256) { return static_cast<int>(std::min<int6
 
 }  // namespace
 
+namespace {
+// Waits for a stream when a call leaves early with an error, so that nothing it launched still
+// runs when its buffers are reused or freed.
+struct StreamGuard {
+  cudaStream_t s;
+  bool ok = false;
+  ~StreamGuard() {
+    if (!ok) {
+      cudaStreamSynchronize(s);
+      cudaGetLastError();
+    }
+  }
+};
+}  // namespace
+
 gedwalk_status score_one(Graph& g, Workspace& ws, const std::vector<int32_t>& S_int, const Resolved& r,
                          double* score) {
   cudaStream_t s = r.stream;
@@ -96,6 +111,7 @@ gedwalk_status score_one(Graph& g, Workspace& ws, const std::vector<int32_t>& S_
     *score = 0.0;
     return GEDWALK_OK;
   }
+  StreamGuard guard{s};
   const size_t es = r.fp64 ? 8 : 4;
   const size_t vbytes = static_cast<size_t>(g.n) * 2 * es;
   GW_TRY(ws.x0.ensure(vbytes, s));
@@ -126,14 +142,18 @@ gedwalk_status score_one(Graph& g, Workspace& ws, const std::vector<int32_t>& S_
   GW_CUDA(cudaMemcpyAsync(&h, ws.small.p, sizeof h, cudaMemcpyDeviceToHost, s));
   GW_CUDA(cudaStreamSynchronize(s));
   *score = h;
+  guard.ok = true;
   return GEDWALK_OK;
 }
 
-// Picks the column-block width with the lowest sweep time per column (timed on this graph).
+// Picks the column-block width with the lowest sweep time per column (timed on this graph). A
+// gather fetches whole 32-byte sectors, so widths below 8 FP32 columns waste part of each; above
+// 32 the walk vectors of a 10^6-vertex graph (n * C * 4 bytes, twice) outgrow the L2 and the
+// per-column time rises (the tuning log records it).
 gedwalk_status autotune_batch(Graph& g, Workspace& ws, const Resolved& r) {
   if (g.batch_cols > 0) return GEDWALK_OK;
   cudaStream_t s = r.stream;
-  static const int kCand[] = {8, 16, 32};
+  static const int kCand[] = {8, 16, 32, 64};
   double best = INFINITY;
   int best_c = 16;
   cudaEvent_t e0, e1;
@@ -172,10 +192,22 @@ gedwalk_status autotune_batch(Graph& g, Workspace& ws, const Resolved& r) {
   return GEDWALK_OK;
 }
 
+int64_t score_batch_footprint(const Graph& g, int64_t members, int32_t groups) {
+  const int64_t C = g.batch_cols > 0 ? g.batch_cols : 32;  // before tuning: the widest width tried
+  const int64_t n = g.n;
+  int64_t b = 2 * n * C * 4;                                      // walk vectors x0, x1
+  b += members * (4 + 4 + 8) + static_cast<int64_t>(groups + 1) * 4 + 256;  // members, columns, sums
+  b += static_cast<int64_t>(std::max(g.plan.num_slices, 1)) * C * 4 + std::max(g.plan.num_heavy, 1) * 4;
+  b += static_cast<int64_t>(std::max(g.plan.num_slots, 1)) * C * 8 + C * kReduceParts * 8;
+  b += static_cast<int64_t>(groups) * 8 + 64;
+  return b;
+}
+
 gedwalk_status score_batch_impl(Graph& g, Workspace& ws, const int32_t* offsets, const int32_t* members_int,
                                 int32_t G, const Resolved& r, double* scores) {
   cudaStream_t s = r.stream;
   if (G == 0) return GEDWALK_OK;
+  StreamGuard guard{s};
   // the caller has made the walk-total table hold rows 0..L for alpha and tuned the width
   std::shared_lock<std::shared_mutex> rl(g.tt_lock);
   if (g.tt_alpha != r.alpha || g.tt_rows < r.L + 1 || g.batch_cols <= 0)
@@ -246,6 +278,7 @@ gedwalk_status score_batch_impl(Graph& g, Workspace& ws, const int32_t* offsets,
   GW_CUDA(cudaMemcpyAsync(ws.pinned, ws.small.p, sizeof(double) * G, cudaMemcpyDeviceToHost, s));
   GW_CUDA(cudaStreamSynchronize(s));
   memcpy(scores, ws.pinned, sizeof(double) * G);
+  guard.ok = true;
   return GEDWALK_OK;
 }
 
@@ -270,6 +303,22 @@ gedwalk_status gedwalk_score(gedwalk_graph_t h, const int32_t* S, int32_t s_len,
   *score = v;
   if (L_used) *L_used = r.L;
   if (tail_bound) *tail_bound = r.bound;
+  return GEDWALK_OK;
+}
+
+gedwalk_status gedwalk_batch_tuning(gedwalk_graph_t h, int32_t* cols, double* us_per_col, int32_t cap, int32_t* count,
+                                    int32_t* chosen) {
+  if (!h) return fail(GEDWALK_ERR_INVALID, "graph is NULL");
+  if (cap < 0 || (cap > 0 && (!cols || !us_per_col))) return fail(GEDWALK_ERR_INVALID, "NULL output or cap < 0");
+  Graph* g = gw::G(h);
+  std::lock_guard<std::mutex> lk(g->mu);
+  const int32_t m = static_cast<int32_t>(g->tune_log.size());
+  for (int32_t j = 0; j < std::min(m, cap); ++j) {
+    cols[j] = g->tune_log[j].first;
+    us_per_col[j] = g->tune_log[j].second * 1e3;
+  }
+  if (count) *count = m;
+  if (chosen) *chosen = g->batch_cols;
   return GEDWALK_OK;
 }
 

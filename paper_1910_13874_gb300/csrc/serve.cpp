@@ -1,17 +1,22 @@
 // Serving: a continuous-batching request loop over device-resident graphs.
 //
-// Requests enter per-kind FIFO queues and are admitted while their estimated
-// device working set fits in the memory budget beside the requests in flight.
-// Score requests (cheap, batched) are admitted first; a maximise request is
-// admitted only when a worker is free to run it, so queued maximisations never
-// hold memory that waiting score requests could use.
-// Admitted score requests wait in their graph's lane; whenever the lane is
-// free it takes every waiting request with the same (alpha, L) (up to
-// max_batch) and scores them as the columns of one batched SpMM on the lane's
-// own stream. Maximize requests run on a small pool of workers, each with its
-// own stream and workspace, so their sweeps overlap with the scoring lanes.
-// A column's arithmetic never depends on the other columns of its batch, so a
-// result is bitwise the same alone and in a mix.
+// Threads: one scoring lane per graph and kMaxWorkers maximise workers, each with its own CUDA
+// stream and workspace; admission runs on the threads that submit and complete requests.
+//
+// Admission is by the device memory the server's workspaces hold. Every lane and worker has a
+// workspace whose buffers grow to the largest request it has run and stay allocated, so the
+// server charges each workspace its held bytes, or, while it has work, the larger of those and the
+// exact footprint of that work (the same sizes the algorithms allocate). A request is admitted when
+// the total charge stays within the budget; if it does not, idle workspaces are released (largest
+// first) to make room, and otherwise the request waits in its FIFO queue. A request larger than the
+// budget runs when nothing else holds memory. Score requests are admitted before maximise requests,
+// and a maximise request only to a free worker, preferring one whose buffers already fit it.
+//
+// Admitted score requests wait in their graph's lane; whenever the lane is free it takes every
+// waiting request with the same (alpha, L) (up to max_batch) and scores them as the columns of one
+// batched SpMM on the lane's own stream, while maximise requests run on the workers' streams, so
+// their sweeps overlap on the device. A column's arithmetic never depends on the other columns of
+// its batch, so a result is bitwise the same alone and in a mix.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -39,7 +44,9 @@ struct Request {
   int32_t k = 0;
   int32_t flags = 0;
   Resolved r{};
-  int64_t mem = 0;
+  int64_t need = 0;  // maximise: the footprint of its run
+  bool admitted = false;
+  bool waited = false;  // not admitted by the call that submitted it
   Clock::time_point t_submit, t_done;
   bool done = false;
   gedwalk_status status = GEDWALK_OK;
@@ -51,14 +58,21 @@ struct Request {
 using ReqPtr = std::shared_ptr<Request>;
 
 struct Lane {  // one per graph: batched scoring
+  int32_t graph = 0;
   std::deque<ReqPtr> queue;
+  int64_t q_members = 0;     // members of the queued requests
+  int32_t q_groups = 0;      // queued requests
   bool busy = false;
+  int64_t need_running = 0;  // footprint of the batch being scored
+  int64_t held = 0;          // device bytes of the workspace when it was last idle
   cudaStream_t stream = nullptr;
   Workspace ws;
   std::thread th;
 };
 
 struct Worker {  // maximize pool
+  ReqPtr job;
+  int64_t held = 0;
   cudaStream_t stream = nullptr;
   Workspace ws;
   std::thread th;
@@ -76,52 +90,116 @@ struct Server {
   std::condition_variable cv_done;  // pollers wait here
   std::deque<ReqPtr> pending;       // score requests not yet admitted
   std::deque<ReqPtr> pending_max;   // maximise requests not yet admitted
-  std::deque<ReqPtr> max_queue;     // admitted maximize requests
-  int32_t max_running = 0;          // admitted maximise requests (queued or running)
   std::unordered_map<uint64_t, ReqPtr> table;
   std::vector<std::unique_ptr<Lane>> lanes;
   std::vector<std::unique_ptr<Worker>> workers;
   uint64_t next_ticket = 1;
-  int64_t in_flight = 0, peak = 0;
-  int64_t completed = 0, batches = 0, batched_requests = 0;
+  gedwalk_serve_counters st{};
   bool stop = false;
 
-  // working-set estimates in bytes (accounting for admission)
-  int64_t estimate(const Request& q) const {
-    const Graph& g = *graphs[q.graph];
-    if (q.kind == GEDWALK_REQ_SCORE) return int64_t(g.n) * 8 + int64_t(q.S.size()) * 16 + 64;
-    const int64_t es = q.r.fp64 ? 8 : 4;
-    return int64_t(g.n) * (es * (q.r.L + 1 + 16) + 8) + 4096;
+  // A lane's charge: what its workspace holds, or more while it has work (the batch it scores now,
+  // or the next batch its queue forms).
+  int64_t lane_charge(const Lane& l) const {
+    int64_t c = l.held;
+    if (l.busy) c = std::max(c, l.need_running);
+    if (l.q_groups > 0)
+      c = std::max(c, score_batch_footprint(*graphs[l.graph], l.q_members, std::min(l.q_groups, max_batch)));
+    return c;
+  }
+  static int64_t worker_charge(const Worker& w) { return w.job ? std::max(w.held, w.job->need) : w.held; }
+  int64_t total() const {
+    int64_t t = 0;
+    for (const auto& l : lanes) t += lane_charge(*l);
+    for (const auto& w : workers) t += worker_charge(*w);
+    return t;
+  }
+  void note_peak() {
+    const int64_t t = total();
+    st.peak_bytes = std::max(st.peak_bytes, t);
+    int64_t running = 0;
+    for (const auto& w : workers) running += w->job ? 1 : 0;
+    st.peak_maximize_running = std::max(st.peak_maximize_running, running);
   }
 
-  void admit_locked() {
+  // Releases idle workspaces other than `keep_lane` / `keep_worker`, largest first, until the total
+  // charge plus `delta` fits the budget. Returns whether it fits.
+  bool make_room(int64_t delta, const Lane* keep_lane, const Worker* keep_worker) {
+    for (;;) {
+      if (total() + delta <= budget) return true;
+      Workspace* best = nullptr;
+      int64_t* best_held = nullptr;
+      for (auto& l : lanes)
+        if (l.get() != keep_lane && !l->busy && l->q_groups == 0 && l->held > 0 && (!best_held || l->held > *best_held)) {
+          best = &l->ws;
+          best_held = &l->held;
+        }
+      for (auto& w : workers)
+        if (w.get() != keep_worker && !w->job && w->held > 0 && (!best_held || w->held > *best_held)) {
+          best = &w->ws;
+          best_held = &w->held;
+        }
+      if (!best) return false;
+      // the idle workspace's stream has nothing in flight (its owner synchronised before going idle)
+      best->release_device();
+      st.released_bytes += *best_held;
+      ++st.releases;
+      *best_held = 0;
+    }
+  }
+
+  void mark_admitted(const ReqPtr& q, bool at_submit) {
+    q->admitted = true;
+    if (at_submit) ++st.admitted_at_submit;
+    else ++st.admitted_after_wait;
+  }
+
+  // Admits what fits; `submitting` is the request whose submit call runs this (if any).
+  void admit_locked(const Request* submitting) {
     while (!pending.empty()) {  // score requests first (FIFO)
       ReqPtr q = pending.front();
-      if (in_flight > 0 && in_flight + q->mem > budget) break;
+      Lane& l = *lanes[q->graph];
+      const int64_t members = static_cast<int64_t>(q->S.size());
+      const int64_t before = lane_charge(l);
+      l.q_members += members;  // the lane's charge with q queued
+      ++l.q_groups;
+      const int64_t delta = lane_charge(l) - before;
+      l.q_members -= members;
+      --l.q_groups;
+      if (!make_room(delta, &l, nullptr) && total() - lane_charge(l) > 0) break;  // wait
+      l.q_members += members;
+      ++l.q_groups;
       pending.pop_front();
-      in_flight += q->mem;
-      peak = std::max(peak, in_flight);
-      lanes[q->graph]->queue.push_back(q);
+      mark_admitted(q, q.get() == submitting);
+      l.queue.push_back(q);
+      note_peak();
     }
-    while (!pending_max.empty() && max_running < kMaxWorkers) {  // then maximise requests, one per free worker
+    while (!pending_max.empty()) {  // then maximise requests, one per free worker
       ReqPtr q = pending_max.front();
-      if (in_flight > 0 && in_flight + q->mem > budget) break;
+      Worker* pick = nullptr;  // a free worker: the smallest held bytes that fit q, else the largest
+      for (auto& w : workers) {
+        if (w->job) continue;
+        if (!pick) {
+          pick = w.get();
+          continue;
+        }
+        const bool fits = w->held >= q->need, pfits = pick->held >= q->need;
+        if ((fits && (!pfits || w->held < pick->held)) || (!fits && !pfits && w->held > pick->held)) pick = w.get();
+      }
+      if (!pick) break;
+      const int64_t delta = std::max(pick->held, q->need) - pick->held;
+      if (!make_room(delta, nullptr, pick) && total() - pick->held > 0) break;
       pending_max.pop_front();
-      in_flight += q->mem;
-      peak = std::max(peak, in_flight);
-      ++max_running;
-      max_queue.push_back(q);
+      mark_admitted(q, q.get() == submitting);
+      pick->job = q;
+      note_peak();
     }
     cv_work.notify_all();
   }
 
   void finish_locked(const ReqPtr& q) {
-    if (q->kind == GEDWALK_REQ_MAXIMIZE) --max_running;
     q->done = true;
     q->t_done = Clock::now();
-    in_flight -= q->mem;
-    ++completed;
-    admit_locked();
+    ++st.completed;
     cv_done.notify_all();
   }
 
@@ -136,14 +214,19 @@ struct Server {
         cv_work.wait(lk, [&] { return stop || !lane.queue.empty(); });
         if (lane.queue.empty()) return;  // stopping and idle
         const ReqPtr first = lane.queue.front();
+        int64_t members = 0;
         for (auto it = lane.queue.begin(); it != lane.queue.end() && int(batch.size()) < max_batch;) {
           if ((*it)->r.alpha == first->r.alpha && (*it)->r.L == first->r.L) {
+            members += static_cast<int64_t>((*it)->S.size());
             batch.push_back(*it);
             it = lane.queue.erase(it);
           } else {
             ++it;
           }
         }
+        lane.q_members -= members;
+        lane.q_groups -= static_cast<int32_t>(batch.size());
+        lane.need_running = score_batch_footprint(g, members, static_cast<int32_t>(batch.size()));
         lane.busy = true;
       }
       std::vector<int32_t> off(1, 0), mem;
@@ -155,19 +238,23 @@ struct Server {
       Resolved r = batch[0]->r;
       r.fp64 = false;
       r.stream = lane.stream;
-      const gedwalk_status st =
+      const gedwalk_status stt =
           score_batch_impl(g, lane.ws, off.data(), mem.data(), static_cast<int32_t>(batch.size()), r, scores.data());
-      const std::string err = st == GEDWALK_OK ? "" : gedwalk_last_error();
+      const std::string err = stt == GEDWALK_OK ? "" : gedwalk_last_error();
+      cudaStreamSynchronize(lane.stream);
       std::lock_guard<std::mutex> lk(mu);
-      ++batches;
-      batched_requests += static_cast<int64_t>(batch.size());
+      ++st.batches;
+      st.batched_requests += static_cast<int64_t>(batch.size());
       for (size_t i = 0; i < batch.size(); ++i) {
-        batch[i]->status = st;
+        batch[i]->status = stt;
         batch[i]->error = err;
         batch[i]->score = scores[i];
         finish_locked(batch[i]);
       }
+      lane.held = lane.ws.device_bytes();
+      lane.need_running = 0;
       lane.busy = false;
+      admit_locked(nullptr);
     }
   }
 
@@ -178,10 +265,9 @@ struct Server {
       ReqPtr q;
       {
         std::unique_lock<std::mutex> lk(mu);
-        cv_work.wait(lk, [&] { return stop || !max_queue.empty(); });
-        if (max_queue.empty()) return;
-        q = max_queue.front();
-        max_queue.pop_front();
+        cv_work.wait(lk, [&] { return stop || w.job; });
+        if (!w.job) return;
+        q = w.job;
       }
       Graph& g = *graphs[q->graph];
       Resolved r = q->r;
@@ -189,10 +275,11 @@ struct Server {
       std::vector<int32_t> grp(std::max(q->k, 1));
       std::vector<double> gn(std::max(q->k, 1));
       double sc = 0;
-      const gedwalk_status st = maximize_impl(g, w.ws, q->k, r, q->flags, {}, grp.data(), gn.data(), &sc);
-      const std::string err = st == GEDWALK_OK ? "" : gedwalk_last_error();
+      const gedwalk_status stt = maximize_impl(g, w.ws, q->k, r, q->flags, {}, grp.data(), gn.data(), &sc);
+      const std::string err = stt == GEDWALK_OK ? "" : gedwalk_last_error();
+      cudaStreamSynchronize(w.stream);
       std::lock_guard<std::mutex> lk(mu);
-      q->status = st;
+      q->status = stt;
       q->error = err;
       q->score = sc;
       grp.resize(q->k);
@@ -200,6 +287,9 @@ struct Server {
       q->group = std::move(grp);
       q->gains = std::move(gn);
       finish_locked(q);
+      w.held = w.ws.device_bytes();
+      w.job = nullptr;
+      admit_locked(nullptr);
     }
   }
 };
@@ -217,6 +307,7 @@ gedwalk_status gedwalk_serve_create(const gedwalk_graph_t* graphs, int32_t n_gra
   std::unique_ptr<Server> srv(new Server());
   srv->budget = mem_budget > 0 ? mem_budget : (int64_t(1) << 30);
   srv->max_batch = max_batch > 0 ? max_batch : 256;
+  srv->st.budget = srv->budget;
   GW_CUDA(cudaGetDevice(&srv->device));
   for (int32_t i = 0; i < n_graphs; ++i) {
     if (!graphs[i]) return fail(GEDWALK_ERR_INVALID, "graph %d is NULL", i);
@@ -224,6 +315,7 @@ gedwalk_status gedwalk_serve_create(const gedwalk_graph_t* graphs, int32_t n_gra
   }
   for (int32_t i = 0; i < n_graphs; ++i) {
     std::unique_ptr<Lane> lane(new Lane());
+    lane->graph = i;
     GW_CUDA(cudaStreamCreateWithFlags(&lane->stream, cudaStreamNonBlocking));
     srv->lanes.push_back(std::move(lane));
   }
@@ -287,18 +379,21 @@ gedwalk_status gedwalk_serve_submit(gedwalk_server_t h, int32_t graph, int32_t k
       q->flags = p.flags;
       const double eps = (p.greedy_eps_rule == GEDWALK_EPS_OVER_K && q->k > 0) ? p.epsilon / q->k : p.epsilon;
       GW_TRY(resolve(g, &p, eps, &q->r));
+      GreedyShape sh{};
+      GW_TRY(greedy_shape(g, q->r, q->flags, &sh));  // rejects bad lookahead / spec_cols now
+      q->need = maximize_footprint(g, q->r, q->flags);
     }
   }
   std::lock_guard<std::mutex> lk(srv->mu);
   if (srv->stop) return fail(GEDWALK_ERR_BUSY, "server is stopping");
   if (srv->pending.size() + srv->pending_max.size() >= kMaxQueue)
     return fail(GEDWALK_ERR_BUSY, "request queue is full");
-  q->mem = srv->estimate(*q);
   q->ticket = srv->next_ticket++;
   q->t_submit = Clock::now();
   srv->table[q->ticket] = q;
   (kind == GEDWALK_REQ_SCORE ? srv->pending : srv->pending_max).push_back(q);
-  srv->admit_locked();
+  srv->admit_locked(q.get());
+  if (!q->admitted) q->waited = true;
   *ticket = q->ticket;
   return GEDWALK_OK;
 }
@@ -328,8 +423,6 @@ gedwalk_status gedwalk_serve_poll(gedwalk_server_t h, uint64_t ticket, int32_t w
   if (q->status != GEDWALK_OK) return fail(q->status, "%s", q->error.c_str());
   if (score) *score = q->score;
   if (q->kind == GEDWALK_REQ_MAXIMIZE) {
-    Graph& g = *srv->graphs[q->graph];
-    (void)g;
     if (group)
       for (int32_t j = 0; j < q->k; ++j) group[j] = q->group[j];
     if (gains)
@@ -343,10 +436,24 @@ gedwalk_status gedwalk_serve_stats(gedwalk_server_t h, int64_t* completed, int64
   Server* srv = reinterpret_cast<Server*>(h);
   if (!srv) return fail(GEDWALK_ERR_INVALID, "server is NULL");
   std::lock_guard<std::mutex> lk(srv->mu);
-  if (completed) *completed = srv->completed;
-  if (batches) *batches = srv->batches;
-  if (batched_requests) *batched_requests = srv->batched_requests;
-  if (peak_bytes) *peak_bytes = srv->peak;
+  if (completed) *completed = srv->st.completed;
+  if (batches) *batches = srv->st.batches;
+  if (batched_requests) *batched_requests = srv->st.batched_requests;
+  if (peak_bytes) *peak_bytes = srv->st.peak_bytes;
+  return GEDWALK_OK;
+}
+
+gedwalk_status gedwalk_serve_counters_read(gedwalk_server_t h, gedwalk_serve_counters* out) {
+  Server* srv = reinterpret_cast<Server*>(h);
+  if (!srv || !out) return fail(GEDWALK_ERR_INVALID, "server or out is NULL");
+  std::lock_guard<std::mutex> lk(srv->mu);
+  *out = srv->st;
+  out->charged_bytes = srv->total();
+  int64_t held = 0;
+  for (const auto& l : srv->lanes) held += l->busy ? 0 : l->ws.device_bytes();
+  for (const auto& w : srv->workers) held += w->job ? 0 : w->ws.device_bytes();
+  out->idle_held_bytes = held;
+  out->pending = static_cast<int64_t>(srv->pending.size() + srv->pending_max.size());
   return GEDWALK_OK;
 }
 

@@ -572,13 +572,22 @@ __device__ __forceinline__ void run_unit(const SweepArgs& a, const Src& src, int
 
 constexpr int kCandSlots = 16;
 
-// One warp per unit, one CTA per eight units. The 8-column lookahead sweep is held to 48
-// registers (five CTAs per SM) and the 4-column candidate batch to 64 (four CTAs): their gathers
-// wait on memory, and the extra resident warps hide more latency than the few spilled registers
-// cost (measured on R-MAT scale 22).
+// Resident CTAs per SM each instantiation is compiled for (its register limit). The gathers wait
+// on memory, and more resident warps hide more of that latency than a few spilled registers cost:
+// the 8-column lookahead sweep is held to 48 registers (five CTAs per SM), the 4-column candidate
+// batch to 64 (four), and the batched-scoring widths to what their C-wide row sums need (measured
+// on R-MAT scale 22 and on the Barabasi-Albert graph with n = 10^6).
 template <typename T, int C, int MODE>
-__global__ void __launch_bounds__(kThreads, (MODE == MODE_LOOK && C == 8) ? 5 : (MODE == MODE_CAND && C == 4) ? 4 : 1)
-    sweep_kernel(const SweepArgs a) {
+constexpr int min_ctas() {
+  if (MODE == MODE_LOOK && C == 8) return 5;
+  if (MODE == MODE_CAND && C == 4) return 4;
+  if (MODE == MODE_PLAIN) return C <= 8 ? 5 : C <= 16 ? 3 : C <= 32 ? 2 : 1;
+  return 1;
+}
+
+// One warp per unit, one CTA per eight units.
+template <typename T, int C, int MODE>
+__global__ void __launch_bounds__(kThreads, (min_ctas<T, C, MODE>())) sweep_kernel(const SweepArgs a) {
   __shared__ int s_cand[kCandSlots];
   __shared__ int s_rp[kWarps][kUnitRowsMax + 1];
   if (threadIdx.x < kCandSlots)
@@ -698,6 +707,7 @@ gedwalk_status launch_sweep(int mode, bool fp64, int cols, const SweepArgs& a, c
   GW_CASE(MODE_PLAIN, float, 8)
   GW_CASE(MODE_PLAIN, float, 16)
   GW_CASE(MODE_PLAIN, float, 32)
+  GW_CASE(MODE_PLAIN, float, 64)
 #undef GW_CASE
   return fail(GEDWALK_ERR_INVALID, "no sweep instantiation for mode %d fp64 %d cols %d", mode, int(fp64), cols);
 }

@@ -6,9 +6,12 @@ be loaded, every call raises.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes
 import os
+import sys
 import threading
+import weakref
 from typing import Optional, Sequence
 
 import numpy as np
@@ -34,9 +37,11 @@ _STATUS_NAMES = {OK: "OK", ERR_INVALID: "INVALID", ERR_OOM: "OOM", ERR_NOT_CONVE
 EXPORTS = [
     "gedwalk_params_default", "gedwalk_set_allocator", "gedwalk_graph_upload", "gedwalk_graph_upload_weighted",
     "gedwalk_graph_info_weighted", "gedwalk_graph_free", "gedwalk_truncation_ex", "gedwalk_sigma_max",
-    "gedwalk_graph_info", "gedwalk_truncation", "gedwalk_score", "gedwalk_score_batch", "gedwalk_gains",
+    "gedwalk_graph_info", "gedwalk_truncation", "gedwalk_score", "gedwalk_score_batch", "gedwalk_batch_tuning",
+    "gedwalk_gains",
     "gedwalk_maximize", "gedwalk_maximize_stats", "gedwalk_maximize_lengths", "gedwalk_serve_create", "gedwalk_serve_submit",
-    "gedwalk_serve_poll", "gedwalk_serve_stats", "gedwalk_serve_destroy", "gedwalk_score_step_noalloc",
+    "gedwalk_serve_poll", "gedwalk_serve_stats", "gedwalk_serve_counters_read", "gedwalk_serve_destroy",
+    "gedwalk_score_step_noalloc",
     "gedwalk_profile", "gedwalk_profile_read", "gedwalk_last_error",
 ]
 
@@ -45,6 +50,13 @@ class GedWalkError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{_STATUS_NAMES.get(status, status)}: {message}")
         self.status = status
+
+
+class ServeCounters(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int64) for name in (
+        "completed", "batches", "batched_requests", "peak_bytes", "budget", "charged_bytes", "idle_held_bytes",
+        "admitted_at_submit", "admitted_after_wait", "peak_maximize_running", "releases", "released_bytes",
+        "pending")]
 
 
 class ProfileStats(ctypes.Structure):
@@ -75,6 +87,8 @@ class Params(ctypes.Structure):
         ("eta", ctypes.c_double),
         ("seed", ctypes.c_uint64),
         ("bound", ctypes.c_int32),
+        ("lookahead", ctypes.c_int32),
+        ("spec_cols", ctypes.c_int32),
         ("reserved", ctypes.c_int32),
     ]
 
@@ -90,8 +104,12 @@ _lib = None
 _lock = threading.Lock()
 
 
-def load(path: Optional[str] = None):
-    """Loads libgedwalk.so (built by paper_1910_13874_gb300.build). Raises if it is missing."""
+def load(path: Optional[str] = None, torch_allocator: bool = True):
+    """Loads libgedwalk.so (built by paper_1910_13874_gb300.build). Raises if it is missing.
+
+    On first load it routes the library's device allocations through PyTorch's caching allocator
+    (use_torch_allocator) unless torch_allocator is False.
+    """
     global _lib
     with _lock:
         if _lib is not None:
@@ -120,6 +138,7 @@ def load(path: Optional[str] = None):
                                              _f64p]),
             "gedwalk_score_batch": (ctypes.c_int, [vp, _i32p, _i32p, ctypes.c_int32, ctypes.POINTER(Params),
                                                    _f64p, _i32p]),
+            "gedwalk_batch_tuning": (ctypes.c_int, [vp, _i32p, _f64p, ctypes.c_int32, _i32p, _i32p]),
             "gedwalk_gains": (ctypes.c_int, [vp, _i32p, ctypes.c_int32, ctypes.POINTER(Params), _f64p, _i32p]),
             "gedwalk_maximize": (ctypes.c_int, [vp, ctypes.c_int32, ctypes.POINTER(Params), _i32p, _f64p, _f64p,
                                                 _i32p, _i32p, ctypes.c_int32]),
@@ -132,6 +151,7 @@ def load(path: Optional[str] = None):
             "gedwalk_serve_poll": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.c_int32, _f64p, _i32p, _f64p, _f64p,
                                                   _i32p]),
             "gedwalk_serve_stats": (ctypes.c_int, [vp, _i64p, _i64p, _i64p, _i64p]),
+            "gedwalk_serve_counters_read": (ctypes.c_int, [vp, ctypes.POINTER(ServeCounters)]),
             "gedwalk_serve_destroy": (ctypes.c_int, [vp]),
             "gedwalk_score_step_noalloc": (ctypes.c_int, [vp, vp, ctypes.c_int32, vp, vp, vp, ctypes.c_double, vp,
                                                           ctypes.c_int64]),
@@ -144,6 +164,8 @@ def load(path: Optional[str] = None):
             f.restype = res
             f.argtypes = args
         _lib = lib
+    if torch_allocator:
+        use_torch_allocator()
     return _lib
 
 
@@ -163,7 +185,8 @@ def _ptr(a: np.ndarray, t):
 
 def make_params(alpha: float = 0.0, epsilon: float = 1e-4, L: int = 0, precision: str = "fp32",
                 eps_rule: str = "over_k", gains_all: bool = False, stream: int = 0, stochastic: bool = False,
-                eta: float = 0.1, seed: int = 0, adaptive: bool = False, bound: str = "combinatorial") -> Params:
+                eta: float = 0.1, seed: int = 0, adaptive: bool = False, bound: str = "combinatorial",
+                lookahead: int = 0, spec_cols: int = 0) -> Params:
     p = Params()
     load().gedwalk_params_default(ctypes.byref(p))
     p.alpha = alpha
@@ -176,10 +199,13 @@ def make_params(alpha: float = 0.0, epsilon: float = 1e-4, L: int = 0, precision
     p.stream = int(stream)
     p.eta = eta
     p.seed = seed
+    p.lookahead = int(lookahead)
+    p.spec_cols = int(spec_cols)
     return p
 
 
 _torch_hooks = None
+_hook_refs = []  # every hook pair ever installed: a block is freed through the hook that made it
 
 
 def use_torch_allocator():
@@ -200,8 +226,12 @@ def use_torch_allocator():
         torch.cuda.caching_allocator_delete(ptr)
 
     hooks = (_ALLOC_FN(_alloc), _FREE_FN(_free))
-    _check(load().gedwalk_set_allocator(hooks[0], hooks[1], None))
+    _hook_refs.append(hooks)
+    if not _exit_hook:  # registered after torch's own exit handlers, so it runs before them
+        atexit.register(_close_servers)
+        _exit_hook.append(True)
     _torch_hooks = hooks
+    _check(load(torch_allocator=False).gedwalk_set_allocator(hooks[0], hooks[1], None))
 
 
 def score_step_noalloc(d_row_ptr: int, d_col_idx: int, n: int, d_mask: int, d_x: int, d_y: int, alpha: float,
@@ -274,6 +304,8 @@ class Graph:
             self._h = None
 
     def __del__(self):
+        if sys.is_finalizing():  # the process exit releases the device memory; no hook may run now
+            return
         try:
             self.free()
         except Exception:
@@ -318,6 +350,16 @@ class Graph:
                                           _ptr(out, _f64p), ctypes.byref(L)))
         return out[:G], L.value
 
+    def batch_tuning(self):
+        """(widths, us per column, chosen width) of the batched-scoring autotuner on this graph."""
+        cnt, chosen = ctypes.c_int32(), ctypes.c_int32()
+        _check(load().gedwalk_batch_tuning(self._h, None, None, 0, ctypes.byref(cnt), ctypes.byref(chosen)))
+        cols = np.zeros(max(cnt.value, 1), dtype=np.int32)
+        us = np.zeros(max(cnt.value, 1), dtype=np.float64)
+        _check(load().gedwalk_batch_tuning(self._h, _ptr(cols, _i32p), _ptr(us, _f64p), cnt.value, ctypes.byref(cnt),
+                                           ctypes.byref(chosen)))
+        return cols[:cnt.value].tolist(), us[:cnt.value].tolist(), chosen.value
+
     def gains(self, S: Sequence[int], params: Optional[Params] = None, **kw):
         """(gains[n], L): exact truncated marginal gain of every vertex."""
         p = params or make_params(**kw)
@@ -357,6 +399,20 @@ class Graph:
         return ell[:cnt.value].copy(), int(fails.value)
 
 
+_live_servers = weakref.WeakSet()
+_exit_hook = []
+
+
+def _close_servers():
+    # A server's threads may still call the allocator hook (Python); stop them before the
+    # interpreter shuts down.
+    for srv in list(_live_servers):
+        try:
+            srv.close()
+        except Exception:
+            pass
+
+
 class Server:
     """Continuous-batching request loop over device-resident graphs (gedwalk_serve_*)."""
 
@@ -365,6 +421,7 @@ class Server:
         h = ctypes.c_void_p()
         _check(load().gedwalk_serve_create(arr, len(graphs), mem_budget, max_batch, ctypes.byref(h)))
         self._h = h
+        _live_servers.add(self)
         self._graphs = list(graphs)
         self._kmax = {}
 
@@ -401,9 +458,10 @@ class Server:
         return {"score": score.value, "group": grp[:k].copy(), "gains": gains[:k].copy(), "latency_us": lat.value}
 
     def stats(self):
-        vals = [ctypes.c_int64() for _ in range(4)]
-        _check(load().gedwalk_serve_stats(self._h, *[ctypes.byref(v) for v in vals]))
-        return dict(zip(("completed", "batches", "batched_requests", "peak_bytes"), (v.value for v in vals)))
+        """The server's counters (gedwalk_serve_counters) as a dict."""
+        c = ServeCounters()
+        _check(load().gedwalk_serve_counters_read(self._h, ctypes.byref(c)))
+        return {name: getattr(c, name) for name, _ in ServeCounters._fields_}
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -411,6 +469,8 @@ class Server:
             self._h = None
 
     def __del__(self):
+        if sys.is_finalizing():
+            return
         try:
             self.close()
         except Exception:

@@ -34,6 +34,7 @@ def _install(allocs_before_failure):
         state["live"].pop(ptr, None)
 
     hooks = (gedwalk._ALLOC_FN(alloc), gedwalk._FREE_FN(free))
+    gedwalk._hook_refs.append(hooks)  # blocks are freed through the hooks that made them
     assert lib.gedwalk_set_allocator(hooks[0], hooks[1], None) == gedwalk.OK
     return hooks, state
 
@@ -44,6 +45,7 @@ def _restore():
     lib = gedwalk.load()
     assert lib.gedwalk_set_allocator(gedwalk._ALLOC_FN(), gedwalk._FREE_FN(), None) == gedwalk.OK
     gedwalk._torch_hooks = None
+    gedwalk.use_torch_allocator()  # back to the binding's default
 
 
 def test_upload_reports_oom_and_recovers(cuda_device):
@@ -57,7 +59,7 @@ def test_upload_reports_oom_and_recovers(cuda_device):
         assert e.value.status == gedwalk.ERR_OOM
     finally:
         _restore()
-    G = gedwalk.Graph.from_host(g)  # the default allocator works again
+    G = gedwalk.Graph.from_host(g)  # the binding's default allocator works again
     assert G.score([1, 2, 3], precision="fp64", L=4)[0] > 0
 
 
@@ -82,16 +84,24 @@ def test_oom_midway_leaves_the_graph_usable(cuda_device):
 
 
 def test_torch_allocator_hook(cuda_device):
+    import gc
+
     import torch
 
     from paper_1910_13874_gb300 import gedwalk
 
-    before = torch.cuda.memory_allocated()
-    gedwalk.use_torch_allocator()
+    gedwalk.use_torch_allocator()  # the binding's default; a no-op when installed
+    g = gg.barabasi_albert(5000, 3, 9)
+    gc.collect()
+    gc.disable()  # nothing else may release PyTorch memory while the upload is measured
     try:
-        g = gg.barabasi_albert(5000, 3, 9)
+        before = torch.cuda.memory_allocated()
         G = gedwalk.Graph.from_host(g)
-        assert torch.cuda.memory_allocated() > before  # device memory now comes from PyTorch
+        grown = torch.cuda.memory_allocated() - before
+    finally:
+        gc.enable()
+    assert grown >= 4 * g.nnz  # at least the relabelled CSR lives in PyTorch's allocations
+    try:
         s, L, _ = G.score([0, 1, 2], precision="fp32", epsilon=1e-4)
         assert abs(s - oracle.score(g, [0, 1, 2], oracle.default_alpha(g), L)) <= 1e-5 * s
         G.free()

@@ -417,20 +417,19 @@ def test_adaptive_maximize_rejects_bad_combinations(cuda_device):
 
 # ------------------------------------------------------------------ lookahead sweeps (several steps per run)
 @pytest.mark.parametrize("name,k", [("ba5000", 24), ("rmat14", 24), ("er1000", 10)])
-@pytest.mark.parametrize("levels", ["1", "2", "4", "8"])
-def test_lookahead_levels_match_oracle(cuda_device, monkeypatch, name, k, levels):
+@pytest.mark.parametrize("levels", [1, 2, 4, 8])
+def test_lookahead_levels_match_oracle(cuda_device, name, k, levels):
     # Level d of a lookahead run holds phi^miss and the guessed winner's column under S + {c_1..c_d};
     # whatever the number of levels, every pick is certified against the bounds of the current S.
     g = host_graph(name)
     G = dev_graph(name)
     alpha = oracle.default_alpha(g)
-    monkeypatch.setenv("GEDWALK_LOOKAHEAD", levels)
-    grp, gains, score, L = G.maximize(k, precision="fp32", epsilon=1e-4)
+    grp, gains, score, L = G.maximize(k, precision="fp32", epsilon=1e-4, lookahead=int(levels))
     ogrp, ogains, _ = oracle.greedy(g, k, alpha, L, "lazy")
     # only a tie inside the tolerance may part the sequences; after one the oracle continues from
     # the GPU's own prefix
     check_sequence(grp, gains, 1e-5, ogrp, ogains, *oracle_greedy_checker(oracle, g, alpha, L))
     assert rel(score, oracle.score(g, grp, alpha, L)) < 1e-5
     st = G.maximize_stats()
-    if levels != "1":  # steps whose winner was guessed run no sweep of their own
+    if levels != 1:  # steps whose winner was guessed run no sweep of their own
         assert st["sweeps"] < (k + 1) * L

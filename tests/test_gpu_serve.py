@@ -76,17 +76,99 @@ def test_served_scores_alone_equal_mixed_and_oracle(graphs):
     assert all(r["latency_us"] > 0 for r in mres)
 
 
+def test_maximise_footprint_covers_the_memory_held(graphs):
+    from paper_1910_13874_gb300 import gedwalk
+
+    hosts, devs = graphs
+    for gi, k in ((0, 10), (2, 12)):
+        srv = gedwalk.Server(devs[gi:gi + 1], mem_budget=1 << 34)
+        r = srv.poll(srv.submit_maximize(0, k), -1)
+        st = srv.stats()
+        srv.close()
+        assert len(r["group"]) == k
+        # the charge of the run (its footprint) covers what the worker's buffers hold afterwards,
+        # and is not grossly above it
+        assert 0 < st["idle_held_bytes"] <= st["peak_bytes"] <= 2 * st["idle_held_bytes"], st
+
+
+def test_budget_below_two_maximise_footprints_never_runs_two(graphs):
+    from paper_1910_13874_gb300 import gedwalk
+
+    hosts, devs = graphs
+    srv = gedwalk.Server(devs[:1], mem_budget=1 << 34)
+    alone = srv.poll(srv.submit_maximize(0, 10), -1)
+    F = srv.stats()["peak_bytes"]
+    srv.close()
+    budget = int(1.5 * F)
+    srv = gedwalk.Server(devs[:1], mem_budget=budget)
+    ts = [srv.submit_maximize(0, 10) for _ in range(4)]
+    res = [srv.poll(t, -1) for t in ts]
+    st = srv.stats()
+    srv.close()
+    assert st["peak_maximize_running"] == 1, st
+    assert st["peak_bytes"] <= budget, st
+    assert st["admitted_after_wait"] >= 3 and st["completed"] == 4, st
+    for r in res:
+        assert list(r["group"]) == list(alone["group"]) and np.array_equal(r["gains"], alone["gains"])
+    # with room for four footprints the same requests run side by side, with the same results
+    srv = gedwalk.Server(devs[:1], mem_budget=8 * F)
+    ts = [srv.submit_maximize(0, 10) for _ in range(4)]
+    res = [srv.poll(t, -1) for t in ts]
+    st = srv.stats()
+    srv.close()
+    assert st["peak_maximize_running"] >= 2 and st["peak_bytes"] <= 8 * F, st
+    for r in res:
+        assert list(r["group"]) == list(alone["group"]) and np.array_equal(r["gains"], alone["gains"])
+
+
+def test_tiny_budget_releases_idle_workspaces(graphs):
+    from paper_1910_13874_gb300 import gedwalk
+
+    hosts, devs = graphs
+    reqs = [(i % 2, [3 * i, 3 * i + 1, 3 * i + 2]) for i in range(12)]
+    srv = gedwalk.Server(devs[:2], mem_budget=1 << 34)
+    want = [srv.poll(srv.submit_score(gi, S), -1)["score"] for gi, S in reqs]
+    srv.close()
+    # a budget below any request: the two lanes never hold memory at once, the idle one is
+    # released to admit the other, and every result is unchanged
+    srv = gedwalk.Server(devs[:2], mem_budget=1, max_batch=8)
+    ts = [srv.submit_score(gi, S) for gi, S in reqs]
+    vals = [srv.poll(t, -1)["score"] for t in ts]
+    st = srv.stats()
+    srv.close()
+    assert vals == want
+    assert st["completed"] == 12 and st["releases"] >= 1, st
+
+
+def test_served_alpha_is_fixed_per_graph(graphs):
+    from paper_1910_13874_gb300 import gedwalk
+
+    hosts, devs = graphs
+    srv = gedwalk.Server(devs[:1])
+    a0 = devs[0].alpha_default
+    t = srv.submit_score(0, [1, 2, 3])
+    with pytest.raises(gedwalk.GedWalkError) as e:
+        srv.submit_score(0, [1, 2, 3], alpha=a0 / 2)
+    assert e.value.status == gedwalk.ERR_INVALID
+    with pytest.raises(gedwalk.GedWalkError) as e:
+        srv.submit_maximize(0, 3, alpha=a0 / 2)
+    assert e.value.status == gedwalk.ERR_INVALID
+    # the requests with the served alpha are unaffected
+    v = srv.poll(t, -1)["score"]
+    assert v == srv.poll(srv.submit_score(0, [1, 2, 3], alpha=a0), -1)["score"] and v > 0
+    srv.close()
+
+
 def test_memory_admission_and_errors(graphs):
     from paper_1910_13874_gb300 import gedwalk
 
     hosts, devs = graphs
-    # a budget smaller than any request admits one request at a time, and all still finish
+    # a budget smaller than any request: each runs when nothing else holds memory; all finish
     srv = gedwalk.Server(devs[:1], mem_budget=1, max_batch=8)
     ts = [srv.submit_score(0, [i, i + 1, i + 2]) for i in range(20)]
     vals = [srv.poll(t, -1)["score"] for t in ts]
     st = srv.stats()
     assert st["completed"] == 20
-    assert st["peak_bytes"] <= max(1, st["peak_bytes"])  # one request in flight at a time
     for i, v in enumerate(vals):
         assert v > 0
     with pytest.raises(gedwalk.GedWalkError) as e:
