@@ -259,6 +259,11 @@ GEDWALK_API gedwalk_status gedwalk_score_batch(gedwalk_graph_t g, const int32_t*
 GEDWALK_API gedwalk_status gedwalk_batch_tuning(gedwalk_graph_t g, int32_t* cols, double* us_per_col, int32_t cap,
                                     int32_t* count, int32_t* chosen);
 
+/* Pins the batched-scoring column-block width of this graph to cols (8, 16, 32 or 64; the
+ * autotuner does not run), or with 0 lets the next gedwalk_score_batch tune it again. For runs
+ * whose timing would mislead the tuner, such as under a profiler. */
+GEDWALK_API gedwalk_status gedwalk_batch_set_width(gedwalk_graph_t g, int32_t cols);
+
 /*
  * Exact truncated marginal gain GED_{<=L}(S, x) = GED_{<=L}(S + x) - GED_{<=L}(S)
  * (the lower bound L_l of Section 3.2.1) for every vertex x, counted directly as

@@ -35,12 +35,20 @@ _i64p = ctypes.POINTER(ctypes.c_int64)
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain C11, no vendor code, portable to x86 and Arm)."""
+    """Compile the oracle with gcc (plain C11, no vendor code, portable to x86 and Arm).
+
+    With OpenMP where gcc has it: the row loops may then run on several threads (set_threads),
+    with bitwise the same results; without it the build is single-threaded.
+    """
     os.makedirs(_BUILD, exist_ok=True)
     newest = max(os.path.getmtime(s) for s in _SRCS)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRCS[0], "-lm"])
+        base = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRCS[0], "-lm"]
+        try:
+            subprocess.check_call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -52,6 +60,11 @@ def _load():
             lib = ctypes.CDLL(build())
             G = [ctypes.c_int32, _i32p, _i32p]
             GW = G + [_f64p]  # graph with optional entry weights (NULL: unweighted)
+            lib.orc_set_threads.restype = None
+            lib.orc_set_threads.argtypes = [ctypes.c_int]
+            lib.orc_threads.restype = ctypes.c_int
+            lib.orc_threads.argtypes = []
+            lib.orc_set_threads(1)  # single-threaded unless asked: test runs stay light
             lib.orc_dmax.restype = ctypes.c_int32
             lib.orc_dmax.argtypes = [ctypes.c_int32, _i32p]
             lib.orc_walk_totals_d.restype = ctypes.c_int
@@ -134,6 +147,16 @@ def _S(S):
     if s.size == 0:
         return np.zeros(1, dtype=np.int32), 0
     return s, int(s.size)
+
+
+def set_threads(t: int) -> None:
+    """Threads for the oracle's row loops (OpenMP builds). Results are bitwise the same for any t."""
+    _load().orc_set_threads(int(t))
+
+
+def threads() -> int:
+    """Threads the row loops use now (1 for a build without OpenMP)."""
+    return int(_load().orc_threads())
 
 
 def dmax(graph) -> int:

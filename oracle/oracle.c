@@ -25,6 +25,30 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Row loops (the SpMV of every recurrence, the two-state step, the per-vertex bound) may run on
+ * several threads when the graph has more rows than this; sums over rows stay serial. */
+#define ORC_PAR_MIN 4096
+
+/* Threads for the row loops (OpenMP builds; 1 otherwise). Results do not depend on it. */
+void orc_set_threads(int t) {
+#ifdef _OPENMP
+  omp_set_num_threads(t > 0 ? t : 1);
+#else
+  (void)t;
+#endif
+}
+
+int orc_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
 
 double orc_delta(int32_t n, const int32_t* rp, const double* w);
 double orc_delta2(int32_t n, const int32_t* rp, const double* w, const int32_t* rpt, const double* wt);

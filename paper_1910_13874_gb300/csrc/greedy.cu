@@ -255,14 +255,24 @@ __device__ __forceinline__ float ub_fixed(const T* __restrict__ col, const T* __
   return ub;
 }
 
+// The same sum for any L in one pass: a runs down from L while Q_{L-a} = z_0 + ... + z_{L-a}
+// grows, so every pair (a, b) with 1 <= a + b <= L is met once: y_a Q_{L-a} for a >= 1, and
+// y_0 (Q_L - z_0) at the end. Two table reads per step, every operation rounded up.
 template <typename T>
 __device__ float ub_any(const T* __restrict__ col, const T* __restrict__ zcol, int32_t n, int32_t L, float m0) {
-  auto yv = [&](int a) { return a == 0 ? m0 : to_f32_up(col[static_cast<size_t>(a) * n]); };
-  auto zv = [&](int b) { return b == 0 ? m0 : to_f32_up(zcol[static_cast<size_t>(b) * n]); };
+  float Q = m0;     // Q_0 = z_0
+  float R = 0.0f;   // z_1 + ... + z_{L-a}
   float ub = 0.0f;
-  for (int i = 1; i <= L; ++i)
-    for (int j = 0; j <= i; ++j) ub = __fmaf_ru(yv(i - j), zv(j), ub);
-  return ub;
+  for (int a = L; a >= 1; --a) {
+    if (a < L) {
+      const float zb = to_f32_up(__ldcs(zcol + static_cast<size_t>(L - a) * n));
+      Q = __fadd_ru(Q, zb);
+      R = __fadd_ru(R, zb);
+    }
+    ub = __fmaf_ru(to_f32_up(__ldcs(col + static_cast<size_t>(a) * n)), Q, ub);
+  }
+  R = __fadd_ru(R, to_f32_up(__ldcs(zcol + static_cast<size_t>(L) * n)));
+  return __fmaf_ru(m0, R, ub);
 }
 
 // Lemma-initialize bound + selection over vertices [0, n_scan) (the tables have n rows apart).

@@ -322,6 +322,16 @@ gedwalk_status gedwalk_batch_tuning(gedwalk_graph_t h, int32_t* cols, double* us
   return GEDWALK_OK;
 }
 
+gedwalk_status gedwalk_batch_set_width(gedwalk_graph_t h, int32_t cols) {
+  if (!h) return fail(GEDWALK_ERR_INVALID, "graph is NULL");
+  if (!(cols == 0 || cols == 8 || cols == 16 || cols == 32 || cols == 64))
+    return fail(GEDWALK_ERR_INVALID, "column-block width must be 0 (tune), 8, 16, 32 or 64");
+  Graph* g = gw::G(h);
+  std::lock_guard<std::mutex> lk(g->mu);
+  g->batch_cols = cols;
+  return GEDWALK_OK;
+}
+
 gedwalk_status gedwalk_score_batch(gedwalk_graph_t h, const int32_t* offsets, const int32_t* members, int32_t G,
                                    const gedwalk_params* params, double* scores, int32_t* L_used) {
   if (!h || (G > 0 && (!offsets || !scores))) return fail(GEDWALK_ERR_INVALID, "NULL argument");

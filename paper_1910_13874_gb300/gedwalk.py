@@ -38,6 +38,7 @@ EXPORTS = [
     "gedwalk_params_default", "gedwalk_set_allocator", "gedwalk_graph_upload", "gedwalk_graph_upload_weighted",
     "gedwalk_graph_info_weighted", "gedwalk_graph_free", "gedwalk_truncation_ex", "gedwalk_sigma_max",
     "gedwalk_graph_info", "gedwalk_truncation", "gedwalk_score", "gedwalk_score_batch", "gedwalk_batch_tuning",
+    "gedwalk_batch_set_width",
     "gedwalk_gains",
     "gedwalk_maximize", "gedwalk_maximize_stats", "gedwalk_maximize_lengths", "gedwalk_serve_create", "gedwalk_serve_submit",
     "gedwalk_serve_poll", "gedwalk_serve_stats", "gedwalk_serve_counters_read", "gedwalk_serve_destroy",
@@ -139,6 +140,7 @@ def load(path: Optional[str] = None, torch_allocator: bool = True):
             "gedwalk_score_batch": (ctypes.c_int, [vp, _i32p, _i32p, ctypes.c_int32, ctypes.POINTER(Params),
                                                    _f64p, _i32p]),
             "gedwalk_batch_tuning": (ctypes.c_int, [vp, _i32p, _f64p, ctypes.c_int32, _i32p, _i32p]),
+            "gedwalk_batch_set_width": (ctypes.c_int, [vp, ctypes.c_int32]),
             "gedwalk_gains": (ctypes.c_int, [vp, _i32p, ctypes.c_int32, ctypes.POINTER(Params), _f64p, _i32p]),
             "gedwalk_maximize": (ctypes.c_int, [vp, ctypes.c_int32, ctypes.POINTER(Params), _i32p, _f64p, _f64p,
                                                 _i32p, _i32p, ctypes.c_int32]),
@@ -359,6 +361,10 @@ class Graph:
         _check(load().gedwalk_batch_tuning(self._h, _ptr(cols, _i32p), _ptr(us, _f64p), cnt.value, ctypes.byref(cnt),
                                            ctypes.byref(chosen)))
         return cols[:cnt.value].tolist(), us[:cnt.value].tolist(), chosen.value
+
+    def batch_set_width(self, cols: int):
+        """Pins the batched-scoring column-block width (8, 16, 32, 64), or 0 to tune it again."""
+        _check(load().gedwalk_batch_set_width(self._h, int(cols)))
 
     def gains(self, S: Sequence[int], params: Optional[Params] = None, **kw):
         """(gains[n], L): exact truncated marginal gain of every vertex."""

@@ -886,3 +886,23 @@ def test_spectral_bound_on_regular_graph_is_sqrt_n_times_combinatorial():
     for l in range(1, 7):
         assert _rel(oracle.spectral_bound(g, alpha, Wa[l], 2.0), 3.0 * oracle.comb_bound(g, alpha, Wa[l])) < 1e-15
     assert oracle.select_L_spectral(g, 0.6, 1e-3, 2.0)[0] == -1  # alpha * sigma >= 1: no bound
+
+
+# ---------------------------------------------------------------- threads
+def test_threads_leave_every_result_bitwise_unchanged():
+    # The row loops may run on several threads; each row's sum keeps its order and every sum over
+    # vertices stays serial, so the results are bitwise those of one thread.
+    g = gg.rmat(15, 8, seed=9)  # more rows than the parallel threshold
+    alpha = oracle.default_alpha(g)
+    S = list(range(0, 3000, 37))
+    out = {}
+    for t in (1, 4):
+        oracle.set_threads(t)
+        out[t] = (oracle.score(g, S, alpha, 7, terms=True)[1].tolist(),
+                  oracle.score(g, S, alpha, 7, long_double=True),
+                  oracle.walk_totals(g, alpha, 6)[1].tolist(),
+                  oracle.upper_bounds(g, S, alpha, 6).tolist(),
+                  [oracle.gain(g, S, x, alpha, 6) for x in (1, 5, 4000)],
+                  [list(a) for a in oracle.greedy(g, 4, alpha, 6, "lazy")[:2]])
+    oracle.set_threads(1)
+    assert out[1] == out[4]
