@@ -540,7 +540,9 @@ def run_reference(args):
     g = make_graph(spec["graph"])
     w = oracle.normalized_weights(g) if spec.get("weighted") else None
     alpha = oracle.default_alpha(g, w)
-    L, _ = oracle.select_L(g, alpha, spec["eps"] / spec["k"], w=w)
+    oracle.set_threads(os.cpu_count() or 1)
+    L, _ = oracle.select_L(g, alpha, spec["eps"] / spec["k"], Lcap=64, w=w)  # L is 9 at these sizes
+    oracle.set_threads(1)
     samples = []
     cores = os.cpu_count() or 1
     for _ in range(args.warmup + args.steps):

@@ -262,8 +262,8 @@ struct ColAcc<float, N> {
 // The epilogue of the rows whose warp holds a candidate row (at most kCandSlots rows of the graph;
 // every lane of the warp calls it, shuffles inside). y holds alpha * s, zeroed on S.
 template <typename T, int C, int MODE, int CPL>
-__device__ __noinline__ void candidate_rows(const SweepArgs& a, const int* __restrict__ s_cand, int r, bool valid,
-                                            int c0, int base, T (&y)[CPL]) {
+__device__ __forceinline__ void candidate_rows(const SweepArgs& a, const int* __restrict__ s_cand, int r, bool valid,
+                                               int c0, int base, T (&y)[CPL]) {
   if constexpr (MODE == MODE_FUSED) {
     // column 0 is phi^miss under S; candidate column j >= 1 takes it at the candidate's row
     // (every S-avoiding walk ending at c_j visits c_j)
@@ -575,12 +575,16 @@ constexpr int kCandSlots = 16;
 // Resident CTAs per SM each instantiation is compiled for (its register limit). The gathers wait
 // on memory, and more resident warps hide more of that latency than a few spilled registers cost:
 // the 8-column lookahead sweep is held to 48 registers (five CTAs per SM), the 4-column candidate
-// batch to 64 (four), and the batched-scoring widths to what their C-wide row sums need (measured
-// on R-MAT scale 22 and on the Barabasi-Albert graph with n = 10^6).
+// batch to 64 (four), the one-step fused and two-state sweeps of 1-2 columns to 32 (eight) and of 4
+// to 40 (six), and the batched-scoring widths to what their C-wide row sums need (measured on R-MAT
+// scale 22 and on the Barabasi-Albert graph with n = 10^6).
 template <typename T, int C, int MODE>
 constexpr int min_ctas() {
+  if (sizeof(T) == 8) return 1;
   if (MODE == MODE_LOOK && C == 8) return 5;
   if (MODE == MODE_CAND && C == 4) return 4;
+  if ((MODE == MODE_FUSED || MODE == MODE_SCORE) && C <= 2) return 8;
+  if (MODE == MODE_FUSED && C == 4) return 6;
   if (MODE == MODE_PLAIN) return C <= 8 ? 5 : C <= 16 ? 3 : C <= 32 ? 2 : 1;
   return 1;
 }
