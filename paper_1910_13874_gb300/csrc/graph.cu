@@ -72,7 +72,13 @@ Profiler& prof() {
 }
 }  // namespace
 
-void count_launch() { prof().launches.fetch_add(1, std::memory_order_relaxed); }
+// While a thread captures a CUDA graph its launches are not executions: they are counted when the
+// graph runs.
+static thread_local bool t_capturing = false;
+void set_capturing(bool on) { t_capturing = on; }
+void count_launch() {
+  if (!t_capturing) prof().launches.fetch_add(1, std::memory_order_relaxed);
+}
 void count_launches(int n) { prof().launches.fetch_add(n, std::memory_order_relaxed); }
 
 void profile_add(double ms, double bytes, int key) {
@@ -173,20 +179,22 @@ void SweepGraph::reset() {
 int64_t Workspace::device_bytes() const {
   int64_t b = 0;
   for (const DevBuf* d : {&x0, &x1, &mtab, &ztab, &pvec, &partial, &counters, &slots, &parts, &mask, &stale, &sel,
-                          &small, &members})
+                          &small, &members, &ctl})
     b += static_cast<int64_t>(d->bytes);
   return b;
 }
 
 void Workspace::release_device() {
   for (SweepGraph& sg : graphs) sg.reset();
+  greedy_loop.reset();
   for (DevBuf* d : {&x0, &x1, &mtab, &ztab, &pvec, &partial, &counters, &slots, &parts, &mask, &stale, &sel, &small,
-                    &members})
+                    &members, &ctl})
     d->release();
 }
 
 Workspace::~Workspace() {
   for (SweepGraph& sg : graphs) sg.reset();
+  greedy_loop.reset();
   if (order_ev) cudaEventDestroy(order_ev);
   if (own_stream) cudaStreamDestroy(own_stream);
   if (pinned) cudaFreeHost(pinned);

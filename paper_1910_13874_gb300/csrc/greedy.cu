@@ -41,11 +41,21 @@ struct Stale {
 struct SelOut {  // device -> host after each selection pass
   float val[kTopK];
   int32_t id[kTopK];
-  int32_t zero_min_caller;  // smallest caller id among unevaluated vertices with bound exactly 0
-  int32_t sampled;          // stochastic greedy: sampled vertices outside S seen by the pass
-  int32_t pad[2];
-  double gains[16];          // exact gains of the last candidate batch
+  // the unevaluated vertex with bound exactly 0 and the smallest caller id, packed as
+  // (caller id << 32) | internal id (all ones: none)
+  unsigned long long zero_min;
+  int32_t sampled;  // stochastic greedy: sampled vertices outside S seen by the pass
+  int32_t pad;
+  double gains[16];  // exact gains of the last candidate batch
 };
+
+constexpr unsigned long long kNoZero = ~0ull;
+__host__ __device__ inline int32_t zero_caller(unsigned long long z) {
+  return z == kNoZero ? INT_MAX : static_cast<int32_t>(z >> 32);
+}
+__host__ __device__ inline int32_t zero_internal(unsigned long long z) {
+  return static_cast<int32_t>(z & 0xffffffffull);
+}
 
 __device__ __forceinline__ bool better(float a, int ia, float b, int ib) { return a > b || (a == b && ia < ib); }
 
@@ -283,8 +293,16 @@ __global__ void __launch_bounds__(kThreads) ub_select(const T* __restrict__ mtab
                                                      const uint32_t* __restrict__ mask,
                                                      const Stale* __restrict__ stale, int32_t step,
                                                      const int32_t* __restrict__ perm, float* __restrict__ sel_v,
-                                                     int* __restrict__ sel_id, int32_t* __restrict__ zero_min,
-                                                     const Sampling smp, int32_t* __restrict__ sampled) {
+                                                     int* __restrict__ sel_id,
+                                                     unsigned long long* __restrict__ zero_min, const Sampling smp,
+                                                     int32_t* __restrict__ sampled, const int32_t* level_ptr,
+                                                     int64_t level_stride, const int32_t* step_ptr) {
+  if (level_ptr) {  // the table (lookahead level) the device-resident loop chose for this step
+    const int64_t off = level_stride * __ldg(level_ptr);
+    mtab += off;
+    ztab += off;
+  }
+  if (step_ptr) step = __ldg(step_ptr);  // the device-resident loop's step
   int nsampled = 0;
   float v[kTopK];
   int id[kTopK];
@@ -321,7 +339,7 @@ __global__ void __launch_bounds__(kThreads) ub_select(const T* __restrict__ mtab
       if (!live[k]) continue;
       const int32_t x = base + k * stride;
       if (b[k] == 0.0f) {
-        atomicMin(zero_min, __ldg(perm + x));
+        atomicMin(zero_min, (static_cast<unsigned long long>(__ldg(perm + x)) << 32) | static_cast<uint32_t>(x));
         continue;
       }
       topk_push(v, id, b[k], x);
@@ -345,18 +363,20 @@ template <typename T>
 cudaError_t launch_ub_select(int nb, cudaStream_t s, const T* mtab, const T* ztab, int32_t L, int32_t n,
                              int32_t n_scan, const uint32_t* mask,
                              const Stale* stale, int32_t step, const int32_t* perm, float* sel_v, int* sel_id,
-                             int32_t* zero_min, const Sampling& smp, int32_t* sampled) {
+                             unsigned long long* zero_min, const Sampling& smp, int32_t* sampled,
+                             const int32_t* level_ptr = nullptr, int64_t level_stride = 0,
+                             const int32_t* step_ptr = nullptr) {
 #define GW_UB(LL)                                                                                          \
   case LL:                                                                                                 \
-    ub_select<T, LL><<<nb, kThreads, 0, s>>>(mtab, ztab, L, n, n_scan, mask, stale, step, perm, sel_v, sel_id, zero_min, smp, \
-                                             sampled);                                                     \
+    ub_select<T, LL><<<nb, kThreads, 0, s>>>(mtab, ztab, L, n, n_scan, mask, stale, step, perm, sel_v, sel_id, \
+                                             zero_min, smp, sampled, level_ptr, level_stride, step_ptr);   \
     break;
   switch (L) {
     GW_UB(1) GW_UB(2) GW_UB(3) GW_UB(4) GW_UB(5) GW_UB(6) GW_UB(7) GW_UB(8)
     GW_UB(9) GW_UB(10) GW_UB(11) GW_UB(12) GW_UB(13) GW_UB(14) GW_UB(15) GW_UB(16)
     default:
-      ub_select<T, 0><<<nb, kThreads, 0, s>>>(mtab, ztab, L, n, n_scan, mask, stale, step, perm, sel_v, sel_id, zero_min, smp,
-                                              sampled);
+      ub_select<T, 0><<<nb, kThreads, 0, s>>>(mtab, ztab, L, n, n_scan, mask, stale, step, perm, sel_v, sel_id,
+                                              zero_min, smp, sampled, level_ptr, level_stride, step_ptr);
   }
 #undef GW_UB
   return cudaGetLastError();
@@ -387,7 +407,7 @@ __global__ void __launch_bounds__(kMergeThreads) select_merge(const float* __res
 
 // Resets the per-pass counters of a selection pass.
 __global__ void reset_selection(SelOut* out) {
-  out->zero_min_caller = INT_MAX;
+  out->zero_min = kNoZero;
   out->sampled = 0;
 }
 
@@ -423,7 +443,23 @@ struct GreedyCtx {
   SelOut* h_out;
   int64_t sweeps = 0;
   size_t tab_off = 0;  // elements: the phi^miss table in use (lookahead level) within ws.mtab
+  // device-resident loop: candidate rows read the table level the device chose (nullptr: none)
+  const int32_t* level_ptr = nullptr;
+  int64_t level_stride = 0;
+  // device-resident loop: a kernel stamps the device clock around the sweeps (stamp >= 0)
+  void* stamp_ctl = nullptr;
+  int stamp_end = 0;
 };
+
+// Stamps the device clock (%globaltimer, nanoseconds) into the controller: kind 0 opens an
+// interval, kind 1 adds it to the lookahead runs' time, kind 2 to the candidate batches'.
+__global__ void ctl_stamp(unsigned long long* __restrict__ t, int kind) {
+  if (threadIdx.x != 0) return;
+  unsigned long long now;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+  if (kind == 0) t[0] = now;
+  else t[kind] += now - t[0];
+}
 
 // Issues init + L sweeps + column-sum reduction on c.s. ev (optional): two external events
 // around each sweep (graph capture).
@@ -471,11 +507,21 @@ gedwalk_status issue_sweeps(GreedyCtx& c, int mode, int cols, bool profile, cons
     else if (mode == MODE_LOOK) a.Mout = tab.as<char>() + static_cast<size_t>(t) * g.n * c.es;
     else a.Min = row;
     a.mout_stride = look_stride;
+    a.level_ptr = c.level_ptr;
+    a.level_stride = c.level_stride;
     // external events bracket the whole run of sweeps (event nodes between kernel nodes cost
     // a few microseconds each)
     if (ev && t == 1) GW_CUDA(cudaEventRecordWithFlags((*ev)[0], c.s, cudaEventRecordExternal));
+    if (c.stamp_ctl && t == 1) {
+      ctl_stamp<<<1, 32, 0, c.s>>>(static_cast<unsigned long long*>(c.stamp_ctl), 0);
+      GW_KCHECK();
+    }
     GW_TRY(launch_sweep(mode, fp64, cols, a, c.s, profile));
     if (ev && t == c.L) GW_CUDA(cudaEventRecordWithFlags((*ev)[1], c.s, cudaEventRecordExternal));
+    if (c.stamp_ctl && t == c.L) {
+      ctl_stamp<<<1, 32, 0, c.s>>>(static_cast<unsigned long long*>(c.stamp_ctl), c.stamp_end);
+      GW_KCHECK();
+    }
     std::swap(cur, nxt);
   }
   const int nsum = sweep_sums(mode, cols);
@@ -539,7 +585,9 @@ gedwalk_status run_sweeps(GreedyCtx& c, int mode, int cols, const std::vector<in
     sg.ev.assign(2, nullptr);
     for (cudaEvent_t& e : sg.ev) GW_CUDA(cudaEventCreate(&e));
     GW_CUDA(cudaStreamBeginCapture(c.s, cudaStreamCaptureModeThreadLocal));
+    set_capturing(true);
     const gedwalk_status st = issue_sweeps(c, mode, cols, false, &sg.ev, rev);
+    set_capturing(false);
     cudaGraph_t graph = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(c.s, &graph);
     if (st != GEDWALK_OK || ce != cudaSuccess || !graph) {
@@ -598,6 +646,266 @@ gedwalk_status greedy_stream(Workspace& ws, cudaStream_t caller, cudaStream_t* o
   return GEDWALK_OK;
 }
 
+// ---------------------------------------------------------------- device-resident greedy loop
+// The plain greedy with lookahead runs as one CUDA graph: an outer WHILE node over the k steps; in
+// each, a controller kernel either takes the next lookahead level (its table and its candidate's
+// exact gain are already there) or starts a new run (IF node: the L lookahead sweeps), then an
+// inner WHILE node repeats bound pass -> merge -> certification, with a candidate batch (IF node)
+// whenever the best exact value does not beat every unevaluated bound. The decisions the host loop
+// takes (certification, the next candidates, the speculative guesses, the lookahead level) are
+// taken by single-thread kernels on the same data, in the same order and with the same ties, so
+// the picks and gains are those of the host loop. A step that needs more than `max_batches`
+// candidate batches stops the loop with an error flag instead of running on.
+constexpr int kMaxEval = 64;  // exact values one step keeps (the largest, if more)
+
+struct DevCtl {
+  int32_t step, k, levels, L;
+  int32_t look_lvl, tab_level;  // the level the next step may take; the table this step reads
+  int32_t run_look, looping, run_cand, n_last;
+  int32_t first_batch, guessed, e_n, spec_n;
+  int32_t iso_next, batches_step, err, cols_cand;
+  int32_t look_c[8];
+  int32_t spec_v[8];
+  int32_t e_v[kMaxEval];
+  double look_g[8];
+  double spec_g[8];
+  double e_g[kMaxEval];
+  long long evals, batches, spec_miss, runs, cand_batches, iters;
+  unsigned long long t[3];  // device clock: interval start, lookahead-run sweeps, candidate-batch sweeps
+};
+
+__device__ __forceinline__ bool dev_in(const uint32_t* mask, int32_t v) { return (mask[v >> 5] >> (v & 31)) & 1u; }
+
+// Opens a step: the next lookahead level, or a new run whose guesses are the best remaining values
+// (at the first step without any, the highest-degree vertices outside S).
+__global__ void ctl_begin(DevCtl* __restrict__ c, Stale* __restrict__ stale, const uint32_t* __restrict__ mask,
+                          int32_t n, int32_t* __restrict__ cand, cudaGraphConditionalHandle h_run,
+                          cudaGraphConditionalHandle h_loop) {
+  if (threadIdx.x != 0) return;
+  c->e_n = 0;
+  c->first_batch = 1;
+  c->guessed = 0;
+  c->batches_step = 0;
+  c->n_last = 0;
+  c->looping = 1;
+  const int lvl = c->look_lvl;
+  if (lvl > 0 && lvl < c->levels && c->look_c[lvl] >= 0) {
+    const int32_t v = c->look_c[lvl];
+    c->tab_level = lvl;
+    Stale st;
+    st.ub = __double2float_ru(c->look_g[lvl]);
+    st.step = c->step;
+    stale[v] = st;
+    c->e_v[0] = v;
+    c->e_g[0] = c->look_g[lvl];
+    c->e_n = 1;
+    c->guessed = 1;
+    c->run_look = 0;
+  } else {
+    int m = 0;
+    for (int j = 0; j < c->spec_n && m < c->levels; ++j) cand[m++] = c->spec_v[j];
+    if (m == 0 && c->step == 0)
+      for (int32_t v = 0; v < n && m < c->levels; ++v)
+        if (!dev_in(mask, v)) cand[m++] = v;
+    for (int j = m; j < 16; ++j) cand[j] = -1;
+    for (int j = 0; j < c->levels; ++j) c->look_c[j] = cand[j];
+    c->look_lvl = 0;
+    c->tab_level = 0;
+    c->guessed = m > 0;
+    c->n_last = m > 0 ? 1 : 0;  // level 0's guess has its exact gain once the run is done
+    c->evals += m;
+    c->batches += m > 0;
+    c->runs += 1;
+    c->run_look = 1;
+  }
+  cudaGraphSetConditional(h_run, c->run_look ? 1u : 0u);
+  cudaGraphSetConditional(h_loop, 1u);
+}
+
+// After a run: the exact gains of every level's guess (each under S + the earlier guesses).
+__global__ void ctl_after_run(DevCtl* __restrict__ c, const double* __restrict__ gains) {
+  if (threadIdx.x < c->levels) c->look_g[threadIdx.x] = gains[threadIdx.x];
+}
+
+// Records the exact gains of the last evaluated candidates (as the stale bounds of this step and
+// in the step's list of exact values, which keeps the kMaxEval largest).
+__global__ void ctl_record(DevCtl* __restrict__ c, Stale* __restrict__ stale, const int32_t* __restrict__ cand,
+                           const double* __restrict__ gains, const int32_t* __restrict__ perm) {
+  if (threadIdx.x != 0) return;
+  for (int j = 0; j < c->n_last; ++j) {
+    const int32_t v = cand[j];
+    if (v < 0) continue;
+    Stale st;
+    st.ub = __double2float_ru(gains[j]);
+    st.step = c->step;
+    stale[v] = st;
+    if (c->e_n < kMaxEval) {
+      c->e_v[c->e_n] = v;
+      c->e_g[c->e_n] = gains[j];
+      ++c->e_n;
+    } else {  // replace the smallest exact value (never the best: certification needs only that)
+      int w = 0;
+      for (int i = 1; i < kMaxEval; ++i)
+        if (c->e_g[i] < c->e_g[w] || (c->e_g[i] == c->e_g[w] && perm[c->e_v[i]] > perm[c->e_v[w]])) w = i;
+      if (gains[j] > c->e_g[w]) {
+        c->e_v[w] = v;
+        c->e_g[w] = gains[j];
+      }
+    }
+  }
+  c->n_last = 0;
+}
+
+__device__ __forceinline__ bool cand_first(double ga, int32_t ca, double gb, int32_t cb) {
+  return ga > gb || (ga == gb && ca < cb);
+}
+
+// Certification after a bound pass: the best exact value wins once it beats every unevaluated
+// bound (inflated by tol); then the step's outputs, the vertex joins S, the next step's guesses and
+// lookahead level are set. Otherwise the best-bounded unevaluated vertices become a candidate batch.
+__global__ void ctl_certify(DevCtl* __restrict__ c, const SelOut* __restrict__ sel, uint32_t* __restrict__ mask,
+                            const int32_t* __restrict__ perm, int32_t n, int32_t* __restrict__ cand,
+                            int32_t* __restrict__ out_group, double* __restrict__ out_gains, double tol,
+                            int32_t max_batches, cudaGraphConditionalHandle h_loop,
+                            cudaGraphConditionalHandle h_cand) {
+  if (threadIdx.x != 0) return;
+  ++c->iters;
+  // the zero-gain candidate: the bound pass's, or the smallest isolated row outside S
+  unsigned long long z = sel->zero_min;
+  while (c->iso_next < n && dev_in(mask, c->iso_next)) ++c->iso_next;
+  if (c->iso_next < n) {
+    const unsigned long long iso =
+        (static_cast<unsigned long long>(perm[c->iso_next]) << 32) | static_cast<uint32_t>(c->iso_next);
+    if (iso < z) z = iso;
+  }
+  // the best exact value (larger gain first, then the lower caller id)
+  int32_t bv = -1, bc = INT_MAX;
+  double bg = -1.0;
+  for (int j = 0; j < c->e_n; ++j) {
+    const int32_t cc = perm[c->e_v[j]];
+    if (bv < 0 || cand_first(c->e_g[j], cc, bg, bc)) {
+      bv = c->e_v[j];
+      bc = cc;
+      bg = c->e_g[j];
+    }
+  }
+  if (z != kNoZero && (bv < 0 || cand_first(0.0, zero_caller(z), bg, bc))) {
+    bv = zero_internal(z);
+    bc = zero_caller(z);
+    bg = 0.0;
+  }
+  const bool top_empty = sel->id[0] == INT_MAX;
+  const double ub0 = top_empty ? -1.0 : static_cast<double>(sel->val[0]) * (1.0 + tol);
+  const bool certified = top_empty || (bv >= 0 && ub0 < bg);
+  if (certified) {
+    if (bv < 0) {  // no vertex left to add
+      c->err = 2;
+      c->looping = 0;
+      c->run_cand = 0;
+    } else {
+      out_group[c->step] = bc;
+      out_gains[c->step] = bg;
+      mask[bv >> 5] |= 1u << (bv & 31);
+      // the next run's guesses: the best remaining values, exact or bounds, positive only
+      int32_t pv[kMaxEval + kTopK];
+      double pg[kMaxEval + kTopK];
+      int np = 0;
+      for (int j = 0; j < c->e_n; ++j)
+        if (c->e_v[j] != bv) {
+          pv[np] = c->e_v[j];
+          pg[np++] = c->e_g[j];
+        }
+      for (int j = 0; j < kTopK; ++j)
+        if (sel->id[j] != INT_MAX && sel->id[j] != bv) {
+          pv[np] = sel->id[j];
+          pg[np++] = static_cast<double>(sel->val[j]);
+        }
+      int ns = 0;
+      while (ns < c->levels) {
+        int w = -1;
+        for (int j = 0; j < np; ++j) {
+          if (pv[j] < 0 || !(pg[j] > 0.0)) continue;
+          if (w < 0 || cand_first(pg[j], perm[pv[j]], pg[w], perm[pv[w]])) w = j;
+        }
+        if (w < 0) break;
+        c->spec_v[ns] = pv[w];
+        c->spec_g[ns++] = pg[w];
+        pv[w] = -1;
+      }
+      c->spec_n = ns;
+      const int lvl = c->look_lvl;
+      if (lvl >= 0 && bv == c->look_c[lvl] && lvl + 1 < c->levels && c->look_c[lvl + 1] >= 0) c->look_lvl = lvl + 1;
+      else c->look_lvl = -1;
+      ++c->step;
+      c->looping = 0;
+      c->run_cand = 0;
+    }
+  } else {
+    if (c->first_batch && c->guessed) ++c->spec_miss;
+    c->first_batch = 0;
+    int m = 0;
+    for (int j = 0; j < kTopK && m < c->cols_cand; ++j)
+      if (sel->id[j] != INT_MAX) cand[m++] = sel->id[j];
+    for (int j = m; j < 16; ++j) cand[j] = -1;
+    c->n_last = m;
+    c->evals += m;
+    c->batches += 1;
+    c->cand_batches += 1;
+    if (++c->batches_step > max_batches) {
+      c->err = 1;
+      c->looping = 0;
+      c->run_cand = 0;
+    } else {
+      c->looping = 1;
+      c->run_cand = 1;
+    }
+  }
+  cudaGraphSetConditional(h_loop, c->looping ? 1u : 0u);
+  cudaGraphSetConditional(h_cand, c->run_cand ? 1u : 0u);
+}
+
+__global__ void ctl_end(const DevCtl* __restrict__ c, cudaGraphConditionalHandle h_step) {
+  if (threadIdx.x == 0) cudaGraphSetConditional(h_step, (c->step < c->k && c->err == 0) ? 1u : 0u);
+}
+
+// Adds a conditional node (IF or WHILE, one body) at the current point of a capture on s.
+gedwalk_status add_conditional(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                               cudaGraph_t* body) {
+  cudaStreamCaptureStatus st;
+  cudaGraph_t graph = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  GW_CUDA(cudaStreamGetCaptureInfo(s, &st, nullptr, &graph, &deps, nullptr, &nd));
+  if (st != cudaStreamCaptureStatusActive) return fail(GEDWALK_ERR_DEVICE, "stream is not capturing");
+  cudaGraphNodeParams p{};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = h;
+  p.conditional.type = type;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  GW_CUDA(cudaGraphAddNode(&node, graph, deps, nullptr, nd, &p));
+  GW_CUDA(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  *body = p.conditional.phGraph_out[0];
+  return GEDWALK_OK;
+}
+
+// Captures `fill` into `graph` on s (BeginCaptureToGraph); the capture ends whatever fill returns.
+template <class F>
+gedwalk_status capture_into(cudaStream_t s, cudaGraph_t graph, F&& fill) {
+  GW_CUDA(cudaStreamBeginCaptureToGraph(s, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  set_capturing(true);
+  const gedwalk_status st = fill();
+  set_capturing(false);
+  cudaGraph_t out = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(s, &out);
+  if (st != GEDWALK_OK) {
+    cudaGetLastError();
+    return st;
+  }
+  if (ce != cudaSuccess) return fail(GEDWALK_ERR_DEVICE, "capture of the greedy loop failed: %s", cudaGetErrorString(ce));
+  return GEDWALK_OK;
+}
+
 }  // namespace
 
 gedwalk_status greedy_shape(const Graph& g, const Resolved& r, int32_t flags, GreedyShape* out) {
@@ -639,7 +947,25 @@ gedwalk_status greedy_shape(const Graph& g, const Resolved& r, int32_t flags, Gr
   return GEDWALK_OK;
 }
 
-int64_t maximize_footprint(const Graph& g, const Resolved& r, int32_t flags) {
+namespace {
+// The plain greedy with lookahead runs its k steps as one CUDA graph (device-resident loop).
+bool uses_device_loop(const Graph& g, const GreedyShape& sh, int32_t flags, int32_t k) {
+  return sh.levels > 1 && (flags & (GEDWALK_GAINS_ALL | GEDWALK_STOCHASTIC | GEDWALK_ADAPTIVE_L)) == 0 && !g.directed &&
+         k > 0 && g.plan.num_units > 0;
+}
+// Its controller block: the state, then the group and the gains of up to kcap steps.
+int32_t loop_kcap(int32_t k) {
+  int32_t kcap = 64;
+  while (kcap < k) kcap *= 2;
+  return kcap;
+}
+size_t loop_ctl_bytes(int32_t k) {
+  return (sizeof(DevCtl) + 255) / 256 * 256 + static_cast<size_t>(loop_kcap(k)) * (sizeof(double) + sizeof(int32_t)) +
+         256;
+}
+}  // namespace
+
+int64_t maximize_footprint(const Graph& g, const Resolved& r, int32_t flags, int32_t k) {
   GreedyShape sh{};
   if (greedy_shape(g, r, flags, &sh) != GEDWALK_OK) return 0;
   const int64_t n = g.n, es = r.fp64 ? 8 : 4;
@@ -654,8 +980,195 @@ int64_t maximize_footprint(const Graph& g, const Resolved& r, int32_t flags) {
   b += (n + 31) / 32 * 4;                                           // S bitmask
   b += n * static_cast<int64_t>(sizeof(Stale)) + static_cast<int64_t>(kSelBlocks) * kTopK * 8;
   b += static_cast<int64_t>(sizeof(SelOut)) + 16 * 4 + 16 * 8 + 256;
+  if (uses_device_loop(g, sh, flags, k)) b += static_cast<int64_t>(loop_ctl_bytes(k));
   return b;
 }
+
+namespace {
+
+uint64_t mix_all(std::initializer_list<uint64_t> vs) {
+  uint64_t key = 0;
+  for (uint64_t v : vs) key ^= v + 0x9e3779b97f4a7c15ULL + (key << 6) + (key >> 2);
+  return key;
+}
+
+// Runs the k steps of the plain greedy with lookahead as one CUDA graph launch (the loop's graph is
+// built once per configuration of the workspace) and reads back the group and the gains.
+gedwalk_status run_device_loop(GreedyCtx& c, int32_t k, int levels, int cols_cand, int cols_max, size_t tab_elems,
+                               int nb_sel, int32_t n_scan, double tol, Stale* stale, float* sel_v, int* sel_id,
+                               int32_t* group, double* gains, bool* launched) {
+  *launched = false;
+  Graph& g = c.g;
+  Workspace& ws = c.ws;
+  const cudaStream_t s = c.s;
+  const bool fp64 = c.r.fp64;
+  const int32_t L = c.L;
+  // controller state, then the outputs for up to kcap steps
+  const int32_t kcap = loop_kcap(k);
+  const size_t ctl_bytes = (sizeof(DevCtl) + 255) / 256 * 256;
+  GW_TRY(ws.ctl.ensure(loop_ctl_bytes(k), s));
+  char* base = ws.ctl.as<char>();
+  DevCtl* dctl = reinterpret_cast<DevCtl*>(base);
+  double* d_ogains = reinterpret_cast<double*>(base + ctl_bytes);
+  int32_t* d_ogroup = reinterpret_cast<int32_t*>(d_ogains + kcap);
+  const int32_t* d_level = reinterpret_cast<const int32_t*>(base + offsetof(DevCtl, tab_level));
+  const int32_t* d_step = reinterpret_cast<const int32_t*>(base + offsetof(DevCtl, step));
+  void* d_stamp = base + offsetof(DevCtl, t);
+  // buffers the captured sweeps use, sized before the capture
+  const size_t es = fp64 ? 8 : 4;
+  GW_TRY(ws.x0.ensure(static_cast<size_t>(g.n) * cols_max * es, s));
+  GW_TRY(ws.x1.ensure(static_cast<size_t>(g.n) * cols_max * es, s));
+  GW_TRY(ensure_sweep_scratch(g, ws, cols_max, fp64, s));
+  GW_TRY(configure_sweep(MODE_LOOK, fp64, 2 * levels));
+  GW_TRY(configure_sweep(MODE_CAND, fp64, cols_cand));
+  DevCtl h{};
+  h.k = k;
+  h.levels = levels;
+  h.L = L;
+  h.look_lvl = -1;
+  h.iso_next = n_scan;
+  h.cols_cand = cols_cand;
+  for (int j = 0; j < 8; ++j) h.look_c[j] = -1;
+  GW_CUDA(cudaMemcpyAsync(dctl, &h, sizeof h, cudaMemcpyHostToDevice, s));
+  const int32_t max_batches = n_scan / std::max(cols_cand, 1) + 64;
+  uint64_t abits;
+  memcpy(&abits, &c.r.alpha, 8);
+  uint64_t tbits;
+  memcpy(&tbits, &tol, 8);
+  const uint64_t key = mix_all(
+      {uint64_t(levels), uint64_t(cols_cand), uint64_t(fp64), uint64_t(L), uint64_t(g.n), uint64_t(kcap),
+       uint64_t(nb_sel), uint64_t(n_scan), abits, tbits, reinterpret_cast<uint64_t>(&g), reinterpret_cast<uint64_t>(s),
+       reinterpret_cast<uint64_t>(ws.x0.p), reinterpret_cast<uint64_t>(ws.x1.p), reinterpret_cast<uint64_t>(ws.mtab.p),
+       reinterpret_cast<uint64_t>(ws.slots.p), reinterpret_cast<uint64_t>(ws.parts.p),
+       reinterpret_cast<uint64_t>(ws.partial.p), reinterpret_cast<uint64_t>(ws.counters.p),
+       reinterpret_cast<uint64_t>(ws.mask.p), reinterpret_cast<uint64_t>(ws.stale.p),
+       reinterpret_cast<uint64_t>(ws.sel.p), reinterpret_cast<uint64_t>(ws.small.p),
+       reinterpret_cast<uint64_t>(ws.ctl.p)});
+  SweepGraph& sg = ws.greedy_loop;
+  if (sg.key != key || !sg.exec) {
+    sg.reset();
+    cudaGraph_t root = nullptr;
+    GW_CUDA(cudaGraphCreate(&root, 0));
+    struct Owner {
+      cudaGraph_t g;
+      ~Owner() {
+        if (g) cudaGraphDestroy(g);
+      }
+    } owner{root};
+    cudaGraphConditionalHandle h_step, h_run, h_loop, h_cand;
+    GW_CUDA(cudaGraphConditionalHandleCreate(&h_step, root, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams p{};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h_step;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t n_step;
+    GW_CUDA(cudaGraphAddNode(&n_step, root, nullptr, nullptr, 0, &p));
+    cudaGraph_t body_step = p.conditional.phGraph_out[0];
+    GW_CUDA(cudaGraphConditionalHandleCreate(&h_run, body_step, 0, 0));
+    GW_CUDA(cudaGraphConditionalHandleCreate(&h_loop, body_step, 0, 0));
+    cudaGraph_t body_run = nullptr, body_loop = nullptr, body_cand = nullptr;
+    uint32_t* mask = ws.mask.as<uint32_t>();
+    const int32_t* perm = g.perm_d.as<int32_t>();
+    // step: open (level or run), the run, the certification loop, close
+    GW_TRY(capture_into(s, body_step, [&]() -> gedwalk_status {
+      ctl_begin<<<1, 32, 0, s>>>(dctl, stale, mask, g.n, c.d_cand, h_run, h_loop);
+      GW_CUDA(cudaGetLastError());
+      GW_TRY(add_conditional(s, h_run, cudaGraphCondTypeIf, &body_run));
+      GW_TRY(add_conditional(s, h_loop, cudaGraphCondTypeWhile, &body_loop));
+      ctl_end<<<1, 32, 0, s>>>(dctl, h_step);
+      GW_CUDA(cudaGetLastError());
+      return GEDWALK_OK;
+    }));
+    // the lookahead run: init, L sweeps (device-clock stamps around them), column sums, the gains
+    GW_TRY(capture_into(s, body_run, [&]() -> gedwalk_status {
+      c.tab_off = 0;
+      c.stamp_ctl = d_stamp;
+      c.stamp_end = 1;
+      const gedwalk_status st = issue_sweeps(c, MODE_LOOK, 2 * levels, false, nullptr, false);
+      c.stamp_ctl = nullptr;
+      GW_TRY(st);
+      ctl_after_run<<<1, 32, 0, s>>>(dctl, c.d_gains);
+      GW_CUDA(cudaGetLastError());
+      return GEDWALK_OK;
+    }));
+    // one certification round: record the last gains, bound pass, merge, certify, maybe a batch
+    GW_CUDA(cudaGraphConditionalHandleCreate(&h_cand, body_loop, 0, 0));
+    GW_TRY(capture_into(s, body_loop, [&]() -> gedwalk_status {
+      ctl_record<<<1, 32, 0, s>>>(dctl, stale, c.d_cand, c.d_gains, perm);
+      GW_CUDA(cudaGetLastError());
+      reset_selection<<<1, 1, 0, s>>>(c.d_out);
+      GW_CUDA(cudaGetLastError());
+      const Sampling all{~0ull, 0, 0};
+      if (fp64)
+        GW_CUDA(launch_ub_select<double>(nb_sel, s, ws.mtab.as<double>(), ws.mtab.as<double>(), L, g.n, n_scan, mask,
+                                         stale, 0, perm, sel_v, sel_id, &c.d_out->zero_min, all, &c.d_out->sampled,
+                                         d_level, static_cast<int64_t>(tab_elems), d_step));
+      else
+        GW_CUDA(launch_ub_select<float>(nb_sel, s, ws.mtab.as<float>(), ws.mtab.as<float>(), L, g.n, n_scan, mask,
+                                        stale, 0, perm, sel_v, sel_id, &c.d_out->zero_min, all, &c.d_out->sampled,
+                                        d_level, static_cast<int64_t>(tab_elems), d_step));
+      select_merge<<<1, kMergeThreads, 0, s>>>(sel_v, sel_id, nb_sel * kTopK, c.d_out);
+      GW_CUDA(cudaGetLastError());
+      ctl_certify<<<1, 32, 0, s>>>(dctl, c.d_out, mask, perm, g.n, c.d_cand, d_ogroup, d_ogains, tol, max_batches,
+                                   h_loop, h_cand);
+      GW_CUDA(cudaGetLastError());
+      return add_conditional(s, h_cand, cudaGraphCondTypeIf, &body_cand);
+    }));
+    // the candidate batch: candidate rows read the table of the step's level
+    GW_TRY(capture_into(s, body_cand, [&]() -> gedwalk_status {
+      c.tab_off = 0;
+      c.level_ptr = d_level;
+      c.level_stride = static_cast<int64_t>(tab_elems);
+      c.stamp_ctl = d_stamp;
+      c.stamp_end = 2;
+      const gedwalk_status st = issue_sweeps(c, MODE_CAND, cols_cand, false, nullptr, false);
+      c.stamp_ctl = nullptr;
+      c.level_ptr = nullptr;
+      c.level_stride = 0;
+      return st;
+    }));
+    GW_CUDA(cudaGraphInstantiate(&sg.exec, root, 0));
+    sg.key = key;
+  }
+  *launched = true;
+  GW_CUDA(cudaGraphLaunch(sg.exec, s));
+  DevCtl out{};
+  std::vector<double> og(k);
+  std::vector<int32_t> ogr(k);
+  GW_CUDA(cudaMemcpyAsync(&out, dctl, sizeof out, cudaMemcpyDeviceToHost, s));
+  GW_CUDA(cudaMemcpyAsync(og.data(), d_ogains, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+  GW_CUDA(cudaMemcpyAsync(ogr.data(), d_ogroup, sizeof(int32_t) * k, cudaMemcpyDeviceToHost, s));
+  GW_CUDA(cudaStreamSynchronize(s));
+  if (out.err == 2) return fail(GEDWALK_ERR_INVALID, "no vertex left to add");
+  if (out.err != 0 || out.step != k)
+    return fail(GEDWALK_ERR_DEVICE, "the greedy loop stopped at step %d of %d (certification exceeded %d batches)",
+                out.step, k, max_batches);
+  for (int32_t j = 0; j < k; ++j) {
+    group[j] = ogr[j];
+    if (gains) gains[j] = og[j];
+  }
+  ws.st_evals = out.evals;
+  ws.st_batches = out.batches;
+  ws.st_spec_miss = out.spec_miss;
+  ws.st_sweeps = (out.runs + out.cand_batches) * L;
+  ws.st_ell.assign(k, L);
+  // launches the graph ran: per step open/close, per run init + L sweeps + 2 stamps + 2 reduce +
+  // after_run, per certification round 5 kernels, per batch init + L sweeps + 2 stamps + 2 reduce
+  count_launches(static_cast<int>(2 * k + out.runs * (L + 6) + out.iters * 5 + out.cand_batches * (L + 5)));
+  if (profiling()) {  // the sweeps' device time, from the device-clock stamps around each run / batch
+    const double b_look = sweep_bytes(MODE_LOOK, fp64, 2 * levels, g.n, g.nnz, g.weighted);
+    const double b_cand = sweep_bytes(MODE_CAND, fp64, cols_cand, g.n, g.nnz, g.weighted);
+    const int64_t n_look = out.runs * L, n_cand = out.cand_batches * L;
+    for (int64_t i = 0; i < n_look; ++i)
+      profile_add(static_cast<double>(out.t[1]) / 1e6 / n_look, b_look, (MODE_LOOK * 1000 + 2 * levels) * 2 + fp64);
+    for (int64_t i = 0; i < n_cand; ++i)
+      profile_add(static_cast<double>(out.t[2]) / 1e6 / n_cand, b_cand, (MODE_CAND * 1000 + cols_cand) * 2 + fp64);
+  }
+  return GEDWALK_OK;
+}
+
+}  // namespace
 
 namespace {
 // Waits for a stream when a call leaves early with an error, so that nothing it launched still
@@ -781,12 +1294,12 @@ gedwalk_status maximize_impl(Graph& g, Workspace& ws, int32_t k, const Resolved&
       GW_CUDA(launch_ub_select<double>(nb_sel, s, ws.mtab.as<double>() + c.tab_off,
                                        g.directed ? ws.ztab.as<double>() : ws.mtab.as<double>() + c.tab_off, c.L, g.n,
                                        n_scan, ws.mask.as<uint32_t>(), stale, st, g.perm_d.as<int32_t>(), sel_v,
-                                       sel_id, &c.d_out->zero_min_caller, smp, &c.d_out->sampled));
+                                       sel_id, &c.d_out->zero_min, smp, &c.d_out->sampled));
     else
       GW_CUDA(launch_ub_select<float>(nb_sel, s, ws.mtab.as<float>() + c.tab_off,
                                       g.directed ? ws.ztab.as<float>() : ws.mtab.as<float>() + c.tab_off, c.L, g.n,
                                       n_scan, ws.mask.as<uint32_t>(), stale, st, g.perm_d.as<int32_t>(), sel_v,
-                                      sel_id, &c.d_out->zero_min_caller, smp, &c.d_out->sampled));
+                                      sel_id, &c.d_out->zero_min, smp, &c.d_out->sampled));
     count_launch();
     select_merge<<<1, kMergeThreads, 0, s>>>(sel_v, sel_id, nb_sel * kTopK, c.d_out);
     GW_KCHECK();
@@ -794,9 +1307,40 @@ gedwalk_status maximize_impl(Graph& g, Workspace& ws, int32_t k, const Resolved&
     GW_CUDA(cudaStreamSynchronize(s));
     read_graph_timing(ws);
     while (iso_next < g.n && inS[iso_next]) ++iso_next;
-    if (iso_next < g.n) c.h_out->zero_min_caller = std::min(c.h_out->zero_min_caller, g.perm[iso_next]);
+    if (iso_next < g.n) {
+      const unsigned long long iso =
+          (static_cast<unsigned long long>(g.perm[iso_next]) << 32) | static_cast<uint32_t>(iso_next);
+      c.h_out->zero_min = std::min(c.h_out->zero_min, iso);
+    }
     return GEDWALK_OK;
   };
+
+  // The plain greedy with lookahead runs as one CUDA graph (device-resident loop); the others keep
+  // the host loop below.
+  bool device_loop = uses_device_loop(g, shape, flags, k);
+  if (device_loop) {
+    bool launched = false;
+    const gedwalk_status st = run_device_loop(c, k, levels, cols_cand, shape.cols_max, tab_elems, nb_sel, n_scan, tol,
+                                              stale, sel_v, sel_id, group, gains, &launched);
+    if (st != GEDWALK_OK && launched) return st;
+    if (st != GEDWALK_OK) {  // the loop's graph could not be built: the host loop below runs instead
+      cudaGetLastError();
+      ws.greedy_loop.reset();
+      device_loop = false;
+    }
+  }
+  if (device_loop) {
+    std::vector<int32_t> S_dev = init_int;
+    for (int32_t j = 0; j < k; ++j) S_dev.push_back(g.inv[group[j]]);
+    if (score) {
+      double v = 0;
+      GW_TRY(score_one(g, ws, S_dev, r, &v));
+      *score = v;
+    }
+    GW_CUDA(cudaStreamSynchronize(s));
+    guard.ok = true;
+    return GEDWALK_OK;
+  }
 
   for (int32_t step = 0; step < k; ++step) {
     std::vector<Cand> E;  // evaluated with the current S
@@ -896,8 +1440,8 @@ gedwalk_status maximize_impl(Graph& g, Workspace& ws, int32_t k, const Resolved&
           for (int j = 0; j < kTopK; ++j)
             if (c.h_out->id[j] != INT_MAX) top.push_back(c.h_out->id[j]);
           X = E;
-          const int32_t zmin = c.h_out->zero_min_caller;
-          if (zmin != INT_MAX) X.push_back(Cand{0.0, g.inv[zmin], zmin});
+          const unsigned long long zmin = c.h_out->zero_min;
+          if (zmin != kNoZero) X.push_back(Cand{0.0, zero_internal(zmin), zero_caller(zmin)});
           std::sort(X.begin(), X.end(), cand_before);
           const double ub0 = top.empty() ? -1.0 : static_cast<double>(c.h_out->val[0]) * (1.0 + tol);
           const bool certified =

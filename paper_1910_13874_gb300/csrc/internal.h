@@ -156,6 +156,8 @@ struct Workspace {
   static constexpr int kGraphCache = 16;
   SweepGraph graphs[kGraphCache];
   uint64_t graph_clock = 0;
+  SweepGraph greedy_loop;  // the device-resident greedy loop of the last configuration
+  DevBuf ctl;              // its controller state and outputs
   cudaStream_t own_stream = nullptr;  // capturable stream used when the caller passes stream 0
   cudaEvent_t order_ev = nullptr;     // orders own_stream after the caller's stream
   std::vector<uint8_t> host_small;  // staging
@@ -266,6 +268,10 @@ struct SweepArgs {
   // computes the true value alpha s_v (A x~)(v), sums it, and stores it times s_v.
   const float* rs_f;
   const double* rs_d;
+  // MODE_CAND with the table chosen on the device: candidate rows read Min + level * level_stride
+  // (level read from level_ptr once per launch; nullptr: Min as given)
+  const int32_t* level_ptr;
+  int64_t level_stride;
 };
 
 // Profiling hooks around sweep launches (no-ops unless gedwalk_profile(1) was called).
@@ -276,10 +282,15 @@ void profile_end(cudaStream_t s, cudaEvent_t a, double bytes, int key);
 void profile_add(double ms, double bytes, int key);
 // Counts n kernel launches (graph replays).
 void count_launches(int n);
+// Marks the calling thread as capturing a graph (its launches are counted when the graph runs).
+void set_capturing(bool on);
 // Algorithmic bytes of one sweep launch: CSR once, x read once, y written once, plus the mask
 // and the phi^miss row where the mode reads or writes them.
 double sweep_bytes(int mode, bool fp64, int cols, int32_t n, int64_t nnz, bool weighted = false);
 
+// Sets a sweep instantiation's launch attributes on the current device (before a stream capture
+// that launches it; launch_sweep does it on first use otherwise).
+gedwalk_status configure_sweep(int mode, bool fp64, int cols);
 // Launches one sweep (instantiated for the supported (type, columns, mode) triples).
 gedwalk_status launch_sweep(int mode, bool fp64, int cols, const SweepArgs& a, cudaStream_t s, bool profile = true);
 // Column-sum count of a mode at width cols.
@@ -324,8 +335,8 @@ struct GreedyShape {
   int32_t cols_max;   // widest sweep of the run (walk vectors are sized for it)
 };
 gedwalk_status greedy_shape(const Graph& g, const Resolved& r, int32_t flags, GreedyShape* out);
-// Device bytes a maximisation with this configuration needs in its workspace.
-int64_t maximize_footprint(const Graph& g, const Resolved& r, int32_t flags);
+// Device bytes a maximisation of k vertices with this configuration needs in its workspace.
+int64_t maximize_footprint(const Graph& g, const Resolved& r, int32_t flags, int32_t k);
 // Device bytes a batched scoring of `groups` groups with `members` members needs in its workspace.
 int64_t score_batch_footprint(const Graph& g, int64_t members, int32_t groups);
 // Resolves alpha (0 -> default), L (from epsilon unless forced) for a given epsilon.

@@ -381,7 +381,7 @@ gedwalk_status gedwalk_serve_submit(gedwalk_server_t h, int32_t graph, int32_t k
       GW_TRY(resolve(g, &p, eps, &q->r));
       GreedyShape sh{};
       GW_TRY(greedy_shape(g, q->r, q->flags, &sh));  // rejects bad lookahead / spec_cols now
-      q->need = maximize_footprint(g, q->r, q->flags);
+      q->need = maximize_footprint(g, q->r, q->flags, q->k);
     }
   }
   std::lock_guard<std::mutex> lk(srv->mu);

@@ -28,6 +28,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 
 #include "internal.h"
@@ -274,9 +275,10 @@ __device__ __forceinline__ void candidate_rows(const SweepArgs& a, const int* __
       if (valid && c >= 1 && s_cand[c - 1] == r) y[k] = m;
     }
   } else if constexpr (MODE == MODE_CAND) {
+    const T* min = static_cast<const T*>(a.Min) + (a.level_ptr ? a.level_stride * __ldg(a.level_ptr) : 0);
 #pragma unroll
     for (int k = 0; k < CPL; ++k)
-      if (valid && s_cand[c0 + k] == r) y[k] = __ldg(static_cast<const T*>(a.Min) + r);
+      if (valid && s_cand[c0 + k] == r) y[k] = __ldg(min + r);
   } else if constexpr (MODE == MODE_LOOK) {
     // level d = c / 2 runs under S + {c_1..c_d}: column 2d is its phi^miss, column 2d+1 the
     // walks through c_{d+1}, whose own row takes column 2d's value
@@ -644,18 +646,30 @@ __global__ void reduce_slots_final(const double* __restrict__ parts, int32_t nsu
   out[c] = s;
 }
 
+// Sets the instantiation's shared-memory carveout on the current device, once per device: a small
+// carveout leaves the rest of the unified L1/shared array to cache the gathered rows of x.
+template <typename T, int C, int MODE>
+void configure() {
+  constexpr int kMaxDevices = 64;
+  static std::atomic<bool> done[kMaxDevices];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return;
+  }
+  if (done[dev].load(std::memory_order_acquire)) return;
+  cudaFuncSetAttribute(sweep_kernel<T, C, MODE>, cudaFuncAttributePreferredSharedMemoryCarveout, 16);
+  cudaGetLastError();
+  done[dev].store(true, std::memory_order_release);
+}
+
 template <typename T, int C, int MODE>
 gedwalk_status run(const SweepArgs& a, cudaStream_t s, bool profile) {
   if (a.num_units == 0) return GEDWALK_OK;
   cudaEvent_t ev = nullptr;
   const bool prof = profile && profiling();
   if (prof) profile_begin(s, &ev);
-  static bool configured = false;  // small shared-memory carveout: the rest of the unified
-  if (!configured) {               // L1/shared array caches the gathered rows of x
-    cudaFuncSetAttribute(sweep_kernel<T, C, MODE>, cudaFuncAttributePreferredSharedMemoryCarveout, 16);
-    cudaGetLastError();
-    configured = true;
-  }
+  configure<T, C, MODE>();
   const int grid = (a.num_units + kWarps - 1) / kWarps;
   SweepArgs b = a;  // rows gathered with L1 priority: about kL1HubBytes of them
   b.hub = static_cast<int32_t>(std::min<int64_t>(a.n, kL1HubBytes / (sizeof(T) * C)));
@@ -683,6 +697,23 @@ int sweep_sums(int mode, int cols) {
     default:
       return 0;
   }
+}
+
+gedwalk_status configure_sweep(int mode, bool fp64, int cols) {
+#define GW_CASE(M, T, C)                                     \
+  if (mode == M && fp64 == (sizeof(T) == 8) && cols == C) { \
+    configure<T, C, M>();                                    \
+    return GEDWALK_OK;                                       \
+  }
+  GW_CASE(MODE_LOOK, float, 4)
+  GW_CASE(MODE_LOOK, float, 8)
+  GW_CASE(MODE_LOOK, float, 16)
+  GW_CASE(MODE_LOOK, double, 4)
+  GW_CASE(MODE_CAND, float, 4)
+  GW_CASE(MODE_CAND, double, 4)
+#undef GW_CASE
+  return fail(GEDWALK_ERR_INVALID, "no sweep instantiation to configure for mode %d fp64 %d cols %d", mode,
+              int(fp64), cols);
 }
 
 gedwalk_status launch_sweep(int mode, bool fp64, int cols, const SweepArgs& a, cudaStream_t s, bool profile) {
