@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--scale", type=int, default=22, help="R-MAT scale (22 is the configured size)")
     ap.add_argument("--k", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--device-loop", action="store_true",
+                    help="greedy: run the k steps as one device-resident CUDA graph (its kernels are hidden from ncu)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--batch-cols", type=int, default=0,
                     help="batch workload: pin the column-block width (0 = the autotuner picks it)")
@@ -289,7 +291,8 @@ def run_greedy(args, spec, rank, world, local):
     upload_s = time.perf_counter() - t_up
     params = gedwalk.make_params(epsilon=spec["eps"], precision=spec["precision"], stream=stream.cuda_stream,
                                  stochastic=spec.get("stochastic", False), eta=spec.get("eta", 0.1),
-                                 seed=spec.get("seed", 0), adaptive=spec.get("adaptive", False))
+                                 seed=spec.get("seed", 0), adaptive=spec.get("adaptive", False),
+                                 device_loop=args.device_loop)
     k = spec["k"]
     for _ in range(args.warmup):
         grp, gains, score, L = G.maximize(k, params=params)

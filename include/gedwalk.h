@@ -73,7 +73,9 @@ enum {
 enum {
   GEDWALK_GAINS_ALL = 1,  /* maximize: evaluate every vertex's exact gain at every step (no pruning) */
   GEDWALK_STOCHASTIC = 2, /* maximize: stochastic greedy (Appendix D), see gedwalk_maximize */
-  GEDWALK_ADAPTIVE_L = 4  /* maximize: lazy greedy with l-doubling (Algorithm 2), see gedwalk_maximize */
+  GEDWALK_ADAPTIVE_L = 4, /* maximize: lazy greedy with l-doubling (Algorithm 2), see gedwalk_maximize */
+  GEDWALK_DEVICE_LOOP = 8 /* maximize: with the lookahead on, run the k steps as one device-resident
+                           * CUDA graph instead of the host loop; same kernels, same result */
 };
 
 /* gedwalk_graph_upload flags */
@@ -88,7 +90,7 @@ typedef struct {
   int32_t L;               /* 0: smallest l with B_l < epsilon (Algorithm 1); > 0: forced length */
   int32_t precision;       /* GEDWALK_FP64 or GEDWALK_FP32 */
   int32_t greedy_eps_rule; /* GEDWALK_EPS_OVER_K (default) or GEDWALK_EPS_PLAIN */
-  int32_t flags;           /* GEDWALK_GAINS_ALL, GEDWALK_STOCHASTIC */
+  int32_t flags;           /* GEDWALK_GAINS_ALL, GEDWALK_STOCHASTIC, GEDWALK_ADAPTIVE_L, GEDWALK_DEVICE_LOOP */
   int64_t stream;          /* cudaStream_t to run on (e.g. torch.cuda.current_stream().cuda_stream); 0 = default */
   double eta;              /* stochastic greedy: sample (n/k) ln(1/eta) vertices per step, 0 < eta < 1 */
   uint64_t seed;           /* stochastic greedy: seed of the counter-based sample draws */
@@ -305,6 +307,10 @@ GEDWALK_API gedwalk_status gedwalk_gains(gedwalk_graph_t g, const int32_t* S, in
  * params->lookahead (1 = off, 2, 4; 8 in FP32) sets the number of steps per run
  * (0: 4 in FP32, 2 in FP64); params->spec_cols the width of the one-step fused
  * sweep when the lookahead is off. Other values return INVALID.
+ * The host drives the steps: one synchronisation per bound pass, to read the
+ * selection. With the lookahead on, GEDWALK_DEVICE_LOOP runs the k steps as one
+ * device-resident CUDA graph instead (conditional nodes: the certification loop
+ * never returns to the host). The picks and gains do not depend on it.
  * GEDWALK_ADAPTIVE_L runs the lazy greedy of Algorithm 2 (Section 3.2.3): the
  * walk length l starts at 1 and only doubles. At each step u, the vertex with the
  * largest L_l(S, u) = GED_{<=l}(S, u), is taken when it is separated from v, the

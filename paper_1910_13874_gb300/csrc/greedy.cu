@@ -31,7 +31,9 @@ namespace gw {
 namespace {
 
 constexpr int kTopK = 16;
-constexpr int kSelBlocks = 152 * 8;
+constexpr int kSelPerSM = 4;               // resident blocks of the bound pass per SM
+constexpr int kSelU = 2;                   // vertices per lane and iteration of the bound pass
+constexpr int kSelBlocks = 152 * kSelPerSM;
 
 struct Stale {
   float ub;      // last exact gain rounded up (an upper bound for every later step)
@@ -45,7 +47,7 @@ struct SelOut {  // device -> host after each selection pass
   // (caller id << 32) | internal id (all ones: none)
   unsigned long long zero_min;
   int32_t sampled;  // stochastic greedy: sampled vertices outside S seen by the pass
-  int32_t pad;
+  int32_t done;     // blocks of the pass that have finished
   double gains[16];  // exact gains of the last candidate batch
 };
 
@@ -75,86 +77,71 @@ struct Sampling {
   uint32_t step;
 };
 
-__device__ __forceinline__ void topk_push(float (&v)[kTopK], int (&id)[kTopK], float x, int ix) {
-  if (!better(x, ix, v[kTopK - 1], id[kTopK - 1])) return;
-  v[kTopK - 1] = x;
-  id[kTopK - 1] = ix;
-#pragma unroll
-  for (int i = kTopK - 1; i > 0; --i) {
-    if (better(v[i], id[i], v[i - 1], id[i - 1])) {
-      const float tv = v[i];
-      v[i] = v[i - 1];
-      v[i - 1] = tv;
-      const int ti = id[i];
-      id[i] = id[i - 1];
-      id[i - 1] = ti;
+constexpr unsigned kFullMask = 0xffffffffu;
+
+// A warp's sorted list of its kTopK best (value, id) pairs in the order of `better`: lane i <
+// kTopK holds the i-th entry (value -1, id INT_MAX: empty); `tag` travels with its entry.
+struct WarpList {
+  float v = -1.0f;
+  int id = INT_MAX;
+  int tag = 0;
+};
+
+// Offers every lane's (x, ix, tag) where `want` holds. Only the lanes that beat the list's last
+// entry are inserted, one at a time (lowest lane first); after each insertion the others are
+// checked again against the new last entry. Ids must be distinct. All 32 lanes take part.
+__device__ __forceinline__ void warp_list_offer(WarpList& w, bool want, float x, int ix, int tag) {
+  const int lane = threadIdx.x & 31;
+  float tv = __shfl_sync(kFullMask, w.v, kTopK - 1);
+  int ti = __shfl_sync(kFullMask, w.id, kTopK - 1);
+  unsigned m = __ballot_sync(kFullMask, want && better(x, ix, tv, ti));
+  while (m) {
+    const int src = __ffs(m) - 1;
+    const float cv = __shfl_sync(kFullMask, x, src);
+    const int ci = __shfl_sync(kFullMask, ix, src);
+    const int ct = __shfl_sync(kFullMask, tag, src);
+    // the entries ahead of the new one form a prefix of the sorted list
+    const int pos = __popc(__ballot_sync(kFullMask, lane < kTopK && better(w.v, w.id, cv, ci)));
+    const float uv = __shfl_up_sync(kFullMask, w.v, 1);
+    const int ui = __shfl_up_sync(kFullMask, w.id, 1);
+    const int ut = __shfl_up_sync(kFullMask, w.tag, 1);
+    if (lane == pos) {
+      w.v = cv;
+      w.id = ci;
+      w.tag = ct;
+    } else if (lane > pos && lane < kTopK) {
+      w.v = uv;
+      w.id = ui;
+      w.tag = ut;
     }
+    tv = __shfl_sync(kFullMask, w.v, kTopK - 1);
+    ti = __shfl_sync(kFullMask, w.id, kTopK - 1);
+    m &= m - 1;
+    m &= __ballot_sync(kFullMask, want && better(x, ix, tv, ti));
   }
 }
 
-// Block-wide top-K of the threads' sorted lists (NT threads); out[0..K) is written (by thread 0)
-// before the closing barrier. First every warp draws its own top K (K rounds of a warp-wide argmax
-// over the lanes' list heads, the winning lane popping its head), then warp 0 merges the NT/32
-// sorted warp lists the same way. Ids are distinct across the lists, so one lane pops per round.
-template <int NT>
-__device__ void block_topk(float (&v)[kTopK], int (&id)[kTopK], float* out_v, int* out_id) {
-  constexpr int NW = NT / 32;
-  static_assert(NW <= 32, "one lane per warp list in the merge");
-  __shared__ float wv[NW][kTopK];
-  __shared__ int wi[NW][kTopK];
+// Merges the NW warp lists of a block into warp 0's list (staged through shared memory sv/si/st,
+// NW * kTopK entries each). Every thread of the block calls it.
+template <int NW>
+__device__ void block_list_merge(WarpList& w, float* sv, int* si, int* st) {
+  static_assert(kTopK == 16, "two warp lists per 32-lane offer");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int round = 0; round < kTopK; ++round) {
-    float bv = v[0];
-    int bi = id[0];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (better(ov, oi, bv, bi)) {
-        bv = ov;
-        bi = oi;
-      }
-    }
-    if (lane == 0) {
-      wv[warp][round] = bv;
-      wi[warp][round] = bi;
-    }
-    if (bi != INT_MAX && id[0] == bi && v[0] == bv) {
-#pragma unroll
-      for (int i = 0; i < kTopK - 1; ++i) {
-        v[i] = v[i + 1];
-        id[i] = id[i + 1];
-      }
-      v[kTopK - 1] = -1.0f;
-      id[kTopK - 1] = INT_MAX;
-    }
+  if (lane < kTopK) {
+    sv[warp * kTopK + lane] = w.v;
+    si[warp * kTopK + lane] = w.id;
+    st[warp * kTopK + lane] = w.tag;
   }
   __syncthreads();
   if (warp == 0) {
-    int p = 0;  // lane w: the next entry of warp w's list
-    for (int round = 0; round < kTopK; ++round) {
-      float hv = -1.0f;
-      int hi = INT_MAX;
-      if (lane < NW && p < kTopK) {
-        hv = wv[lane][p];
-        hi = wi[lane][p];
-      }
-      float bv = hv;
-      int bi = hi;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (better(ov, oi, bv, bi)) {
-          bv = ov;
-          bi = oi;
-        }
-      }
-      if (lane == 0) {
-        out_v[round] = bv;
-        out_id[round] = bi;
-      }
-      if (bi != INT_MAX && hi == bi && hv == bv) ++p;
+    for (int j = 1; j < NW; j += 2) {  // lists j and j + 1 on lanes 0-15 and 16-31
+      const int src = j + (lane >> 4);
+      const bool ok = src < NW;
+      const int e = src * kTopK + (lane & 15);
+      const float x = ok ? sv[e] : -1.0f;
+      const int ix = ok ? si[e] : INT_MAX;
+      const int t = ok ? st[e] : 0;
+      warp_list_offer(w, ix != INT_MAX, x, ix, t);
     }
   }
   __syncthreads();
@@ -182,25 +169,71 @@ __global__ void greedy_init(T* __restrict__ m0, T* __restrict__ X, int cols, int
 
 // MODE_LOOK initialisation: level d (columns 2d, 2d+1) runs under S + {c_1..c_d}: column 2d is
 // its phi^miss_0 (also table d, row 0), column 2d+1 the unit vector of c_{d+1} (0 without one).
+// The walk vectors are written 16 bytes per thread (consecutive threads, consecutive chunks).
 template <typename T>
-__global__ void look_init(T* __restrict__ tab, int64_t tab_stride, T* __restrict__ X, int levels,
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using type = float4;
+  __device__ static float4 make(const float* e) { return make_float4(e[0], e[1], e[2], e[3]); }
+};
+template <>
+struct Vec16<double> {
+  using type = double2;
+  __device__ static double2 make(const double* e) { return make_double2(e[0], e[1]); }
+};
+
+template <typename T, int LV>
+__global__ void look_init(T* __restrict__ tab, int64_t tab_stride, T* __restrict__ X,
                           const int32_t* __restrict__ cand, const uint32_t* __restrict__ mask, int32_t n,
                           const T* __restrict__ rs) {
-  __shared__ int sc[8];
-  if (threadIdx.x < 8) sc[threadIdx.x] = threadIdx.x < levels ? cand[threadIdx.x] : -1;
+  constexpr int cols = 2 * LV;
+  constexpr int per = 16 / static_cast<int>(sizeof(T));  // elements per 16-byte chunk
+  static_assert(cols % per == 0, "a row is whole 16-byte chunks");
+  constexpr int cpr = cols / per;                         // chunks per row
+  __shared__ int sc[LV];
+  if (threadIdx.x < LV) sc[threadIdx.x] = cand[threadIdx.x];
   __syncthreads();
-  const int cols = 2 * levels;
-  for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-    bool out = (mask[v >> 5] >> (v & 31)) & 1u;
+  const int64_t chunks = static_cast<int64_t>(n) * cpr;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  using V = typename Vec16<T>::type;
+  for (int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < chunks; q += stride) {
+    const int32_t v = static_cast<int32_t>(q / cpr);
+    const int part = static_cast<int>(q % cpr);
+    const bool inS = (__ldg(mask + (v >> 5)) >> (v & 31)) & 1u;
     const T sv = rs ? rs[v] : T(1);
-    T* row = X + static_cast<size_t>(v) * cols;
-    for (int d = 0; d < levels; ++d) {
-      if (d > 0 && sc[d - 1] == v) out = true;
-      const T m = out ? T(0) : T(1);
-      tab[tab_stride * d + v] = m;
-      row[2 * d] = m * sv;
-      row[2 * d + 1] = sc[d] == v ? sv : T(0);
+    T e[per];
+#pragma unroll
+    for (int j = 0; j < per; ++j) {
+      const int col = part * per + j;
+      const int d = col >> 1;
+      if (col & 1) {
+        e[j] = sc[d] == v ? sv : T(0);
+      } else {
+        bool out = inS;
+        for (int i = 0; i < d; ++i) out |= sc[i] == v;
+        e[j] = out ? T(0) : sv;
+      }
     }
+    reinterpret_cast<V*>(X)[q] = Vec16<T>::make(e);
+  }
+  for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    bool out = (__ldg(mask + (v >> 5)) >> (v & 31)) & 1u;
+#pragma unroll
+    for (int d = 0; d < LV; ++d) {
+      if (d > 0 && sc[d - 1] == v) out = true;
+      tab[tab_stride * d + v] = out ? T(0) : T(1);
+    }
+  }
+}
+
+template <typename T>
+void launch_look_init(int levels, int blocks, cudaStream_t s, T* tab, int64_t tab_stride, T* X, const int32_t* cand,
+                      const uint32_t* mask, int32_t n, const T* rs) {
+  switch (levels) {
+    case 2: look_init<T, 2><<<blocks, 256, 0, s>>>(tab, tab_stride, X, cand, mask, n, rs); break;
+    case 4: look_init<T, 4><<<blocks, 256, 0, s>>>(tab, tab_stride, X, cand, mask, n, rs); break;
+    default: look_init<T, 8><<<blocks, 256, 0, s>>>(tab, tab_stride, X, cand, mask, n, rs); break;
   }
 }
 
@@ -285,40 +318,43 @@ __device__ float ub_any(const T* __restrict__ col, const T* __restrict__ zcol, i
   return __fmaf_ru(m0, R, ub);
 }
 
-// Lemma-initialize bound + selection over vertices [0, n_scan) (the tables have n rows apart).
-// LF = L when L <= 16, else 0 (any L).
+// Lemma-initialize bound + selection over vertices [0, n_scan) (the tables have n rows apart):
+// the kTopK unevaluated vertices outside S with the largest bounds go to out->val / out->id.
+// Each warp keeps its own list (bounds offered 32 at a time, two per lane per iteration), a block
+// merges its warps' lists into sel_v / sel_id[block], and the last block to finish merges the
+// blocks' lists: only the kTopK blocks whose heads rank among the best kTopK heads can hold an
+// entry of the result (any other head has kTopK better entries ahead of it). out->done counts the
+// finished blocks (0 before the pass). LF = L when L <= 16, else 0 (any L).
 template <typename T, int LF>
-__global__ void __launch_bounds__(kThreads) ub_select(const T* __restrict__ mtab, const T* __restrict__ ztab,
+__global__ void __launch_bounds__(kThreads, kSelPerSM) ub_select(const T* __restrict__ mtab, const T* __restrict__ ztab,
                                                      int32_t L, int32_t n, int32_t n_scan,
                                                      const uint32_t* __restrict__ mask,
                                                      const Stale* __restrict__ stale, int32_t step,
                                                      const int32_t* __restrict__ perm, float* __restrict__ sel_v,
-                                                     int* __restrict__ sel_id,
-                                                     unsigned long long* __restrict__ zero_min, const Sampling smp,
-                                                     int32_t* __restrict__ sampled, const int32_t* level_ptr,
+                                                     int* __restrict__ sel_id, SelOut* __restrict__ out,
+                                                     const Sampling smp, const int32_t* level_ptr,
                                                      int64_t level_stride, const int32_t* step_ptr) {
+  constexpr int NW = kThreads / 32;
+  static_assert(2 * NW >= kTopK, "the final merge gives each warp two block lists");
+  constexpr int U = kSelU;
   if (level_ptr) {  // the table (lookahead level) the device-resident loop chose for this step
     const int64_t off = level_stride * __ldg(level_ptr);
     mtab += off;
     ztab += off;
   }
   if (step_ptr) step = __ldg(step_ptr);  // the device-resident loop's step
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int nsampled = 0;
-  float v[kTopK];
-  int id[kTopK];
+  WarpList w;
+  // U * 32 consecutive vertices per warp and iteration, all loads issued before any decision
+  const int32_t wid = blockIdx.x * NW + warp;
+  const int32_t wstride = gridDim.x * NW * (U * 32);
+  for (int32_t base = wid * (U * 32); base < n_scan; base += wstride) {
+    float b[U];
+    bool live[U];
 #pragma unroll
-  for (int i = 0; i < kTopK; ++i) {
-    v[i] = -1.0f;
-    id[i] = INT_MAX;
-  }
-  // four vertices per iteration, all of their loads issued before any decision
-  const int32_t stride = gridDim.x * blockDim.x;
-  for (int32_t base = blockIdx.x * blockDim.x + threadIdx.x; base < n_scan; base += 4 * stride) {
-    float b[4];
-    bool live[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int32_t xr = base + k * stride;
+    for (int k = 0; k < U; ++k) {
+      const int32_t xr = base + k * 32 + lane;
       const int32_t x = xr < n_scan ? xr : n_scan - 1;
       const bool inS = (__ldg(mask + (x >> 5)) >> (x & 31)) & 1u;
       const Stale st = stale[x];
@@ -335,27 +371,64 @@ __global__ void __launch_bounds__(kThreads) ub_select(const T* __restrict__ mtab
       live[k] = xr < n_scan && !inS && in_sample && st.step != step;
     }
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      if (!live[k]) continue;
-      const int32_t x = base + k * stride;
-      if (b[k] == 0.0f) {
-        atomicMin(zero_min, (static_cast<unsigned long long>(__ldg(perm + x)) << 32) | static_cast<uint32_t>(x));
-        continue;
-      }
-      topk_push(v, id, b[k], x);
+    for (int k = 0; k < U; ++k) {
+      const int32_t x = base + k * 32 + lane;
+      if (live[k] && b[k] == 0.0f)
+        atomicMin(&out->zero_min, (static_cast<unsigned long long>(__ldg(perm + x)) << 32) | static_cast<uint32_t>(x));
+      warp_list_offer(w, live[k] && b[k] != 0.0f, b[k], x, 0);
     }
   }
   if (smp.thr != ~0ull) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) nsampled += __shfl_xor_sync(0xffffffffu, nsampled, o);
-    if ((threadIdx.x & 31) == 0 && nsampled) atomicAdd(sampled, nsampled);
+    for (int o = 16; o > 0; o >>= 1) nsampled += __shfl_xor_sync(kFullMask, nsampled, o);
+    if (lane == 0 && nsampled) atomicAdd(&out->sampled, nsampled);
   }
-  __shared__ float ov[kTopK];
-  __shared__ int oi[kTopK];
-  block_topk<kThreads>(v, id, ov, oi);
-  if (threadIdx.x < kTopK) {
-    sel_v[blockIdx.x * kTopK + threadIdx.x] = ov[threadIdx.x];
-    sel_id[blockIdx.x * kTopK + threadIdx.x] = oi[threadIdx.x];
+  __shared__ float sv[NW * kTopK];
+  __shared__ int si[NW * kTopK], st[NW * kTopK];
+  __shared__ int is_last;
+  block_list_merge<NW>(w, sv, si, st);
+  if (warp == 0) {
+    if (lane < kTopK) {
+      sel_v[blockIdx.x * kTopK + lane] = w.v;
+      sel_id[blockIdx.x * kTopK + lane] = w.id;
+    }
+    __threadfence();
+    __syncwarp();
+    int done = 0;
+    if (lane == 0) done = atomicAdd(&out->done, 1);
+    if (lane == 0) is_last = done == static_cast<int>(gridDim.x) - 1;
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  // the best kTopK block heads (tag: the block)
+  WarpList h;
+  for (int32_t b0 = warp * 32; b0 < static_cast<int32_t>(gridDim.x); b0 += NW * 32) {
+    const int32_t blk = b0 + lane;
+    const bool ok = blk < static_cast<int32_t>(gridDim.x);
+    const float x = ok ? __ldcg(sel_v + static_cast<size_t>(blk) * kTopK) : -1.0f;
+    const int ix = ok ? __ldcg(sel_id + static_cast<size_t>(blk) * kTopK) : INT_MAX;
+    warp_list_offer(h, ix != INT_MAX, x, ix, blk);
+  }
+  block_list_merge<NW>(h, sv, si, st);
+  __shared__ int heads[kTopK];
+  if (warp == 0 && lane < kTopK) heads[lane] = h.id != INT_MAX ? h.tag : -1;
+  __syncthreads();
+  // the entries of those blocks, two block lists per warp
+  WarpList f;
+  {
+    const int j = 2 * warp + (lane >> 4);
+    const int blk = j < kTopK ? heads[j] : -1;
+    const bool ok = blk >= 0;
+    const size_t e = static_cast<size_t>(ok ? blk : 0) * kTopK + (lane & 15);
+    const float x = ok ? __ldcg(sel_v + e) : -1.0f;
+    const int ix = ok ? __ldcg(sel_id + e) : INT_MAX;
+    warp_list_offer(f, ix != INT_MAX, x, ix, 0);
+  }
+  block_list_merge<NW>(f, sv, si, st);
+  if (warp == 0 && lane < kTopK) {
+    out->val[lane] = f.v;
+    out->id[lane] = f.id;
   }
 }
 
@@ -363,52 +436,36 @@ template <typename T>
 cudaError_t launch_ub_select(int nb, cudaStream_t s, const T* mtab, const T* ztab, int32_t L, int32_t n,
                              int32_t n_scan, const uint32_t* mask,
                              const Stale* stale, int32_t step, const int32_t* perm, float* sel_v, int* sel_id,
-                             unsigned long long* zero_min, const Sampling& smp, int32_t* sampled,
+                             SelOut* out, const Sampling& smp,
                              const int32_t* level_ptr = nullptr, int64_t level_stride = 0,
                              const int32_t* step_ptr = nullptr) {
 #define GW_UB(LL)                                                                                          \
   case LL:                                                                                                 \
     ub_select<T, LL><<<nb, kThreads, 0, s>>>(mtab, ztab, L, n, n_scan, mask, stale, step, perm, sel_v, sel_id, \
-                                             zero_min, smp, sampled, level_ptr, level_stride, step_ptr);   \
+                                             out, smp, level_ptr, level_stride, step_ptr);                 \
     break;
   switch (L) {
     GW_UB(1) GW_UB(2) GW_UB(3) GW_UB(4) GW_UB(5) GW_UB(6) GW_UB(7) GW_UB(8)
     GW_UB(9) GW_UB(10) GW_UB(11) GW_UB(12) GW_UB(13) GW_UB(14) GW_UB(15) GW_UB(16)
     default:
       ub_select<T, 0><<<nb, kThreads, 0, s>>>(mtab, ztab, L, n, n_scan, mask, stale, step, perm, sel_v, sel_id,
-                                              zero_min, smp, sampled, level_ptr, level_stride, step_ptr);
+                                              out, smp, level_ptr, level_stride, step_ptr);
   }
 #undef GW_UB
   return cudaGetLastError();
 }
 
-constexpr int kMergeThreads = 1024;
-
-__global__ void __launch_bounds__(kMergeThreads) select_merge(const float* __restrict__ sel_v,
-                                                             const int* __restrict__ sel_id, int count,
-                                                             SelOut* __restrict__ out) {
-  float v[kTopK];
-  int id[kTopK];
-#pragma unroll
-  for (int i = 0; i < kTopK; ++i) {
-    v[i] = -1.0f;
-    id[i] = INT_MAX;
-  }
-  for (int i = threadIdx.x; i < count; i += kMergeThreads)
-    if (sel_id[i] != INT_MAX) topk_push(v, id, sel_v[i], sel_id[i]);
-  __shared__ float ov[kTopK];
-  __shared__ int oi[kTopK];
-  block_topk<kMergeThreads>(v, id, ov, oi);
-  if (threadIdx.x < kTopK) {
-    out->val[threadIdx.x] = ov[threadIdx.x];
-    out->id[threadIdx.x] = oi[threadIdx.x];
-  }
+// Blocks of a selection pass: one wave at kSelPerSM blocks per SM, one iteration per lane at least.
+int sel_blocks(int32_t n_scan) {
+  constexpr int64_t per_block = int64_t(kThreads) * kSelU;
+  return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(kSelBlocks, (int64_t(n_scan) + per_block - 1) / per_block)));
 }
 
 // Resets the per-pass counters of a selection pass.
 __global__ void reset_selection(SelOut* out) {
   out->zero_min = kNoZero;
   out->sampled = 0;
+  out->done = 0;
 }
 
 int blocks_for(int64_t n) { return static_cast<int>(std::min<int64_t>((n + 255) / 256, 152 * 16)); }
@@ -476,14 +533,15 @@ gedwalk_status issue_sweeps(GreedyCtx& c, int mode, int cols, bool profile, cons
   const int64_t look_stride = static_cast<int64_t>(c.L + 1) * g.n;  // elements between level tables
   void* m0 = mode == MODE_FUSED ? tab.as<char>() + off * c.es : nullptr;
   if (mode == MODE_LOOK) {
+    // lookahead levels: 2, 4 or 8 (the shape admits no other)
+    const int64_t chunks = static_cast<int64_t>(g.n) * cols * static_cast<int64_t>(c.es) / 16;
     if (fp64)
-      look_init<double><<<blocks_for(g.n), 256, 0, c.s>>>(ws.mtab.as<double>(), look_stride, ws.x0.as<double>(),
-                                                          cols / 2, c.d_cand, ws.mask.as<uint32_t>(), g.n,
-                                                          g.weighted ? g.rs_d.as<double>() : nullptr);
+      launch_look_init<double>(cols / 2, blocks_for(chunks), c.s, ws.mtab.as<double>(), look_stride,
+                               ws.x0.as<double>(), c.d_cand, ws.mask.as<uint32_t>(), g.n,
+                               g.weighted ? g.rs_d.as<double>() : nullptr);
     else
-      look_init<float><<<blocks_for(g.n), 256, 0, c.s>>>(ws.mtab.as<float>(), look_stride, ws.x0.as<float>(),
-                                                         cols / 2, c.d_cand, ws.mask.as<uint32_t>(), g.n,
-                                                         g.weighted ? g.rs_f.as<float>() : nullptr);
+      launch_look_init<float>(cols / 2, blocks_for(chunks), c.s, ws.mtab.as<float>(), look_stride, ws.x0.as<float>(),
+                              c.d_cand, ws.mask.as<uint32_t>(), g.n, g.weighted ? g.rs_f.as<float>() : nullptr);
   } else if (fp64)
     greedy_init<double><<<blocks_for(g.n), 256, 0, c.s>>>(static_cast<double*>(m0), ws.x0.as<double>(), cols, first,
                                                            c.d_cand, ws.mask.as<uint32_t>(), g.n,
@@ -948,10 +1006,11 @@ gedwalk_status greedy_shape(const Graph& g, const Resolved& r, int32_t flags, Gr
 }
 
 namespace {
-// The plain greedy with lookahead runs its k steps as one CUDA graph (device-resident loop).
+// GEDWALK_DEVICE_LOOP: the plain greedy with lookahead runs its k steps as one CUDA graph.
 bool uses_device_loop(const Graph& g, const GreedyShape& sh, int32_t flags, int32_t k) {
-  return sh.levels > 1 && (flags & (GEDWALK_GAINS_ALL | GEDWALK_STOCHASTIC | GEDWALK_ADAPTIVE_L)) == 0 && !g.directed &&
-         k > 0 && g.plan.num_units > 0;
+  return (flags & GEDWALK_DEVICE_LOOP) && sh.levels > 1 &&
+         (flags & (GEDWALK_GAINS_ALL | GEDWALK_STOCHASTIC | GEDWALK_ADAPTIVE_L)) == 0 && !g.directed && k > 0 &&
+         g.plan.num_units > 0;
 }
 // Its controller block: the state, then the group and the gains of up to kcap steps.
 int32_t loop_kcap(int32_t k) {
@@ -1102,14 +1161,12 @@ gedwalk_status run_device_loop(GreedyCtx& c, int32_t k, int levels, int cols_can
       const Sampling all{~0ull, 0, 0};
       if (fp64)
         GW_CUDA(launch_ub_select<double>(nb_sel, s, ws.mtab.as<double>(), ws.mtab.as<double>(), L, g.n, n_scan, mask,
-                                         stale, 0, perm, sel_v, sel_id, &c.d_out->zero_min, all, &c.d_out->sampled,
-                                         d_level, static_cast<int64_t>(tab_elems), d_step));
+                                         stale, 0, perm, sel_v, sel_id, c.d_out, all, d_level,
+                                         static_cast<int64_t>(tab_elems), d_step));
       else
         GW_CUDA(launch_ub_select<float>(nb_sel, s, ws.mtab.as<float>(), ws.mtab.as<float>(), L, g.n, n_scan, mask,
-                                        stale, 0, perm, sel_v, sel_id, &c.d_out->zero_min, all, &c.d_out->sampled,
-                                        d_level, static_cast<int64_t>(tab_elems), d_step));
-      select_merge<<<1, kMergeThreads, 0, s>>>(sel_v, sel_id, nb_sel * kTopK, c.d_out);
-      GW_CUDA(cudaGetLastError());
+                                        stale, 0, perm, sel_v, sel_id, c.d_out, all, d_level,
+                                        static_cast<int64_t>(tab_elems), d_step));
       ctl_certify<<<1, 32, 0, s>>>(dctl, c.d_out, mask, perm, g.n, c.d_cand, d_ogroup, d_ogains, tol, max_batches,
                                    h_loop, h_cand);
       GW_CUDA(cudaGetLastError());
@@ -1154,8 +1211,8 @@ gedwalk_status run_device_loop(GreedyCtx& c, int32_t k, int levels, int cols_can
   ws.st_sweeps = (out.runs + out.cand_batches) * L;
   ws.st_ell.assign(k, L);
   // launches the graph ran: per step open/close, per run init + L sweeps + 2 stamps + 2 reduce +
-  // after_run, per certification round 5 kernels, per batch init + L sweeps + 2 stamps + 2 reduce
-  count_launches(static_cast<int>(2 * k + out.runs * (L + 6) + out.iters * 5 + out.cand_batches * (L + 5)));
+  // after_run, per certification round 4 kernels, per batch init + L sweeps + 2 stamps + 2 reduce
+  count_launches(static_cast<int>(2 * k + out.runs * (L + 6) + out.iters * 4 + out.cand_batches * (L + 5)));
   if (profiling()) {  // the sweeps' device time, from the device-clock stamps around each run / batch
     const double b_look = sweep_bytes(MODE_LOOK, fp64, 2 * levels, g.n, g.nnz, g.weighted);
     const double b_cand = sweep_bytes(MODE_CAND, fp64, cols_cand, g.n, g.nnz, g.weighted);
@@ -1285,24 +1342,22 @@ gedwalk_status maximize_impl(Graph& g, Workspace& ws, int32_t k, const Resolved&
   // The relabelling is a stable sort by degree, so the isolated rows hold increasing caller ids.
   const int32_t n_scan = stochastic ? g.n : g.n_active;
   int32_t iso_next = stochastic ? g.n : g.n_active;  // first isolated row not in S
-  const int nb_sel =
-      static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(kSelBlocks, (int64_t(n_scan) + 1023) / 1024)));
+  const int nb_sel = sel_blocks(n_scan);
   // One bound + selection pass into c.d_out / c.h_out; `step` decides which stale gains are exact.
   auto select_pass = [&](int32_t st, const Sampling& smp) -> gedwalk_status {
     reset_selection<<<1, 1, 0, s>>>(c.d_out);
+    GW_KCHECK();
     if (r.fp64)
       GW_CUDA(launch_ub_select<double>(nb_sel, s, ws.mtab.as<double>() + c.tab_off,
                                        g.directed ? ws.ztab.as<double>() : ws.mtab.as<double>() + c.tab_off, c.L, g.n,
                                        n_scan, ws.mask.as<uint32_t>(), stale, st, g.perm_d.as<int32_t>(), sel_v,
-                                       sel_id, &c.d_out->zero_min, smp, &c.d_out->sampled));
+                                       sel_id, c.d_out, smp));
     else
       GW_CUDA(launch_ub_select<float>(nb_sel, s, ws.mtab.as<float>() + c.tab_off,
                                       g.directed ? ws.ztab.as<float>() : ws.mtab.as<float>() + c.tab_off, c.L, g.n,
                                       n_scan, ws.mask.as<uint32_t>(), stale, st, g.perm_d.as<int32_t>(), sel_v,
-                                      sel_id, &c.d_out->zero_min, smp, &c.d_out->sampled));
+                                      sel_id, c.d_out, smp));
     count_launch();
-    select_merge<<<1, kMergeThreads, 0, s>>>(sel_v, sel_id, nb_sel * kTopK, c.d_out);
-    GW_KCHECK();
     GW_CUDA(cudaMemcpyAsync(c.h_out, c.d_out, sizeof(SelOut), cudaMemcpyDeviceToHost, s));
     GW_CUDA(cudaStreamSynchronize(s));
     read_graph_timing(ws);

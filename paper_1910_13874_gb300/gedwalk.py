@@ -25,6 +25,7 @@ EPS_OVER_K, EPS_PLAIN = 0, 1
 GAINS_ALL = 1
 STOCHASTIC = 2
 ADAPTIVE_L = 4
+DEVICE_LOOP = 8
 BOUND_COMBINATORIAL, BOUND_SPECTRAL = 0, 1
 UPLOAD_TRUSTED = 1
 UPLOAD_DIRECTED = 2
@@ -188,7 +189,7 @@ def _ptr(a: np.ndarray, t):
 def make_params(alpha: float = 0.0, epsilon: float = 1e-4, L: int = 0, precision: str = "fp32",
                 eps_rule: str = "over_k", gains_all: bool = False, stream: int = 0, stochastic: bool = False,
                 eta: float = 0.1, seed: int = 0, adaptive: bool = False, bound: str = "combinatorial",
-                lookahead: int = 0, spec_cols: int = 0) -> Params:
+                lookahead: int = 0, spec_cols: int = 0, device_loop: bool = False) -> Params:
     p = Params()
     load().gedwalk_params_default(ctypes.byref(p))
     p.alpha = alpha
@@ -196,7 +197,8 @@ def make_params(alpha: float = 0.0, epsilon: float = 1e-4, L: int = 0, precision
     p.L = L
     p.precision = FP64 if precision in ("fp64", "f64", FP64) else FP32
     p.greedy_eps_rule = EPS_PLAIN if eps_rule == "plain" else EPS_OVER_K
-    p.flags = (GAINS_ALL if gains_all else 0) | (STOCHASTIC if stochastic else 0) | (ADAPTIVE_L if adaptive else 0)
+    p.flags = ((GAINS_ALL if gains_all else 0) | (STOCHASTIC if stochastic else 0) | (ADAPTIVE_L if adaptive else 0)
+               | (DEVICE_LOOP if device_loop else 0))
     p.bound = {"combinatorial": BOUND_COMBINATORIAL, "spectral": BOUND_SPECTRAL}[bound]
     p.stream = int(stream)
     p.eta = eta

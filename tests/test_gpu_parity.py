@@ -433,3 +433,40 @@ def test_lookahead_levels_match_oracle(cuda_device, name, k, levels):
     st = G.maximize_stats()
     if levels != 1:  # steps whose winner was guessed run no sweep of their own
         assert st["sweeps"] < (k + 1) * L
+
+
+@pytest.mark.parametrize("name,k,levels,prec,init", [
+    ("ba5000", 24, 4, "fp32", ()), ("rmat14", 24, 8, "fp32", ()), ("er1000", 10, 2, "fp64", ()),
+    ("rmat15", 40, 2, "fp64", ()), ("isolated", 12, 4, "fp32", ()), ("isolated", 3, 2, "fp64", (0, 1, 2, 5, 6)),
+    ("star", 6, 4, "fp32", ()), ("path", 9, 2, "fp32", (4,))])
+def test_device_loop_matches_host_loop(cuda_device, name, k, levels, prec, init):
+    # The device-resident loop (conditional graph nodes) and the host-driven loop run the same
+    # kernels on the same tables: identical picks, gains equal to the last bit, same counters.
+    g = host_graph(name)
+    G = dev_graph(name)
+    alpha = oracle.default_alpha(g)
+    kw = dict(precision=prec, epsilon=1e-4, lookahead=levels, init=list(init) or None)
+    grp_h, gains_h, score_h, L_h = G.maximize(k, **kw)
+    st_h = G.maximize_stats()
+    grp_d, gains_d, score_d, L_d = G.maximize(k, device_loop=True, **kw)
+    st_d = G.maximize_stats()
+    assert L_h == L_d
+    assert list(grp_d) == list(grp_h)
+    assert np.array_equal(gains_d, gains_h)
+    assert score_d == score_h
+    assert st_d["evaluations"] == st_h["evaluations"] and st_d["spec_misses"] == st_h["spec_misses"]
+    # and the oracle agrees with both (from the same init group)
+    ini = [int(x) for x in init]
+    ogrp, ogains, _ = oracle.greedy(g, k, alpha, L_d, "lazy", init=ini or None)
+
+    def gain_of(prefix, v):
+        return oracle.gain(g, ini + list(prefix), v, alpha, L_d)
+
+    def continue_from(prefix, count):
+        cg, cgains, _ = oracle.greedy(g, count, alpha, L_d, "lazy", init=ini + list(prefix))
+        return cg, np.asarray(cgains)
+
+    check_sequence(grp_d, gains_d, TOL[prec], ogrp, ogains, gain_of, continue_from)
+    # the loop's graph is reused by the next call with the same configuration
+    grp_r, gains_r, _, _ = G.maximize(k, device_loop=True, **kw)
+    assert list(grp_r) == list(grp_d) and np.array_equal(gains_r, gains_d)
