@@ -278,18 +278,238 @@ __global__ void relabel_kernel(const int32_t* __restrict__ raw_rp, const int32_t
   }
 }
 
-// Sorts segments of the relabelled CSR (one warp per segment of at most 1024 entries): whole rows
-// up to 1024 entries, and 1024-entry pieces of longer rows (those are summed slice by slice
-// anyway). Ascending neighbour ids put the high-degree neighbours, the most gathered rows, first
-// in every row. A bitonic network: in registers up to 32 entries, in the warp's shared memory above.
+static int grid_for(int64_t n) { return static_cast<int>(std::min<int64_t>((n + 255) / 256, 152 * 16)); }
+
+// ---------------------------------------------------------------- device relabelling
+// Exclusive scan of m unsigned counts (m >= 1), in tiles of kScanTile: each tile is scanned by one
+// block, the tiles' totals are scanned the same way (recursively), then added back.
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int64_t kScanTile = int64_t(kScanThreads) * kScanItems;
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t* warp_tot, uint32_t* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t inc = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) warp_tot[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    constexpr int NW = kScanThreads / 32;
+    uint32_t t = lane < NW ? warp_tot[lane] : 0u;
+    uint32_t ti = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, ti, o);
+      if (lane >= o) ti += y;
+    }
+    if (lane < NW) warp_tot[lane] = ti - t;  // exclusive offsets of the warps
+    if (lane == NW - 1) *total = ti;
+  }
+  __syncthreads();
+  return warp_tot[warp] + inc - x;
+}
+
+// out[i] = sum of in[tile start .. i) within each tile; sums[tile] = the tile's total.
+__global__ void __launch_bounds__(kScanThreads) scan_tiles_kernel(const uint32_t* __restrict__ in, int64_t m,
+                                                                  uint32_t* __restrict__ out,
+                                                                  uint32_t* __restrict__ sums) {
+  __shared__ uint32_t warp_tot[kScanThreads / 32];
+  __shared__ uint32_t total;
+  const int64_t base = int64_t(blockIdx.x) * kScanTile + int64_t(threadIdx.x) * kScanItems;
+  uint32_t v[kScanItems];
+  uint32_t acc = 0;
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) {
+    v[j] = base + j < m ? in[base + j] : 0u;
+    acc += v[j];
+  }
+  uint32_t run = block_exclusive_scan(acc, warp_tot, &total);
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) {
+    if (base + j < m) out[base + j] = run;
+    run += v[j];
+  }
+  if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void scan_add_kernel(uint32_t* __restrict__ out, int64_t m, const uint32_t* __restrict__ offs) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < m; i += int64_t(gridDim.x) * blockDim.x)
+    out[i] += offs[i / kScanTile];
+}
+
+// out[0..m) = exclusive scan of in[0..m); *total_out (device, may be null) = the sum. Scratch is
+// allocated per level.
+static gedwalk_status exclusive_scan(const uint32_t* in, int64_t m, uint32_t* out, uint32_t* total_out) {
+  const int64_t tiles = (m + kScanTile - 1) / kScanTile;
+  DevBuf sums, sums_scan;
+  GW_TRY(sums.ensure(static_cast<size_t>(tiles) * sizeof(uint32_t), 0));
+  scan_tiles_kernel<<<static_cast<int>(tiles), kScanThreads>>>(in, m, out, sums.as<uint32_t>());
+  GW_KCHECK();
+  if (tiles == 1) {
+    if (total_out) GW_CUDA(cudaMemcpy(total_out, sums.p, sizeof(uint32_t), cudaMemcpyDeviceToDevice));
+    return GEDWALK_OK;
+  }
+  GW_TRY(sums_scan.ensure(static_cast<size_t>(tiles) * sizeof(uint32_t), 0));
+  GW_TRY(exclusive_scan(sums.as<uint32_t>(), tiles, sums_scan.as<uint32_t>(), total_out));
+  scan_add_kernel<<<grid_for(m), 256>>>(out, m, sums_scan.as<uint32_t>());
+  GW_KCHECK();
+  return GEDWALK_OK;
+}
+
+// Stable LSD radix sort of (key, value) pairs by 8-bit digits. A block takes kRadixTile
+// consecutive pairs, each of its warps kRadixTile / 8 consecutive ones in chunks of 32 lanes in
+// index order; equal digits are ranked by __match_any_sync, so the order of equal keys is kept.
+constexpr int kRadixThreads = 256;
+constexpr int kRadixWarps = kRadixThreads / 32;
+constexpr int64_t kRadixTile = 4096;
+constexpr int kRadixChunks = static_cast<int>(kRadixTile / kRadixWarps / 32);
+
+// counts[digit * blocks + block] = pairs of the block with that digit
+__global__ void __launch_bounds__(kRadixThreads) radix_count_kernel(const uint32_t* __restrict__ keys, int64_t n,
+                                                                    int shift, uint32_t* __restrict__ counts) {
+  __shared__ uint32_t h[256];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < 256; i += kRadixThreads) h[i] = 0;
+  __syncthreads();
+  const int64_t base = int64_t(blockIdx.x) * kRadixTile + int64_t(warp) * (kRadixTile / kRadixWarps);
+  for (int c = 0; c < kRadixChunks; ++c) {
+    const int64_t j = base + c * 32 + lane;
+    const bool ok = j < n;
+    const uint32_t d = ok ? (keys[j] >> shift) & 255u : 256u;
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    if (ok && lane == __ffs(peers) - 1) atomicAdd(&h[d], static_cast<uint32_t>(__popc(peers)));
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 256; i += kRadixThreads) counts[int64_t(i) * gridDim.x + blockIdx.x] = h[i];
+}
+
+// Scatters the block's pairs to offs[digit * blocks + block] + their stable rank. vals_in null:
+// the values are the indices.
+__global__ void __launch_bounds__(kRadixThreads) radix_scatter_kernel(const uint32_t* __restrict__ keys_in,
+                                                                      const int32_t* __restrict__ vals_in, int64_t n,
+                                                                      int shift, const uint32_t* __restrict__ offs,
+                                                                      uint32_t* __restrict__ keys_out,
+                                                                      int32_t* __restrict__ vals_out) {
+  __shared__ uint32_t wc[kRadixWarps][256];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < kRadixWarps * 256; i += kRadixThreads) wc[i / 256][i % 256] = 0;
+  __syncthreads();
+  const int64_t base = int64_t(blockIdx.x) * kRadixTile + int64_t(warp) * (kRadixTile / kRadixWarps);
+  const unsigned lt = (1u << lane) - 1u;
+  for (int c = 0; c < kRadixChunks; ++c) {  // per-warp digit counts
+    const int64_t j = base + c * 32 + lane;
+    const bool ok = j < n;
+    const uint32_t d = ok ? (keys_in[j] >> shift) & 255u : 256u;
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    if (ok && lane == __ffs(peers) - 1) wc[warp][d] += __popc(peers);
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < 256; d += kRadixThreads) {  // warp offsets within the digit's range
+    uint32_t run = offs[int64_t(d) * gridDim.x + blockIdx.x];
+    for (int w = 0; w < kRadixWarps; ++w) {
+      const uint32_t t = wc[w][d];
+      wc[w][d] = run;
+      run += t;
+    }
+  }
+  __syncthreads();
+  for (int c = 0; c < kRadixChunks; ++c) {
+    const int64_t j = base + c * 32 + lane;
+    const bool ok = j < n;
+    const uint32_t key = ok ? keys_in[j] : 0u;
+    const uint32_t d = ok ? (key >> shift) & 255u : 256u;
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    if (ok) {
+      const uint32_t pos = wc[warp][d] + __popc(peers & lt);
+      keys_out[pos] = key;
+      vals_out[pos] = vals_in ? vals_in[j] : static_cast<int32_t>(j);
+    }
+    __syncwarp();
+    if (ok && lane == __ffs(peers) - 1) wc[warp][d] += __popc(peers);
+    __syncwarp();
+  }
+}
+
+// key[v] = dmax - degree(v): ascending keys order the rows by decreasing degree
+__global__ void degree_key_kernel(const int32_t* __restrict__ rp, int32_t n, int32_t dmax, uint32_t* __restrict__ key) {
+  for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x)
+    key[v] = static_cast<uint32_t>(dmax - (rp[v + 1] - rp[v]));
+}
+
+// inv[perm[i]] = i and deg[i] = dmax - key[i] (the sorted keys)
+__global__ void perm_finish_kernel(const int32_t* __restrict__ perm, const uint32_t* __restrict__ key, int32_t n,
+                                   int32_t dmax, int32_t* __restrict__ inv, uint32_t* __restrict__ deg) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    inv[perm[i]] = static_cast<int32_t>(i);
+    deg[i] = static_cast<uint32_t>(dmax) - key[i];
+  }
+}
+
+// perm: new -> caller id (decreasing degree, equal degrees by caller id), inv its inverse, deg
+// and rp the relabelled degrees and row pointers (rp[n] = nnz), all on the device.
+static gedwalk_status degree_order(const int32_t* raw_rp, int32_t n, int32_t dmax, int32_t* perm, int32_t* inv,
+                                   int32_t* deg, int32_t* rp) {
+  const int64_t blocks = (int64_t(n) + kRadixTile - 1) / kRadixTile;
+  DevBuf k0, k1, v1, counts, offs;
+  GW_TRY(k0.ensure(static_cast<size_t>(n) * sizeof(uint32_t), 0));
+  GW_TRY(k1.ensure(static_cast<size_t>(n) * sizeof(uint32_t), 0));
+  GW_TRY(v1.ensure(static_cast<size_t>(n) * sizeof(int32_t), 0));
+  GW_TRY(counts.ensure(static_cast<size_t>(blocks) * 256 * sizeof(uint32_t), 0));
+  GW_TRY(offs.ensure(static_cast<size_t>(blocks) * 256 * sizeof(uint32_t), 0));
+  degree_key_kernel<<<grid_for(n), 256>>>(raw_rp, n, dmax, k0.as<uint32_t>());
+  GW_KCHECK();
+  int bits = 0;
+  while (bits < 32 && (static_cast<uint32_t>(dmax) >> bits) != 0) ++bits;
+  const int passes = std::max(1, (bits + 7) / 8);
+  // ping-pong so that the last pass writes perm: passes odd -> k0/perm first
+  uint32_t* kin = k0.as<uint32_t>();
+  const int32_t* vin = nullptr;
+  for (int ps = 0; ps < passes; ++ps) {
+    const bool last_to_perm = ((passes - 1 - ps) % 2) == 0;
+    uint32_t* kout = (kin == k0.as<uint32_t>()) ? k1.as<uint32_t>() : k0.as<uint32_t>();
+    int32_t* vout = last_to_perm ? perm : v1.as<int32_t>();
+    radix_count_kernel<<<static_cast<int>(blocks), kRadixThreads>>>(kin, n, 8 * ps, counts.as<uint32_t>());
+    GW_KCHECK();
+    GW_TRY(exclusive_scan(counts.as<uint32_t>(), blocks * 256, offs.as<uint32_t>(), nullptr));
+    radix_scatter_kernel<<<static_cast<int>(blocks), kRadixThreads>>>(kin, vin, n, 8 * ps, offs.as<uint32_t>(), kout,
+                                                                      vout);
+    GW_KCHECK();
+    kin = kout;
+    vin = vout;
+  }
+  perm_finish_kernel<<<grid_for(n), 256>>>(perm, kin, n, dmax, inv, reinterpret_cast<uint32_t*>(deg));
+  GW_KCHECK();
+  GW_TRY(exclusive_scan(reinterpret_cast<const uint32_t*>(deg), n, reinterpret_cast<uint32_t*>(rp),
+                        reinterpret_cast<uint32_t*>(rp + n)));
+  return GEDWALK_OK;
+}
+
+// Sorts segments of the relabelled CSR (one warp per segment of at most 1024 entries): the
+// 1024-entry pieces of rows longer than that (listed in seg; those rows are summed slice by slice
+// anyway), then the whole rows [r0, r1). Ascending neighbour ids put the high-degree neighbours,
+// the most gathered rows, first in every row. A bitonic network: in registers up to 32 entries,
+// in the warp's shared memory above.
 constexpr int kSortSeg = 1024;
 __global__ void __launch_bounds__(256) sort_segments_kernel(const int2* __restrict__ seg, int64_t nseg,
+                                                            const int32_t* __restrict__ rp, int32_t r0, int32_t r1,
                                                             int32_t* __restrict__ ci) {
   __shared__ int32_t buf[8][kSortSeg];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t warps = (int64_t(gridDim.x) * blockDim.x) >> 5;
-  for (int64_t sidx = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; sidx < nseg; sidx += warps) {
-    const int2 sg = seg[sidx];
+  const int64_t total = nseg + (r1 - r0);
+  for (int64_t sidx = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; sidx < total; sidx += warps) {
+    int2 sg;
+    if (sidx < nseg) {
+      sg = seg[sidx];
+    } else {
+      const int32_t r = r0 + static_cast<int32_t>(sidx - nseg);
+      sg = make_int2(rp[r], rp[r + 1] - rp[r]);
+    }
+    if (sg.y <= 1) continue;
     int32_t* p = ci + sg.x;
     const int len = sg.y;
     if (len <= 32) {
@@ -386,18 +606,74 @@ static int row_class(int32_t d) {
   return cls;
 }
 
+static gedwalk_status finish_plan(Plan& plan, const std::vector<int4>& units, const std::vector<int4>& heavy) {
+  plan.num_units = static_cast<int32_t>(units.size());
+  plan.num_slots = plan.num_units + plan.num_heavy;
+  GW_TRY(plan.units.ensure(units.size() * sizeof(int4) + 16, 0));
+  GW_TRY(plan.heavy.ensure(heavy.size() * sizeof(int4) + 16, 0));
+  if (!units.empty()) GW_CUDA(cudaMemcpy(plan.units.p, units.data(), units.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  if (!heavy.empty()) GW_CUDA(cudaMemcpy(plan.heavy.p, heavy.data(), heavy.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  return GEDWALK_OK;
+}
+
 // Work units of one CSR. Heavy rows (degree > kHeavyDeg) are cut into slices wherever they sit;
 // the other rows [0, n_active) form contiguous runs of one degree class. Rows from n_active on have
 // no units (isolated vertices: nothing gathers them). With rows sorted by decreasing degree (the
 // relabelled forward CSR) the heavy rows are the prefix and every class is one contiguous run; the
 // reverse CSR of a directed graph keeps the forward order, so its runs are shorter.
+// With `sorted` (the forward CSR) the runs are found by binary search over degrees and row
+// pointers; otherwise the rows are walked one by one.
 static gedwalk_status build_plan(Plan& plan, const std::vector<int32_t>& deg, const std::vector<int32_t>& rp,
-                                 int32_t n_active, int32_t n) {
+                                 int32_t n_active, int32_t n, bool sorted) {
+  if (!sorted) {
+    std::vector<int4> units, heavy;
+    int32_t slice = 0;
+    for (int32_t r = 0; r < n_active; ++r) {
+      const int32_t d = deg[r];
+      if (d <= kHeavyDeg) continue;
+      const int32_t ns = (d + kSliceEdges - 1) / kSliceEdges;
+      const int32_t hi = static_cast<int32_t>(heavy.size());
+      heavy.push_back(make_int4(r, slice, ns, 0));
+      for (int32_t k = 0; k < ns; ++k) {
+        const int32_t e0 = rp[r] + static_cast<int32_t>(static_cast<int64_t>(d) * k / ns);
+        const int32_t e1 = rp[r] + static_cast<int32_t>(static_cast<int64_t>(d) * (k + 1) / ns);
+        units.push_back(make_int4(hi, e0, e1, slice + k));
+      }
+      slice += ns;
+    }
+    plan.num_slices = slice;
+    plan.num_heavy = static_cast<int32_t>(heavy.size());
+    int32_t r = 0;
+    while (r < n_active) {
+      if (deg[r] > kHeavyDeg) {
+        ++r;
+        continue;
+      }
+      const int cls = row_class(deg[r]);
+      // a short-row unit takes up to kUnitRowsMax rows; on small graphs fewer, down to one
+      // iteration of its warp (2 rows per lane group), so that every SM gets work
+      const int32_t iter_rows = cls == 6 ? 1 : 2 * (32 >> cls);
+      const int32_t small_cap = std::max<int32_t>(iter_rows, n_active / kTargetUnits);
+      const int32_t max_rows = std::min<int32_t>(cls == 6 ? 32 : kUnitRowsMax, small_cap);
+      const int64_t max_edges = cls == 6 ? kLongUnitEdges : kUnitEdges;
+      int32_t r1 = r;
+      int64_t edges = 0;
+      while (r1 < n_active && deg[r1] <= kHeavyDeg && row_class(deg[r1]) == cls && r1 - r < max_rows &&
+             (r1 == r || edges + deg[r1] <= max_edges)) {
+        edges += deg[r1];
+        ++r1;
+      }
+      units.push_back(make_int4(r, r1, cls, -1));
+      r = r1;
+    }
+    return finish_plan(plan, units, heavy);
+  }
+  // rows are ordered by decreasing degree: the heavy rows form a prefix, then runs of one class
   std::vector<int4> units, heavy;
   int32_t slice = 0;
-  for (int32_t r = 0; r < n_active; ++r) {
+  int32_t r = 0;
+  for (; r < n_active && deg[r] > kHeavyDeg; ++r) {
     const int32_t d = deg[r];
-    if (d <= kHeavyDeg) continue;
     const int32_t ns = (d + kSliceEdges - 1) / kSliceEdges;
     const int32_t hi = static_cast<int32_t>(heavy.size());
     heavy.push_back(make_int4(r, slice, ns, 0));
@@ -410,37 +686,31 @@ static gedwalk_status build_plan(Plan& plan, const std::vector<int32_t>& deg, co
   }
   plan.num_slices = slice;
   plan.num_heavy = static_cast<int32_t>(heavy.size());
-  int32_t r = 0;
   while (r < n_active) {
-    if (deg[r] > kHeavyDeg) {
-      ++r;
-      continue;
-    }
     const int cls = row_class(deg[r]);
+    // the run of this class: classes do not increase along the rows
+    const int32_t cls_end = static_cast<int32_t>(
+        std::partition_point(deg.begin() + r, deg.begin() + n_active, [&](int32_t d) { return row_class(d) == cls; }) -
+        deg.begin());
     // a short-row unit takes up to kUnitRowsMax rows; on small graphs fewer, down to one
     // iteration of its warp (2 rows per lane group), so that every SM gets work
     const int32_t iter_rows = cls == 6 ? 1 : 2 * (32 >> cls);
     const int32_t small_cap = std::max<int32_t>(iter_rows, n_active / kTargetUnits);
     const int32_t max_rows = std::min<int32_t>(cls == 6 ? 32 : kUnitRowsMax, small_cap);
     const int64_t max_edges = cls == 6 ? kLongUnitEdges : kUnitEdges;
-    int32_t r1 = r;
-    int64_t edges = 0;
-    while (r1 < n_active && deg[r1] <= kHeavyDeg && row_class(deg[r1]) == cls && r1 - r < max_rows &&
-           (r1 == r || edges + deg[r1] <= max_edges)) {
-      edges += deg[r1];
-      ++r1;
+    while (r < cls_end) {
+      // the most rows from r whose entries stay within max_edges (at least one row)
+      const int64_t cap = static_cast<int64_t>(rp[r]) + max_edges;
+      const auto it = std::upper_bound(rp.begin() + r + 1, rp.begin() + cls_end + 1, cap,
+                                       [](int64_t c, int32_t x) { return c < x; });
+      int32_t r1 = static_cast<int32_t>(it - rp.begin()) - 1;
+      r1 = std::max(r + 1, std::min({r1, r + max_rows, cls_end}));
+      units.push_back(make_int4(r, r1, cls, -1));
+      r = r1;
     }
-    units.push_back(make_int4(r, r1, cls, -1));
-    r = r1;
   }
   (void)n;
-  plan.num_units = static_cast<int32_t>(units.size());
-  plan.num_slots = plan.num_units + plan.num_heavy;
-  GW_TRY(plan.units.ensure(units.size() * sizeof(int4) + 16, 0));
-  GW_TRY(plan.heavy.ensure(heavy.size() * sizeof(int4) + 16, 0));
-  if (!units.empty()) GW_CUDA(cudaMemcpy(plan.units.p, units.data(), units.size() * sizeof(int4), cudaMemcpyHostToDevice));
-  if (!heavy.empty()) GW_CUDA(cudaMemcpy(plan.heavy.p, heavy.data(), heavy.size() * sizeof(int4), cudaMemcpyHostToDevice));
-  return GEDWALK_OK;
+  return finish_plan(plan, units, heavy);
 }
 
 // ---------------------------------------------------------------- small kernels
@@ -466,7 +736,6 @@ __global__ void first_crossing_kernel(const double* Wa, int32_t lo, int32_t rows
   *out_b = b;
 }
 
-static int grid_for(int64_t n) { return static_cast<int>(std::min<int64_t>((n + 255) / 256, 152 * 16)); }
 
 SweepArgs base_args(Graph& g, Workspace& ws) {
   SweepArgs a{};
@@ -1010,66 +1279,74 @@ static gedwalk_status upload_impl(const int32_t* row_ptr, const int32_t* col_idx
   // vertex with no arc at all sorts last, so the isolated rows form the tail.
   g->perm.resize(n);
   g->inv.resize(n);
+  g->deg.resize(n);
+  std::vector<int32_t> rp(static_cast<size_t>(n) + 1);
+  GW_TRY(g->rp.ensure(rp.size() * sizeof(int32_t), 0));
+  const size_t ci_len = static_cast<size_t>(nnz) + 4;  // 4 zero pad entries for the vector loads at the end
+  GW_TRY(g->ci.ensure(ci_len * sizeof(int32_t), 0));
+  GW_TRY(g->perm_d.ensure(static_cast<size_t>(n) * sizeof(int32_t), 0));
+  DevBuf inv_d;
+  GW_TRY(inv_d.ensure(static_cast<size_t>(n) * sizeof(int32_t), 0));
   if (!directed) {
-    std::vector<int64_t> start(static_cast<size_t>(dmax) + 2, 0);  // stable counting sort
-    for (int32_t v = 0; v < n; ++v) start[dmax - deg_old[v] + 1]++;
-    for (size_t i = 1; i < start.size(); ++i) start[i] += start[i - 1];
-    for (int32_t v = 0; v < n; ++v) g->perm[start[dmax - deg_old[v]]++] = v;
+    // on the device: a stable radix sort by degree, the inverse, the new degrees and row pointers
+    DevBuf deg_d;
+    GW_TRY(deg_d.ensure(static_cast<size_t>(n) * sizeof(int32_t), 0));
+    GW_TRY(degree_order(raw_rp.as<int32_t>(), n, dmax, g->perm_d.as<int32_t>(), inv_d.as<int32_t>(),
+                        deg_d.as<int32_t>(), g->rp.as<int32_t>()));
+    GW_CUDA(cudaMemcpy(g->perm.data(), g->perm_d.p, static_cast<size_t>(n) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    GW_CUDA(cudaMemcpy(g->inv.data(), inv_d.p, static_cast<size_t>(n) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    GW_CUDA(cudaMemcpy(g->deg.data(), deg_d.p, static_cast<size_t>(n) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    GW_CUDA(cudaMemcpy(rp.data(), g->rp.p, rp.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
   } else {
     for (int32_t v = 0; v < n; ++v) g->perm[v] = v;
     std::stable_sort(g->perm.begin(), g->perm.end(), [&](int32_t a, int32_t b) {
       if (deg_old[a] != deg_old[b]) return deg_old[a] > deg_old[b];
       return rdeg_old[a] > rdeg_old[b];
     });
-  }
-  for (int32_t i = 0; i < n; ++i) g->inv[g->perm[i]] = i;
-  g->deg.resize(n);
-  std::vector<int32_t> rp(static_cast<size_t>(n) + 1);
-  rp[0] = 0;
-  for (int32_t i = 0; i < n; ++i) {
-    g->deg[i] = deg_old[g->perm[i]];
-    rp[i + 1] = rp[i] + g->deg[i];
+    for (int32_t i = 0; i < n; ++i) g->inv[g->perm[i]] = i;
+    rp[0] = 0;
+    for (int32_t i = 0; i < n; ++i) {
+      g->deg[i] = deg_old[g->perm[i]];
+      rp[i + 1] = rp[i] + g->deg[i];
+    }
+    GW_CUDA(cudaMemcpy(g->rp.p, rp.data(), rp.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    GW_CUDA(cudaMemcpy(g->perm_d.p, g->perm.data(), static_cast<size_t>(n) * sizeof(int32_t), cudaMemcpyHostToDevice));
+    GW_CUDA(cudaMemcpy(inv_d.p, g->inv.data(), static_cast<size_t>(n) * sizeof(int32_t), cudaMemcpyHostToDevice));
   }
   // rows from n_active on are isolated: no entry in either direction
   g->n_active = n;
   if (!directed) {
-    while (g->n_active > 0 && g->deg[g->n_active - 1] == 0) --g->n_active;
+    g->n_active = static_cast<int32_t>(
+        std::partition_point(g->deg.begin(), g->deg.end(), [](int32_t d) { return d > 0; }) - g->deg.begin());
   } else {
     while (g->n_active > 0 && g->deg[g->n_active - 1] == 0 && rdeg_old[g->perm[g->n_active - 1]] == 0) --g->n_active;
   }
-  GW_TRY(g->rp.ensure(rp.size() * sizeof(int32_t), 0));
-  const size_t ci_len = static_cast<size_t>(nnz) + 4;  // 4 zero pad entries for the vector loads at the end
-  GW_TRY(g->ci.ensure(ci_len * sizeof(int32_t), 0));
-  GW_TRY(g->perm_d.ensure(static_cast<size_t>(n) * sizeof(int32_t), 0));
-  GW_CUDA(cudaMemcpy(g->rp.p, rp.data(), rp.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-  GW_CUDA(cudaMemcpy(g->perm_d.p, g->perm.data(), static_cast<size_t>(n) * sizeof(int32_t), cudaMemcpyHostToDevice));
   {
-    DevBuf inv_d;
-    GW_TRY(inv_d.ensure(static_cast<size_t>(n) * sizeof(int32_t), 0));
-    GW_CUDA(cudaMemcpy(inv_d.p, g->inv.data(), static_cast<size_t>(n) * sizeof(int32_t), cudaMemcpyHostToDevice));
     GW_CUDA(cudaMemset(g->ci.as<int32_t>() + nnz, 0, 4 * sizeof(int32_t)));
     const int64_t blocks = std::min<int64_t>((static_cast<int64_t>(n) * 32 + 255) / 256, 152 * 32);
     relabel_kernel<<<static_cast<int>(blocks), 256>>>(raw_rp.as<int32_t>(), raw_ci.as<int32_t>(), g->rp.as<int32_t>(),
                                                       g->perm_d.as<int32_t>(), inv_d.as<int32_t>(), n,
                                                       g->ci.as<int32_t>());
     GW_KCHECK();
-    // sort each row (each 1024-entry piece of a longer row) by new id
+    // sort each row by new id: the rows are ordered by decreasing degree, so the rows above
+    // kSortSeg entries (sorted as 1024-entry pieces) are a prefix, and the others are sorted whole
+    const int32_t n_long = static_cast<int32_t>(
+        std::partition_point(g->deg.begin(), g->deg.begin() + g->n_active, [](int32_t d) { return d > kSortSeg; }) -
+        g->deg.begin());
     std::vector<int2> seg;
-    seg.reserve(static_cast<size_t>(g->n_active));
-    for (int32_t i = 0; i < n; ++i)
-      for (int32_t b = rp[i]; b < rp[i + 1]; b += kSortSeg) {
-        const int32_t len = std::min(kSortSeg, rp[i + 1] - b);
-        if (len > 1) seg.push_back(make_int2(b, len));
-      }
-    if (!seg.empty()) {
-      DevBuf seg_d;
-      GW_TRY(seg_d.ensure(seg.size() * sizeof(int2), 0));
+    for (int32_t i = 0; i < n_long; ++i)
+      for (int32_t b = rp[i]; b < rp[i + 1]; b += kSortSeg) seg.push_back(make_int2(b, std::min(kSortSeg, rp[i + 1] - b)));
+    DevBuf seg_d;
+    GW_TRY(seg_d.ensure(std::max<size_t>(seg.size(), 1) * sizeof(int2), 0));
+    if (!seg.empty())
       GW_CUDA(cudaMemcpy(seg_d.p, seg.data(), seg.size() * sizeof(int2), cudaMemcpyHostToDevice));
-      const int64_t sblocks = std::min<int64_t>((static_cast<int64_t>(seg.size()) * 32 + 255) / 256, 152 * 32);
+    const int64_t work = static_cast<int64_t>(seg.size()) + (g->n_active - n_long);
+    if (work > 0) {
+      const int64_t sblocks = std::min<int64_t>((work * 32 + 255) / 256, 152 * 32);
       sort_segments_kernel<<<static_cast<int>(sblocks), 256>>>(seg_d.as<int2>(), static_cast<int64_t>(seg.size()),
+                                                               g->rp.as<int32_t>(), n_long, g->n_active,
                                                                g->ci.as<int32_t>());
       GW_KCHECK();
-      GW_CUDA(cudaDeviceSynchronize());
     }
     GW_CUDA(cudaDeviceSynchronize());
   }
@@ -1087,7 +1364,7 @@ static gedwalk_status upload_impl(const int32_t* row_ptr, const int32_t* col_idx
     GW_CUDA(cudaMemcpy(g->rs_d.p, sd.data(), sd.size() * sizeof(double), cudaMemcpyHostToDevice));
     GW_CUDA(cudaMemcpy(g->rs_f.p, sf.data(), sf.size() * sizeof(float), cudaMemcpyHostToDevice));
   }
-  GW_TRY(build_plan(g->plan, g->deg, rp, g->n_active, n));
+  GW_TRY(build_plan(g->plan, g->deg, rp, g->n_active, n, true));
   if (directed) {
     // the reverse CSR (row v: the u with an arc u -> v), same ids, rows sorted
     g->deg_r.assign(n, 0);
@@ -1104,7 +1381,7 @@ static gedwalk_status upload_impl(const int32_t* row_ptr, const int32_t* col_idx
     GW_TRY(g->ci_r.ensure(cir.size() * sizeof(int32_t), 0));
     GW_CUDA(cudaMemcpy(g->rp_r.p, rpr.data(), rpr.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
     GW_CUDA(cudaMemcpy(g->ci_r.p, cir.data(), cir.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-    GW_TRY(build_plan(g->plan_r, g->deg_r, rpr, g->n_active, n));
+    GW_TRY(build_plan(g->plan_r, g->deg_r, rpr, g->n_active, n, false));
   }
   *out = reinterpret_cast<gedwalk_graph_t>(g.release());
   return GEDWALK_OK;

@@ -470,3 +470,51 @@ def test_device_loop_matches_host_loop(cuda_device, name, k, levels, prec, init)
     # the loop's graph is reused by the next call with the same configuration
     grp_r, gains_r, _, _ = G.maximize(k, device_loop=True, **kw)
     assert list(grp_r) == list(grp_d) and np.array_equal(gains_r, gains_d)
+
+
+def _relabel_case(kind):
+    # Graphs that take the device relabelling through one, two and three 8-bit radix passes
+    # (d_max < 256, < 65536, >= 65536), with vertices of equal degree far apart, rows cut into
+    # 1024-entry sorting pieces, and isolated vertices spread over the caller ids (their rows must
+    # stay in increasing caller id, the order the zero-gain picks rely on).
+    rng = np.random.default_rng({"one": 11, "two": 12, "three": 13}[kind])
+    n = {"one": 5000, "two": 9000, "three": 85_000}[kind]
+    hub_deg = {"one": 200, "two": 3000, "three": 70_000}[kind]
+    iso = set(range(3, n, 7))
+    live = [v for v in range(n) if v not in iso and v != 5]
+    edges = set()
+    for u in rng.choice(live, size=hub_deg, replace=False):  # hub 5
+        edges.add((5, int(u)))
+    a = rng.choice(live, size=2 * n)  # sparse random edges among the others
+    b = rng.choice(live, size=2 * n)
+    for x, y in zip(a.tolist(), b.tolist()):
+        if x != y:
+            edges.add((min(x, y), max(x, y)))
+    return gg.from_edges(n, sorted(edges))
+
+
+@pytest.mark.parametrize("kind", ["one", "two", "three"])
+def test_device_relabel_radix_passes(cuda_device, kind):
+    from paper_1910_13874_gb300 import gedwalk
+
+    g = _relabel_case(kind)
+    G = gedwalk.Graph.from_host(g)
+    alpha = oracle.default_alpha(g)
+    deg = np.diff(g.row_ptr)
+    assert G.dmax == int(deg.max())
+    S = np.array([5, 1, 2, 8, 13], dtype=np.int32)
+    score, L, _ = G.score(S, precision="fp64", epsilon=1e-6)
+    assert rel(score, oracle.score(g, S, alpha, L)) < 1e-12
+    k = 6
+    grp, gains, _, L = G.maximize(k, precision="fp64", epsilon=1e-4)
+    ogrp, ogains, _ = oracle.greedy(g, k, alpha, L, "lazy")
+    check_sequence(grp, gains, 1e-12, ogrp, ogains, *oracle_greedy_checker(oracle, g, alpha, L))
+    # every isolated vertex has gain 0
+    all_g, _ = G.gains([], precision="fp64", epsilon=1e-4)
+    assert np.all(all_g[deg == 0] == 0.0)
+    # with every vertex that has an edge in S, only isolated vertices are left: the picks are the
+    # lowest caller ids among them (the isolated rows keep increasing caller ids)
+    live = np.flatnonzero(deg > 0).astype(np.int32)
+    grp2, gains2, _, _ = G.maximize(3, precision="fp32", epsilon=1e-4, init=live)
+    assert list(grp2) == [int(x) for x in np.flatnonzero(deg == 0)[:3]] and np.all(gains2 == 0.0)
+    G.free()
