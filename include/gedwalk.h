@@ -289,7 +289,9 @@ GEDWALK_API gedwalk_status gedwalk_gains(gedwalk_graph_t g, const int32_t* S, in
  *  k >= 0 and init_len + k <= n.
  *  group: host int32[k], the added vertices in order.
  *  gains: host double[k], the gain of each addition (may be NULL).
- *  score: GED_{<=L} of init + group (may be NULL).
+ *  score: GED_{<=L} of init + group (may be NULL). Without an init group (and
+ *         without GEDWALK_ADAPTIVE_L) it is the sum of the gains: each gain is
+ *         GED_{<=L}(S + c) - GED_{<=L}(S), and GED_{<=L} of the empty set is 0.
  *  L_used: may be NULL.
  *  init_group/init_len: resume from this prefix group (may be NULL/0).
  * GEDWALK_GAINS_ALL in params->flags evaluates every vertex at every step.

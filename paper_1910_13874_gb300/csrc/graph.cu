@@ -217,11 +217,19 @@ gedwalk_status Workspace::ensure_pinned(size_t need) {
 
 // First malformed row (or -1) and a reason.
 // Entry checks of an uploaded CSR: column in range, and (full) no self-loop, strictly increasing
-// rows and (symmetric) the reverse entry present, by binary search in the other row. The smallest
-// offending (row << 3 | kind) wins. Entries [b, e) of row v, whose row starts at r0.
+// rows and (symmetric) every entry mirrored. The smallest offending (row << 3 | kind) wins.
+// Entries [b, e) of row v, whose row starts at r0.
+// Symmetry: order the vertices by (degree, id). An entry (v, u) is "down" when u comes before v;
+// only down entries look for their mirror (v in row u, the shorter row, by binary search), and
+// counts[0] / counts[1] receive the numbers of down / up entries. The mirror of a down entry is an
+// up entry and distinct entries have distinct mirrors (rows have no repeats), so if every down
+// entry is mirrored and the two counts agree, the mirrors are all the up entries: the CSR is
+// symmetric. all_up = 1 checks every entry (locates the row after the counts disagreed).
 __device__ __forceinline__ void check_entries(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                              int32_t n, int full, int symmetric, int64_t v, int32_t r0, int32_t b,
-                                              int32_t e, int lane, unsigned long long* __restrict__ bad) {
+                                              int32_t n, int full, int symmetric, int all_up, int64_t v, int32_t r0,
+                                              int32_t b, int32_t e, int32_t dv, int lane,
+                                              unsigned long long* __restrict__ bad, unsigned long long& down,
+                                              unsigned long long& up) {
   for (int32_t j = b + lane; j < e; j += 32) {
     const int32_t u = ci[j];
     int k = 0;
@@ -234,12 +242,19 @@ __device__ __forceinline__ void check_entries(const int32_t* __restrict__ rp, co
         k = 3;
       } else if (symmetric) {
         int32_t lo = rp[u], hi = rp[u + 1];
-        while (lo < hi) {  // first entry of row u that is >= v
-          const int32_t mid = lo + ((hi - lo) >> 1);
-          if (ci[mid] < v) lo = mid + 1;
-          else hi = mid;
+        const int32_t du = hi - lo;
+        const bool is_down = du < dv || (du == dv && u < v);
+        if (is_down) ++down;
+        else ++up;
+        if (is_down || all_up) {
+          const int32_t end = hi;
+          while (lo < hi) {  // first entry of row u that is >= v
+            const int32_t mid = lo + ((hi - lo) >> 1);
+            if (ci[mid] < v) lo = mid + 1;
+            else hi = mid;
+          }
+          if (lo == end || ci[lo] != v) k = 4;
         }
-        if (lo == rp[u + 1] || ci[lo] != v) k = 4;
       }
     }
     if (k) atomicMin(bad, (static_cast<unsigned long long>(v) << 3) | static_cast<unsigned long long>(k));
@@ -250,18 +265,31 @@ __device__ __forceinline__ void check_entries(const int32_t* __restrict__ rp, co
 // ({row, first entry, end}), so that no warp walks a hub row alone.
 constexpr int32_t kCheckPiece = 1024;
 __global__ void validate_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, int32_t n,
-                                int full, int symmetric, const int4* __restrict__ pieces, int64_t npieces,
-                                unsigned long long* __restrict__ bad) {
+                                int full, int symmetric, int all_up, const int4* __restrict__ pieces, int64_t npieces,
+                                unsigned long long* __restrict__ bad, unsigned long long* __restrict__ counts) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  unsigned long long down = 0, up = 0;
   for (int64_t w = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; w < n + npieces; w += warps) {
     if (w < n) {
       const int32_t b = rp[w], e = rp[w + 1];
-      if (e - b <= kCheckPiece) check_entries(rp, ci, n, full, symmetric, w, b, b, e, lane, bad);
+      if (e - b <= kCheckPiece)
+        check_entries(rp, ci, n, full, symmetric, all_up, w, b, b, e, e - b, lane, bad, down, up);
     } else {
       const int4 pc = pieces[w - n];
-      check_entries(rp, ci, n, full, symmetric, pc.x, rp[pc.x], pc.y, pc.z, lane, bad);
+      const int32_t r0 = rp[pc.x];
+      check_entries(rp, ci, n, full, symmetric, all_up, pc.x, r0, pc.y, pc.z, rp[pc.x + 1] - r0, lane, bad, down,
+                    up);
     }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    down += __shfl_xor_sync(0xffffffffu, down, o);
+    up += __shfl_xor_sync(0xffffffffu, up, o);
+  }
+  if (lane == 0 && (down | up)) {
+    atomicAdd(counts, down);
+    atomicAdd(counts + 1, up);
   }
 }
 
@@ -548,7 +576,7 @@ __global__ void __launch_bounds__(256) sort_segments_kernel(const int2* __restri
 // Validates a CSR: row_ptr on the host (the kernels index with it), the entries on the device
 // (drp/dci: copies of the same arrays). Returns the first offending row or -1.
 static int64_t validate_csr(const int32_t* rp, const int32_t* drp, const int32_t* dci, int32_t n, int64_t nnz,
-                            bool full, std::string* why, bool symmetric, gedwalk_status* st) {
+                            bool full, std::string* why, bool symmetric, gedwalk_status* st, int32_t* dmax_out) {
   *st = GEDWALK_OK;
   if (rp[0] != 0) {
     *why = "row_ptr[0] != 0";
@@ -558,42 +586,53 @@ static int64_t validate_csr(const int32_t* rp, const int32_t* drp, const int32_t
     *why = "row_ptr[n] != nnz";
     return n;
   }
-  for (int32_t v = 0; v < n; ++v)
-    if (rp[v + 1] < rp[v]) {
+  // one pass: monotone row pointers, the largest degree, the pieces of rows above kCheckPiece
+  std::vector<int4> pieces;  // rows above kCheckPiece entries, cut into pieces
+  int32_t dmax = 0;
+  for (int32_t v = 0; v < n; ++v) {
+    const int32_t d = rp[v + 1] - rp[v];
+    if (d < 0) {
       *why = "row_ptr decreases";
       return v;
     }
-  if (nnz == 0) return -1;
-  std::vector<int4> pieces;  // rows above kCheckPiece entries, cut into pieces
-  for (int32_t v = 0; v < n; ++v)
-    if (rp[v + 1] - rp[v] > kCheckPiece)
+    dmax = std::max(dmax, d);
+    if (d > kCheckPiece)
       for (int32_t b = rp[v]; b < rp[v + 1]; b += kCheckPiece)
         pieces.push_back(make_int4(v, b, std::min(rp[v + 1], b + kCheckPiece), 0));
+  }
+  *dmax_out = dmax;
+  if (nnz == 0) return -1;
   DevBuf dbad, dpieces;
-  unsigned long long hbad = ~0ull;
+  unsigned long long hbad[3] = {~0ull, 0ull, 0ull};  // worst entry, down and up counts
   if ((*st = dbad.ensure(sizeof(hbad), 0)) != GEDWALK_OK) return -1;
   if ((*st = dpieces.ensure(std::max<size_t>(pieces.size(), 1) * sizeof(int4), 0)) != GEDWALK_OK) return -1;
-  cudaError_t e = cudaMemcpy(dbad.p, &hbad, sizeof(hbad), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && !pieces.empty())
-    e = cudaMemcpy(dpieces.p, pieces.data(), pieces.size() * sizeof(int4), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) {
-    const int64_t work = static_cast<int64_t>(n) + static_cast<int64_t>(pieces.size());
-    const int64_t blocks = std::min<int64_t>((work * 32 + 255) / 256, 152 * 32);
-    validate_kernel<<<static_cast<int>(blocks), 256>>>(drp, dci, n, full ? 1 : 0, symmetric ? 1 : 0,
+  cudaError_t e = cudaSuccess;
+  if (!pieces.empty()) e = cudaMemcpy(dpieces.p, pieces.data(), pieces.size() * sizeof(int4), cudaMemcpyHostToDevice);
+  const int64_t work = static_cast<int64_t>(n) + static_cast<int64_t>(pieces.size());
+  const int64_t blocks = std::min<int64_t>((work * 32 + 255) / 256, 152 * 32);
+  // first the down entries only; if every one is mirrored but the counts disagree, every entry
+  for (int all_up = 0; all_up < 2 && e == cudaSuccess; ++all_up) {
+    hbad[0] = ~0ull;
+    hbad[1] = hbad[2] = 0;
+    e = cudaMemcpy(dbad.p, hbad, sizeof(hbad), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) break;
+    validate_kernel<<<static_cast<int>(blocks), 256>>>(drp, dci, n, full ? 1 : 0, symmetric ? 1 : 0, all_up,
                                                        dpieces.as<int4>(), static_cast<int64_t>(pieces.size()),
-                                                       dbad.as<unsigned long long>());
+                                                       dbad.as<unsigned long long>(),
+                                                       dbad.as<unsigned long long>() + 1);
     e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpy(hbad, dbad.p, sizeof(hbad), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess || hbad[0] != ~0ull || !full || !symmetric || hbad[1] == hbad[2]) break;
   }
-  if (e == cudaSuccess) e = cudaMemcpy(&hbad, dbad.p, sizeof(hbad), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) {
     *st = fail(GEDWALK_ERR_DEVICE, "CSR validation: %s", cudaGetErrorString(e));
     return -1;
   }
   static const char* reasons[] = {"", "column index out of range", "self-loop", "row not strictly increasing",
                                   "graph is not symmetric (undirected graphs only)"};
-  if (hbad != ~0ull) {
-    *why = reasons[hbad & 7];
-    return static_cast<int64_t>(hbad >> 3);
+  if (hbad[0] != ~0ull) {
+    *why = reasons[hbad[0] & 7];
+    return static_cast<int64_t>(hbad[0] >> 3);
   }
   return -1;
 }
@@ -1040,7 +1079,16 @@ gedwalk_status truncation_length(Graph& g, double alpha, double eps, int32_t* L,
       return GEDWALK_OK;
     }
     if (rows >= kCap) return fail(GEDWALK_ERR_INVALID, "no truncation length <= %d reaches epsilon %g", kCap, eps);
-    rows = std::min(rows * 2, kCap);
+    // B_l = coef W_l shrinks about geometrically once the walks spread: predict the first l below
+    // eps from the last ratio W_{l}/W_{l-1}, so that few rows beyond L are computed (each row is
+    // one FP64 sweep); without a shrinking ratio, double
+    int32_t next = std::min(rows * 2, kCap);
+    const double w1 = g.Wa[rows - 1], w0 = g.Wa[rows - 2], b1 = coef * w1;
+    if (w0 > 0.0 && w1 > 0.0 && w1 < w0 && b1 > 0.0 && std::isfinite(b1)) {
+      const double m = std::ceil(std::log(eps / b1) / std::log(w1 / w0));
+      if (m >= 1.0 && m < kCap) next = static_cast<int32_t>(std::min<double>(kCap, rows + m));
+    }
+    rows = std::max(rows + 1, next);
   }
 }
 
@@ -1211,6 +1259,7 @@ static gedwalk_status upload_impl(const int32_t* row_ptr, const int32_t* col_idx
   if (directed && weighted) return fail(GEDWALK_ERR_INVALID, "weighted directed graphs are not supported");
   std::string why;
   const bool trusted = (flags & GEDWALK_UPLOAD_TRUSTED) != 0;
+  int32_t dmax = 0;  // the largest row length (found while the row pointers are checked)
   // the caller's CSR on the device: validated there, then relabelled there
   DevBuf raw_rp, raw_ci;
   GW_TRY(raw_rp.ensure((static_cast<size_t>(n) + 1) * sizeof(int32_t), 0));
@@ -1223,7 +1272,7 @@ static gedwalk_status upload_impl(const int32_t* row_ptr, const int32_t* col_idx
     // them); TRUSTED skips the sortedness, self-loop and symmetry checks
     gedwalk_status vst = GEDWALK_OK;
     const int64_t bad = validate_csr(row_ptr, raw_rp.as<int32_t>(), raw_ci.as<int32_t>(), n, nnz, !trusted, &why,
-                                     !directed, &vst);
+                                     !directed, &vst, &dmax);
     if (vst != GEDWALK_OK) return vst;
     if (bad >= 0)
       return fail(GEDWALK_ERR_INVALID, "malformed graph at row %lld: %s", static_cast<long long>(bad), why.c_str());
@@ -1233,12 +1282,12 @@ static gedwalk_status upload_impl(const int32_t* row_ptr, const int32_t* col_idx
   g->n = n;
   g->nnz = nnz;
   g->directed = directed;
-  // degrees by caller id: the rows' own lengths; for a directed graph also the reverse (in) degree
-  std::vector<int32_t> deg_old(n), rdeg_old;
-  int32_t dmax = 0;
-  for (int32_t v = 0; v < n; ++v) {
-    deg_old[v] = row_ptr[v + 1] - row_ptr[v];
-    dmax = std::max(dmax, deg_old[v]);
+  // degrees by caller id (weighted and directed graphs): the rows' own lengths; for a directed
+  // graph also the reverse (in) degree
+  std::vector<int32_t> deg_old, rdeg_old;
+  if (weighted || directed) {
+    deg_old.resize(n);
+    for (int32_t v = 0; v < n; ++v) deg_old[v] = row_ptr[v + 1] - row_ptr[v];
   }
   int32_t rdmax = 0;
   if (directed) {

@@ -1372,6 +1372,21 @@ gedwalk_status maximize_impl(Graph& g, Workspace& ws, int32_t k, const Resolved&
 
   // The plain greedy with lookahead runs as one CUDA graph (device-resident loop); the others keep
   // the host loop below.
+  // GED_{<=L} of the final group. From an empty start it is the sum of the picks' exact gains
+  // g_L(S_j, c_j) = GED_{<=L}(S_j + c_j) - GED_{<=L}(S_j), telescoping from GED_{<=L}(empty) = 0;
+  // otherwise (an init group, or gains at shorter walk lengths) two-state sweeps over the group.
+  auto group_score = [&](const std::vector<int32_t>& S_fin) -> gedwalk_status {
+    if (init_int.empty() && !adaptive && gains) {
+      double v = 0.0;
+      for (int32_t j = 0; j < k; ++j) v += gains[j];
+      *score = v;
+      return GEDWALK_OK;
+    }
+    double v = 0;
+    GW_TRY(score_one(g, ws, S_fin, r, &v));
+    *score = v;
+    return GEDWALK_OK;
+  };
   bool device_loop = uses_device_loop(g, shape, flags, k);
   if (device_loop) {
     bool launched = false;
@@ -1387,11 +1402,7 @@ gedwalk_status maximize_impl(Graph& g, Workspace& ws, int32_t k, const Resolved&
   if (device_loop) {
     std::vector<int32_t> S_dev = init_int;
     for (int32_t j = 0; j < k; ++j) S_dev.push_back(g.inv[group[j]]);
-    if (score) {
-      double v = 0;
-      GW_TRY(score_one(g, ws, S_dev, r, &v));
-      *score = v;
-    }
+    if (score) GW_TRY(group_score(S_dev));
     GW_CUDA(cudaStreamSynchronize(s));
     guard.ok = true;
     return GEDWALK_OK;
@@ -1568,11 +1579,7 @@ gedwalk_status maximize_impl(Graph& g, Workspace& ws, int32_t k, const Resolved&
     }
   }
   ws.st_sweeps = c.sweeps;
-  if (score) {
-    double v = 0;
-    GW_TRY(score_one(g, ws, S_all, r, &v));
-    *score = v;
-  }
+  if (score) GW_TRY(group_score(S_all));
   GW_CUDA(cudaStreamSynchronize(s));
   guard.ok = true;
   return GEDWALK_OK;

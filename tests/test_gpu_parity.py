@@ -185,6 +185,21 @@ def test_upload_rejects_malformed_graphs(cuda_device):
         with pytest.raises(gedwalk.GedWalkError) as e:
             gedwalk.Graph(rp, ci)
         assert e.value.status == gedwalk.ERR_INVALID
+    # A missing mirror is found from the endpoint of smaller (degree, id) (row 0 above), or, when
+    # only the up/down entry counts disagree, by the full pass: here vertex 4 lists the hub 0, which
+    # does not list 4 back.
+    rp = np.array([0, 3, 4, 5, 6, 7], np.int32)
+    ci = np.array([1, 2, 3, 0, 0, 0, 0], np.int32)
+    with pytest.raises(gedwalk.GedWalkError) as e:
+        gedwalk.Graph(rp, ci)
+    assert e.value.status == gedwalk.ERR_INVALID and "row 4" in str(e.value) and "symmetric" in str(e.value)
+    with pytest.raises(gedwalk.GedWalkError) as e:
+        gedwalk.Graph(g.row_ptr, bad_sym)
+    assert "row 0" in str(e.value) and "symmetric" in str(e.value)
+    # the same lists pass when declared directed, and a symmetric star passes undirected
+    gedwalk.Graph(rp, ci, directed=True).free()
+    st = gg.star(40)
+    gedwalk.Graph(st.row_ptr, st.col_idx).free()
 
 
 # ------------------------------------------------------------------ exact gains of every vertex
