@@ -301,9 +301,12 @@ __device__ __forceinline__ void candidate_rows(const SweepArgs& a, const int* __
 // columns c0 .. c0+CPL-1; base is the first lane of the row's group. Every lane of the
 // warp calls it (shuffles inside); `store` marks the lanes that own distinct columns of a
 // valid row. acc accumulates this lane's column sums.
+// maybe_cand (warp-uniform): a candidate row may lie among the rows of this unit; otherwise the
+// per-row candidate test is skipped.
 template <typename T, int C, int MODE, int CPL>
 __device__ __forceinline__ void epilogue(const SweepArgs& a, const int* __restrict__ s_cand, int r, bool valid,
-                                         bool store, int c0, int base, T (&s)[CPL], ColAcc<T, CPL>& acc) {
+                                         bool store, int c0, int base, T (&s)[CPL], ColAcc<T, CPL>& acc,
+                                         bool maybe_cand) {
   T* Y = static_cast<T*>(a.Y);
   constexpr bool kMasked = MODE == MODE_SCORE || MODE == MODE_FUSED || MODE == MODE_CAND || MODE == MODE_LOOK;
   const bool inS = kMasked && valid ? in_mask(a.mask, r) : false;
@@ -336,7 +339,7 @@ __device__ __forceinline__ void epilogue(const SweepArgs& a, const int* __restri
     T y[CPL];
 #pragma unroll
     for (int k = 0; k < CPL; ++k) y[k] = inS ? T(0) : alpha * s[k];
-    if constexpr (Cands<MODE, C>::N > 0) {
+    if (Cands<MODE, C>::N > 0 && maybe_cand) {
       bool special = false;
 #pragma unroll
       for (int j = 0; j < Cands<MODE, C>::N; ++j) special |= s_cand[j] == r;
@@ -364,6 +367,15 @@ __device__ __forceinline__ void epilogue(const SweepArgs& a, const int* __restri
   }
 }
 
+// Whether a candidate row lies in rows [r0, r1) (the unit's rows).
+template <int MODE, int C>
+__device__ __forceinline__ bool unit_has_cand(const int* __restrict__ s_cand, int r0, int r1) {
+  bool any = false;
+#pragma unroll
+  for (int j = 0; j < Cands<MODE, C>::N; ++j) any |= s_cand[j] >= r0 && s_cand[j] < r1;
+  return any;
+}
+
 // Writes this lane's column sums (already reduced over the warp) to slot `slot`.
 template <int MODE, int C, int CPL>
 __device__ __forceinline__ void write_slot(const SweepArgs& a, size_t slot, int c0, const double (&cs)[CPL]) {
@@ -389,6 +401,7 @@ __device__ __forceinline__ void short_rows(const SweepArgs& a, const Src& src, c
   const int r0 = u.x, nrows = u.y - u.x;
   for (int i = lane; i <= nrows; i += 32) s_rp[i] = __ldcs(a.rp + r0 + i);
   __syncwarp();
+  const bool maybe_cand = unit_has_cand<MODE, C>(s_cand, r0, r0 + nrows);
   const int g = lane >> LW, gl = lane & (W - 1);
   const int base = lane & ~(W - 1);
   const int blk = gl & ((1 << SC::HS) - 1);
@@ -434,8 +447,8 @@ __device__ __forceinline__ void short_rows(const SweepArgs& a, const Src& src, c
       sa[k] = acca[k];
       sb[k] = accb[k];
     }
-    epilogue<T, C, MODE, CPL>(a, s_cand, r0 + ra, va, va && owner, c0, base, sa, acc);
-    epilogue<T, C, MODE, CPL>(a, s_cand, r0 + rb, vb, vb && owner, c0, base, sb, acc);
+    epilogue<T, C, MODE, CPL>(a, s_cand, r0 + ra, va, va && owner, c0, base, sa, acc, maybe_cand);
+    epilogue<T, C, MODE, CPL>(a, s_cand, r0 + rb, vb, vb && owner, c0, base, sb, acc, maybe_cand);
   }
   // sum the groups' copies of each column (non-owners hold zeros), in FP64
   double cs[CPL];
@@ -457,6 +470,7 @@ __device__ __forceinline__ void long_rows(const SweepArgs& a, const Src& src, co
   const int r0 = u.x, nrows = u.y - u.x;
   for (int i = lane; i <= nrows; i += 32) s_rp[i] = __ldcs(a.rp + r0 + i);
   __syncwarp();
+  const bool maybe_cand = unit_has_cand<MODE, C>(s_cand, r0, r0 + nrows);
   const int blk = lane & ((1 << SC::HS) - 1);
   const bool owner = (lane >> SC::HS) == 0;
   const int c0 = blk * CPL;
@@ -483,7 +497,7 @@ __device__ __forceinline__ void long_rows(const SweepArgs& a, const Src& src, co
     T s[CPL];
 #pragma unroll
     for (int k = 0; k < CPL; ++k) s[k] = acc[k];
-    epilogue<T, C, MODE, CPL>(a, s_cand, r0 + rr, true, owner, c0, 0, s, cacc);
+    epilogue<T, C, MODE, CPL>(a, s_cand, r0 + rr, true, owner, c0, 0, s, cacc, maybe_cand);
   }
   double cs[CPL];
 #pragma unroll
@@ -544,7 +558,7 @@ __device__ __forceinline__ void heavy_slice(const SweepArgs& a, const Src& src, 
     for (int k = 0; k < CPL; ++k) tot[k] += __ldcg(part + static_cast<size_t>(s) * C + c0 + k);
   ColAcc<T, CPL> cacc;
   cacc.zero();
-  epilogue<T, C, MODE, CPL>(a, s_cand, hr.x, true, owner, c0, 0, tot, cacc);
+  epilogue<T, C, MODE, CPL>(a, s_cand, hr.x, true, owner, c0, 0, tot, cacc, true);
   double cs[CPL];
 #pragma unroll
   for (int k = 0; k < CPL; ++k) cs[k] = cacc.get(k);
