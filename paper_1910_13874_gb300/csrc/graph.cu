@@ -293,6 +293,47 @@ __global__ void validate_kernel(const int32_t* __restrict__ rp, const int32_t* _
   }
 }
 
+// Row-pointer check of an uploaded CSR (rp[0] = 0 and rp[n] = nnz already hold): out[0] = the
+// first row whose pointer decreases (min over rows; all ones if none), out[1] = the largest row
+// length, out[2] = the number of kCheckPiece pieces of the longer rows.
+__global__ void rowptr_check_kernel(const int32_t* __restrict__ rp, int32_t n, unsigned long long* __restrict__ out) {
+  unsigned long long dmax = 0, pcs = 0;
+  for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t d = static_cast<int64_t>(rp[v + 1]) - rp[v];
+    if (d < 0) {
+      atomicMin(out, static_cast<unsigned long long>(v));
+    } else {
+      dmax = static_cast<unsigned long long>(d) > dmax ? static_cast<unsigned long long>(d) : dmax;
+      if (d > kCheckPiece) pcs += static_cast<unsigned long long>((d + kCheckPiece - 1) / kCheckPiece);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long m = __shfl_xor_sync(0xffffffffu, dmax, o);
+    dmax = m > dmax ? m : dmax;
+    pcs += __shfl_xor_sync(0xffffffffu, pcs, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (dmax) atomicMax(out + 1, dmax);
+    if (pcs) atomicAdd(out + 2, pcs);
+  }
+}
+
+// The pieces {row, first entry, end, 0} of the rows above kCheckPiece entries, in any order.
+__global__ void check_pieces_kernel(const int32_t* __restrict__ rp, int32_t n, unsigned long long* __restrict__ count,
+                                    int4* __restrict__ pieces) {
+  for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x) {
+    const int32_t b0 = rp[v], e = rp[v + 1];
+    if (e - b0 <= kCheckPiece) continue;
+    const int32_t np = (e - b0 + kCheckPiece - 1) / kCheckPiece;
+    const unsigned long long at = atomicAdd(count, static_cast<unsigned long long>(np));
+    for (int32_t k = 0; k < np; ++k) {
+      const int32_t b = b0 + k * kCheckPiece;
+      pieces[at + k] = make_int4(static_cast<int32_t>(v), b, min(e, b + kCheckPiece), 0);
+    }
+  }
+}
+
 // Relabelled CSR, one warp per new row i: the entries of old row perm[i], each mapped to its new
 // id, in their old order.
 __global__ void relabel_kernel(const int32_t* __restrict__ raw_rp, const int32_t* __restrict__ raw_ci,
@@ -586,29 +627,39 @@ static int64_t validate_csr(const int32_t* rp, const int32_t* drp, const int32_t
     *why = "row_ptr[n] != nnz";
     return n;
   }
-  // one pass: monotone row pointers, the largest degree, the pieces of rows above kCheckPiece
-  std::vector<int4> pieces;  // rows above kCheckPiece entries, cut into pieces
-  int32_t dmax = 0;
-  for (int32_t v = 0; v < n; ++v) {
-    const int32_t d = rp[v + 1] - rp[v];
-    if (d < 0) {
-      *why = "row_ptr decreases";
-      return v;
-    }
-    dmax = std::max(dmax, d);
-    if (d > kCheckPiece)
-      for (int32_t b = rp[v]; b < rp[v + 1]; b += kCheckPiece)
-        pieces.push_back(make_int4(v, b, std::min(rp[v + 1], b + kCheckPiece), 0));
-  }
-  *dmax_out = dmax;
-  if (nnz == 0) return -1;
+  // on the device: monotone row pointers, the largest degree, the pieces of rows above kCheckPiece
   DevBuf dbad, dpieces;
-  unsigned long long hbad[3] = {~0ull, 0ull, 0ull};  // worst entry, down and up counts
+  // first {first decreasing row, d_max, pieces}, then {worst entry, down and up entry counts}
+  unsigned long long hbad[3] = {~0ull, 0ull, 0ull};
   if ((*st = dbad.ensure(sizeof(hbad), 0)) != GEDWALK_OK) return -1;
-  if ((*st = dpieces.ensure(std::max<size_t>(pieces.size(), 1) * sizeof(int4), 0)) != GEDWALK_OK) return -1;
-  cudaError_t e = cudaSuccess;
-  if (!pieces.empty()) e = cudaMemcpy(dpieces.p, pieces.data(), pieces.size() * sizeof(int4), cudaMemcpyHostToDevice);
-  const int64_t work = static_cast<int64_t>(n) + static_cast<int64_t>(pieces.size());
+  cudaError_t e = cudaMemcpy(dbad.p, hbad, sizeof(hbad), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    rowptr_check_kernel<<<grid_for(n), 256>>>(drp, n, dbad.as<unsigned long long>());
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(hbad, dbad.p, sizeof(hbad), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    *st = fail(GEDWALK_ERR_DEVICE, "CSR validation: %s", cudaGetErrorString(e));
+    return -1;
+  }
+  if (hbad[0] != ~0ull) {
+    *why = "row_ptr decreases";
+    return static_cast<int64_t>(hbad[0]);
+  }
+  *dmax_out = static_cast<int32_t>(hbad[1]);
+  if (nnz == 0) return -1;
+  const int64_t npieces = static_cast<int64_t>(hbad[2]);
+  if ((*st = dpieces.ensure(std::max<size_t>(static_cast<size_t>(npieces), 1) * sizeof(int4), 0)) != GEDWALK_OK)
+    return -1;
+  if (npieces > 0) {
+    hbad[2] = 0;
+    e = cudaMemcpy(dbad.as<unsigned long long>() + 2, &hbad[2], sizeof(hbad[2]), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+      check_pieces_kernel<<<grid_for(n), 256>>>(drp, n, dbad.as<unsigned long long>() + 2, dpieces.as<int4>());
+      e = cudaGetLastError();
+    }
+  }
+  const int64_t work = static_cast<int64_t>(n) + npieces;
   const int64_t blocks = std::min<int64_t>((work * 32 + 255) / 256, 152 * 32);
   // first the down entries only; if every one is mirrored but the counts disagree, every entry
   for (int all_up = 0; all_up < 2 && e == cudaSuccess; ++all_up) {
@@ -617,7 +668,7 @@ static int64_t validate_csr(const int32_t* rp, const int32_t* drp, const int32_t
     e = cudaMemcpy(dbad.p, hbad, sizeof(hbad), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) break;
     validate_kernel<<<static_cast<int>(blocks), 256>>>(drp, dci, n, full ? 1 : 0, symmetric ? 1 : 0, all_up,
-                                                       dpieces.as<int4>(), static_cast<int64_t>(pieces.size()),
+                                                       dpieces.as<int4>(), npieces,
                                                        dbad.as<unsigned long long>(),
                                                        dbad.as<unsigned long long>() + 1);
     e = cudaGetLastError();
@@ -851,11 +902,20 @@ gedwalk_status ensure_totals(Graph& g, double alpha, int32_t rows, cudaStream_t 
     g.ttab.swap(fresh);
     GW_CUDA(cudaStreamSynchronize(s));
   }
+  if (g.Wa_d.bytes < static_cast<size_t>(rows) * sizeof(double)) {
+    // grow the device sums, keeping the rows already computed
+    DevBuf fresh;
+    GW_TRY(fresh.ensure(static_cast<size_t>(std::max(rows, 64)) * sizeof(double), s));
+    if (g.tt_rows > 0)
+      GW_CUDA(cudaMemcpyAsync(fresh.p, g.Wa_d.p, static_cast<size_t>(g.tt_rows) * sizeof(double),
+                              cudaMemcpyDeviceToDevice, s));
+    g.Wa_d.swap(fresh);
+    GW_CUDA(cudaStreamSynchronize(s));
+  }
   Workspace& ws = g.ws;
   GW_TRY(ensure_sweep_scratch(g, ws, 1, true, s));
-  GW_TRY(ws.small.ensure(static_cast<size_t>(rows) * sizeof(double) + 64, s));
   double* T = g.ttab.as<double>();
-  double* dWa = ws.small.as<double>();
+  double* dWa = g.Wa_d.as<double>();
   int32_t r0 = g.tt_rows;
   if (r0 == 0) {
     // t_0 = 1, stored scaled (t~_0 = s) on a weighted graph: the rows of the table are sweep inputs
@@ -866,6 +926,8 @@ gedwalk_status ensure_totals(Graph& g, double alpha, int32_t rows, cudaStream_t 
       GW_KCHECK();
     }
     g.Wa.assign(1, static_cast<double>(g.n));
+    fill_f64_kernel<<<1, 32, 0, s>>>(dWa, 1, static_cast<double>(g.n));
+    GW_KCHECK();
     r0 = 1;
   }
   // t_r counts the walks that start at a vertex; on a directed graph batched scoring needs the
@@ -1058,13 +1120,11 @@ gedwalk_status truncation_length(Graph& g, double alpha, double eps, int32_t* L,
   Workspace& ws = g.ws;
   for (;;) {
     GW_TRY(ensure_totals(g, alpha, rows, s));
-    GW_TRY(ws.small.ensure(static_cast<size_t>(rows) * sizeof(double) + 64, s));
-    // the Wa row sums are re-staged on the device so that the stop test runs there
-    double* dWa = ws.small.as<double>();
-    GW_CUDA(cudaMemcpyAsync(dWa, g.Wa.data(), sizeof(double) * rows, cudaMemcpyHostToDevice, s));
-    int32_t* dl = reinterpret_cast<int32_t*>(dWa + rows);
-    double* db = dWa + rows + 1;
-    first_crossing_kernel<<<1, 32, 0, s>>>(dWa, 1, rows, coef, eps, dl, db);
+    GW_TRY(ws.small.ensure(64, s));
+    // the stop test reads the row sums where the sweeps' reductions left them
+    double* db = ws.small.as<double>();
+    int32_t* dl = reinterpret_cast<int32_t*>(db + 1);
+    first_crossing_kernel<<<1, 32, 0, s>>>(g.Wa_d.as<double>(), 1, rows, coef, eps, dl, db);
     GW_KCHECK();
     int32_t hl = -1;
     double hb = 0;

@@ -208,6 +208,7 @@ struct Graph {
   int32_t tt_rows = 0;
   DevBuf ttab;
   std::vector<double> Wa;
+  DevBuf Wa_d;  // the same sums on the device, where the truncation test reads them
   // readers of ttab hold it shared; growing or replacing the table holds it exclusively
   std::shared_mutex tt_lock;
   // truncation lengths already found: {alpha, epsilon, L, B_L}

@@ -196,6 +196,10 @@ def test_upload_rejects_malformed_graphs(cuda_device):
     with pytest.raises(gedwalk.GedWalkError) as e:
         gedwalk.Graph(g.row_ptr, bad_sym)
     assert "row 0" in str(e.value) and "symmetric" in str(e.value)
+    # row pointers that decrease are caught before any entry is read
+    with pytest.raises(gedwalk.GedWalkError) as e:
+        gedwalk.Graph(np.array([0, 2, 1, 3], np.int32), np.array([1, 2, 0], np.int32))
+    assert "row 1" in str(e.value) and "row_ptr decreases" in str(e.value)
     # the same lists pass when declared directed, and a symmetric star passes undirected
     gedwalk.Graph(rp, ci, directed=True).free()
     st = gg.star(40)
