@@ -696,6 +696,18 @@ static int row_class(int32_t d) {
   return cls;
 }
 
+// The first row in [lo, hi) where pred holds, for a pred that holds on a suffix of the range
+// (hi if none): a binary search.
+template <class P>
+static int32_t first_row(int32_t lo, int32_t hi, P pred) {
+  while (lo < hi) {
+    const int32_t mid = lo + (hi - lo) / 2;
+    if (pred(mid)) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
+}
+
 static gedwalk_status finish_plan(Plan& plan, const std::vector<int4>& units, const std::vector<int4>& heavy) {
   plan.num_units = static_cast<int32_t>(units.size());
   plan.num_slots = plan.num_units + plan.num_heavy;
@@ -759,11 +771,13 @@ static gedwalk_status build_plan(Plan& plan, const std::vector<int32_t>& deg, co
     return finish_plan(plan, units, heavy);
   }
   // rows are ordered by decreasing degree: the heavy rows form a prefix, then runs of one class
+  // (row lengths from the row pointers)
+  auto deg_at = [&](int32_t i) { return rp[i + 1] - rp[i]; };
   std::vector<int4> units, heavy;
   int32_t slice = 0;
   int32_t r = 0;
-  for (; r < n_active && deg[r] > kHeavyDeg; ++r) {
-    const int32_t d = deg[r];
+  for (; r < n_active && deg_at(r) > kHeavyDeg; ++r) {
+    const int32_t d = deg_at(r);
     const int32_t ns = (d + kSliceEdges - 1) / kSliceEdges;
     const int32_t hi = static_cast<int32_t>(heavy.size());
     heavy.push_back(make_int4(r, slice, ns, 0));
@@ -777,11 +791,9 @@ static gedwalk_status build_plan(Plan& plan, const std::vector<int32_t>& deg, co
   plan.num_slices = slice;
   plan.num_heavy = static_cast<int32_t>(heavy.size());
   while (r < n_active) {
-    const int cls = row_class(deg[r]);
+    const int cls = row_class(deg_at(r));
     // the run of this class: classes do not increase along the rows
-    const int32_t cls_end = static_cast<int32_t>(
-        std::partition_point(deg.begin() + r, deg.begin() + n_active, [&](int32_t d) { return row_class(d) == cls; }) -
-        deg.begin());
+    const int32_t cls_end = first_row(r, n_active, [&](int32_t i) { return row_class(deg_at(i)) != cls; });
     // a short-row unit takes up to kUnitRowsMax rows; on small graphs fewer, down to one
     // iteration of its warp (2 rows per lane group), so that every SM gets work
     const int32_t iter_rows = cls == 6 ? 1 : 2 * (32 >> cls);
@@ -1388,7 +1400,6 @@ static gedwalk_status upload_impl(const int32_t* row_ptr, const int32_t* col_idx
   // vertex with no arc at all sorts last, so the isolated rows form the tail.
   g->perm.resize(n);
   g->inv.resize(n);
-  g->deg.resize(n);
   std::vector<int32_t> rp(static_cast<size_t>(n) + 1);
   GW_TRY(g->rp.ensure(rp.size() * sizeof(int32_t), 0));
   const size_t ci_len = static_cast<size_t>(nnz) + 4;  // 4 zero pad entries for the vector loads at the end
@@ -1404,9 +1415,9 @@ static gedwalk_status upload_impl(const int32_t* row_ptr, const int32_t* col_idx
                         deg_d.as<int32_t>(), g->rp.as<int32_t>()));
     GW_CUDA(cudaMemcpy(g->perm.data(), g->perm_d.p, static_cast<size_t>(n) * sizeof(int32_t), cudaMemcpyDeviceToHost));
     GW_CUDA(cudaMemcpy(g->inv.data(), inv_d.p, static_cast<size_t>(n) * sizeof(int32_t), cudaMemcpyDeviceToHost));
-    GW_CUDA(cudaMemcpy(g->deg.data(), deg_d.p, static_cast<size_t>(n) * sizeof(int32_t), cudaMemcpyDeviceToHost));
     GW_CUDA(cudaMemcpy(rp.data(), g->rp.p, rp.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
   } else {
+    g->deg.resize(n);
     for (int32_t v = 0; v < n; ++v) g->perm[v] = v;
     std::stable_sort(g->perm.begin(), g->perm.end(), [&](int32_t a, int32_t b) {
       if (deg_old[a] != deg_old[b]) return deg_old[a] > deg_old[b];
@@ -1425,8 +1436,7 @@ static gedwalk_status upload_impl(const int32_t* row_ptr, const int32_t* col_idx
   // rows from n_active on are isolated: no entry in either direction
   g->n_active = n;
   if (!directed) {
-    g->n_active = static_cast<int32_t>(
-        std::partition_point(g->deg.begin(), g->deg.end(), [](int32_t d) { return d > 0; }) - g->deg.begin());
+    g->n_active = first_row(0, n, [&](int32_t i) { return rp[i + 1] == rp[i]; });
   } else {
     while (g->n_active > 0 && g->deg[g->n_active - 1] == 0 && rdeg_old[g->perm[g->n_active - 1]] == 0) --g->n_active;
   }
@@ -1439,9 +1449,7 @@ static gedwalk_status upload_impl(const int32_t* row_ptr, const int32_t* col_idx
     GW_KCHECK();
     // sort each row by new id: the rows are ordered by decreasing degree, so the rows above
     // kSortSeg entries (sorted as 1024-entry pieces) are a prefix, and the others are sorted whole
-    const int32_t n_long = static_cast<int32_t>(
-        std::partition_point(g->deg.begin(), g->deg.begin() + g->n_active, [](int32_t d) { return d > kSortSeg; }) -
-        g->deg.begin());
+    const int32_t n_long = first_row(0, g->n_active, [&](int32_t i) { return rp[i + 1] - rp[i] <= kSortSeg; });
     std::vector<int2> seg;
     for (int32_t i = 0; i < n_long; ++i)
       for (int32_t b = rp[i]; b < rp[i + 1]; b += kSortSeg) seg.push_back(make_int2(b, std::min(kSortSeg, rp[i + 1] - b)));

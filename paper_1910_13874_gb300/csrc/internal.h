@@ -199,7 +199,7 @@ struct Graph {
   DevBuf perm_d;            // int32[n]: new -> caller id
   std::vector<int32_t> perm;  // new -> caller id
   std::vector<int32_t> inv;   // caller id -> new
-  std::vector<int32_t> deg;   // degree by new id
+  std::vector<int32_t> deg;   // degree by new id (directed graphs only; else the row pointers give it)
   Plan plan;
 
   // alpha-scaled walk totals t_r = alpha A t_{r-1}, t_0 = 1 (FP64, [rows][n]; on a weighted graph
