@@ -96,7 +96,7 @@ typedef struct {
   uint64_t seed;           /* stochastic greedy: seed of the counter-based sample draws */
   int32_t bound;           /* GEDWALK_BOUND_COMBINATORIAL (default) or GEDWALK_BOUND_SPECTRAL */
   int32_t lookahead;       /* maximize: greedy steps carried by one run of sweeps (see gedwalk_maximize):
-                              0 = default (4 in FP32, 2 in FP64), 1 = off, 2, 4 or (FP32) 8 */
+                              0 = default (7 in FP32, 3 in FP64), 1 = off, 3 or (FP32) 7 */
   int32_t spec_cols;       /* maximize without lookahead: columns of the fused sweep (phi^miss plus
                               speculative candidates): 0 = default (2; 4 with GEDWALK_ADAPTIVE_L), 2, 4
                               or (FP32) 8 */
@@ -306,8 +306,8 @@ GEDWALK_API gedwalk_status gedwalk_gains(gedwalk_graph_t g, const int32_t* S, in
  * next steps' phi^miss vectors and exact gains for guessed winners (lookahead):
  * a step whose winner was guessed needs no sweep. Every pick is still certified
  * against the bounds of the actual group, so the results do not depend on it.
- * params->lookahead (1 = off, 2, 4; 8 in FP32) sets the number of steps per run
- * (0: 4 in FP32, 2 in FP64); params->spec_cols the width of the one-step fused
+ * params->lookahead (1 = off, 3; 7 in FP32) sets the number of steps per run
+ * (0: 7 in FP32, 3 in FP64); params->spec_cols the width of the one-step fused
  * sweep when the lookahead is off. Other values return INVALID.
  * The host drives the steps: one synchronisation per bound pass, to read the
  * selection. With the lookahead on, GEDWALK_DEVICE_LOOP runs the k steps as one

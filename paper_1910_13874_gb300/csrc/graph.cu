@@ -113,7 +113,7 @@ double sweep_bytes(int mode, bool fp64, int cols, int32_t n, int64_t nnz, bool w
   double b = 4.0 * double(nnz) + 4.0 * (double(n) + 1.0) + 2.0 * cols * es * double(n);
   if (mode == MODE_SCORE || mode == MODE_FUSED || mode == MODE_CAND || mode == MODE_LOOK) b += double(n) / 8.0;
   if (mode == MODE_FUSED) b += es * double(n);
-  if (mode == MODE_LOOK) b += es * double(n) * (cols / 2);  // one phi^miss row per level
+  if (mode == MODE_LOOK) b += es * double(n) * (cols - 1);  // one phi^miss row per level
   if (weighted) b += es * double(n);  // the vertex scales
   return b;
 }

@@ -167,9 +167,10 @@ __global__ void greedy_init(T* __restrict__ m0, T* __restrict__ X, int cols, int
   }
 }
 
-// MODE_LOOK initialisation: level d (columns 2d, 2d+1) runs under S + {c_1..c_d}: column 2d is
-// its phi^miss_0 (also table d, row 0), column 2d+1 the unit vector of c_{d+1} (0 without one).
-// The walk vectors are written 16 bytes per thread (consecutive threads, consecutive chunks).
+// MODE_LOOK initialisation for a run of C - 1 levels with guesses c_1..c_{C-1}: column 0 is
+// phi^miss_0 under S, column j >= 1 the unit vector of c_j (0 without one); table d, row 0, is
+// phi^miss_0 under S + {c_1..c_d}. The walk vectors are written 16 bytes per thread (consecutive
+// threads, consecutive chunks).
 template <typename T>
 struct Vec16;
 template <>
@@ -183,14 +184,14 @@ struct Vec16<double> {
   __device__ static double2 make(const double* e) { return make_double2(e[0], e[1]); }
 };
 
-template <typename T, int LV>
+template <typename T, int C>
 __global__ void look_init(T* __restrict__ tab, int64_t tab_stride, T* __restrict__ X,
                           const int32_t* __restrict__ cand, const uint32_t* __restrict__ mask, int32_t n,
                           const T* __restrict__ rs) {
-  constexpr int cols = 2 * LV;
+  constexpr int LV = C - 1;                               // levels
   constexpr int per = 16 / static_cast<int>(sizeof(T));  // elements per 16-byte chunk
-  static_assert(cols % per == 0, "a row is whole 16-byte chunks");
-  constexpr int cpr = cols / per;                         // chunks per row
+  static_assert(C % per == 0, "a row is whole 16-byte chunks");
+  constexpr int cpr = C / per;                            // chunks per row
   __shared__ int sc[LV];
   if (threadIdx.x < LV) sc[threadIdx.x] = cand[threadIdx.x];
   __syncthreads();
@@ -206,14 +207,8 @@ __global__ void look_init(T* __restrict__ tab, int64_t tab_stride, T* __restrict
 #pragma unroll
     for (int j = 0; j < per; ++j) {
       const int col = part * per + j;
-      const int d = col >> 1;
-      if (col & 1) {
-        e[j] = sc[d] == v ? sv : T(0);
-      } else {
-        bool out = inS;
-        for (int i = 0; i < d; ++i) out |= sc[i] == v;
-        e[j] = out ? T(0) : sv;
-      }
+      if (col == 0) e[j] = inS ? T(0) : sv;
+      else e[j] = sc[col - 1] == v ? sv : T(0);
     }
     reinterpret_cast<V*>(X)[q] = Vec16<T>::make(e);
   }
@@ -227,14 +222,12 @@ __global__ void look_init(T* __restrict__ tab, int64_t tab_stride, T* __restrict
   }
 }
 
+// cols = levels + 1: 4 or (FP32) 8, the only shapes greedy_shape admits
 template <typename T>
-void launch_look_init(int levels, int blocks, cudaStream_t s, T* tab, int64_t tab_stride, T* X, const int32_t* cand,
+void launch_look_init(int cols, int blocks, cudaStream_t s, T* tab, int64_t tab_stride, T* X, const int32_t* cand,
                       const uint32_t* mask, int32_t n, const T* rs) {
-  switch (levels) {
-    case 2: look_init<T, 2><<<blocks, 256, 0, s>>>(tab, tab_stride, X, cand, mask, n, rs); break;
-    case 4: look_init<T, 4><<<blocks, 256, 0, s>>>(tab, tab_stride, X, cand, mask, n, rs); break;
-    default: look_init<T, 8><<<blocks, 256, 0, s>>>(tab, tab_stride, X, cand, mask, n, rs); break;
-  }
+  if (cols == 4 || sizeof(T) == 8) look_init<T, 4><<<blocks, 256, 0, s>>>(tab, tab_stride, X, cand, mask, n, rs);
+  else look_init<T, 8><<<blocks, 256, 0, s>>>(tab, tab_stride, X, cand, mask, n, rs);
 }
 
 // Records one exact gain known on the host (a lookahead level's candidate) for this step.
@@ -533,14 +526,13 @@ gedwalk_status issue_sweeps(GreedyCtx& c, int mode, int cols, bool profile, cons
   const int64_t look_stride = static_cast<int64_t>(c.L + 1) * g.n;  // elements between level tables
   void* m0 = mode == MODE_FUSED ? tab.as<char>() + off * c.es : nullptr;
   if (mode == MODE_LOOK) {
-    // lookahead levels: 2, 4 or 8 (the shape admits no other)
+    // cols - 1 lookahead levels: 3 or (FP32) 7 (the shape admits no other)
     const int64_t chunks = static_cast<int64_t>(g.n) * cols * static_cast<int64_t>(c.es) / 16;
     if (fp64)
-      launch_look_init<double>(cols / 2, blocks_for(chunks), c.s, ws.mtab.as<double>(), look_stride,
-                               ws.x0.as<double>(), c.d_cand, ws.mask.as<uint32_t>(), g.n,
-                               g.weighted ? g.rs_d.as<double>() : nullptr);
+      launch_look_init<double>(cols, blocks_for(chunks), c.s, ws.mtab.as<double>(), look_stride, ws.x0.as<double>(),
+                               c.d_cand, ws.mask.as<uint32_t>(), g.n, g.weighted ? g.rs_d.as<double>() : nullptr);
     else
-      launch_look_init<float>(cols / 2, blocks_for(chunks), c.s, ws.mtab.as<float>(), look_stride, ws.x0.as<float>(),
+      launch_look_init<float>(cols, blocks_for(chunks), c.s, ws.mtab.as<float>(), look_stride, ws.x0.as<float>(),
                               c.d_cand, ws.mask.as<uint32_t>(), g.n, g.weighted ? g.rs_f.as<float>() : nullptr);
   } else if (fp64)
     greedy_init<double><<<blocks_for(g.n), 256, 0, c.s>>>(static_cast<double*>(m0), ws.x0.as<double>(), cols, first,
@@ -981,14 +973,16 @@ gedwalk_status greedy_shape(const Graph& g, const Resolved& r, int32_t flags, Gr
   }
   // Lookahead (plain greedy on an undirected graph): one run of sweeps carries `levels` steps,
   // level d under S + {c_1..c_d} with the guessed winners c_d; a step whose winner was guessed
-  // needs no sweep of its own. A gather costs one L2 sector request whatever the row width up to
-  // 32 bytes, so 4 FP32 levels (2 FP64) cost little more per sweep than one.
+  // needs no sweep of its own. The run's rows hold levels + 1 columns (phi^miss under S and one
+  // column per guess; every level's phi^miss is a difference of them). A gather costs one L2
+  // sector request whatever the row width up to 32 bytes, so 7 FP32 levels (3 FP64) cost little
+  // more per sweep than one.
   sh.levels = 1;
   if (!(flags & (GEDWALK_ADAPTIVE_L | GEDWALK_STOCHASTIC | GEDWALK_GAINS_ALL)) && !g.directed) {
-    sh.levels = r.fp64 ? 2 : 4;
+    sh.levels = r.fp64 ? 3 : 7;
     if (r.lookahead != 0) {
-      if (!(r.lookahead == 1 || r.lookahead == 2 || (!r.fp64 && (r.lookahead == 4 || r.lookahead == 8))))
-        return fail(GEDWALK_ERR_INVALID, "lookahead must be 0, 1, 2 or (FP32) 4 or 8");
+      if (!(r.lookahead == 1 || r.lookahead == 3 || (!r.fp64 && r.lookahead == 7)))
+        return fail(GEDWALK_ERR_INVALID, "lookahead must be 0, 1, 3 or (FP32) 7");
       sh.levels = r.lookahead;
     }
   }
@@ -999,7 +993,7 @@ gedwalk_status greedy_shape(const Graph& g, const Resolved& r, int32_t flags, Gr
   sh.ell_max = 1;
   while (adaptive && sh.ell_max < r.L) sh.ell_max *= 2;
   sh.tab_L = adaptive ? sh.ell_max : r.L;
-  sh.cols_max = std::max({sh.levels > 1 ? 2 * sh.levels : sh.cols_fused, sh.cols_cand,
+  sh.cols_max = std::max({sh.levels > 1 ? sh.levels + 1 : sh.cols_fused, sh.cols_cand,
                           (flags & GEDWALK_GAINS_ALL) ? sh.cols_all : 0, 2});
   *out = sh;
   return GEDWALK_OK;
@@ -1078,7 +1072,7 @@ gedwalk_status run_device_loop(GreedyCtx& c, int32_t k, int levels, int cols_can
   GW_TRY(ws.x0.ensure(static_cast<size_t>(g.n) * cols_max * es, s));
   GW_TRY(ws.x1.ensure(static_cast<size_t>(g.n) * cols_max * es, s));
   GW_TRY(ensure_sweep_scratch(g, ws, cols_max, fp64, s));
-  GW_TRY(configure_sweep(MODE_LOOK, fp64, 2 * levels));
+  GW_TRY(configure_sweep(MODE_LOOK, fp64, levels + 1));
   GW_TRY(configure_sweep(MODE_CAND, fp64, cols_cand));
   DevCtl h{};
   h.k = k;
@@ -1144,7 +1138,7 @@ gedwalk_status run_device_loop(GreedyCtx& c, int32_t k, int levels, int cols_can
       c.tab_off = 0;
       c.stamp_ctl = d_stamp;
       c.stamp_end = 1;
-      const gedwalk_status st = issue_sweeps(c, MODE_LOOK, 2 * levels, false, nullptr, false);
+      const gedwalk_status st = issue_sweeps(c, MODE_LOOK, levels + 1, false, nullptr, false);
       c.stamp_ctl = nullptr;
       GW_TRY(st);
       ctl_after_run<<<1, 32, 0, s>>>(dctl, c.d_gains);
@@ -1214,11 +1208,11 @@ gedwalk_status run_device_loop(GreedyCtx& c, int32_t k, int levels, int cols_can
   // after_run, per certification round 4 kernels, per batch init + L sweeps + 2 stamps + 2 reduce
   count_launches(static_cast<int>(2 * k + out.runs * (L + 6) + out.iters * 4 + out.cand_batches * (L + 5)));
   if (profiling()) {  // the sweeps' device time, from the device-clock stamps around each run / batch
-    const double b_look = sweep_bytes(MODE_LOOK, fp64, 2 * levels, g.n, g.nnz, g.weighted);
+    const double b_look = sweep_bytes(MODE_LOOK, fp64, levels + 1, g.n, g.nnz, g.weighted);
     const double b_cand = sweep_bytes(MODE_CAND, fp64, cols_cand, g.n, g.nnz, g.weighted);
     const int64_t n_look = out.runs * L, n_cand = out.cand_batches * L;
     for (int64_t i = 0; i < n_look; ++i)
-      profile_add(static_cast<double>(out.t[1]) / 1e6 / n_look, b_look, (MODE_LOOK * 1000 + 2 * levels) * 2 + fp64);
+      profile_add(static_cast<double>(out.t[1]) / 1e6 / n_look, b_look, (MODE_LOOK * 1000 + levels + 1) * 2 + fp64);
     for (int64_t i = 0; i < n_cand; ++i)
       profile_add(static_cast<double>(out.t[2]) / 1e6 / n_cand, b_cand, (MODE_CAND * 1000 + cols_cand) * 2 + fp64);
   }
@@ -1458,7 +1452,7 @@ gedwalk_status maximize_impl(Graph& g, Workspace& ws, int32_t k, const Resolved&
           sc.assign(levels, -1);
           for (size_t j = 0; j < spec.size() && j < static_cast<size_t>(levels); ++j) sc[j] = spec[j].v;
           c.tab_off = 0;
-          GW_TRY(run_sweeps(c, MODE_LOOK, 2 * levels, sc));
+          GW_TRY(run_sweeps(c, MODE_LOOK, levels + 1, sc));
           GW_CUDA(cudaMemcpyAsync(h_look, c.d_gains, sizeof(double) * levels, cudaMemcpyDeviceToHost, s));
           look_lvl = 0;
           look_c = sc;

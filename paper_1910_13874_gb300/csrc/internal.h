@@ -240,7 +240,7 @@ enum SweepMode : int {
   MODE_FUSED = 2,   // greedy: column 0 = phi^miss under S, columns 1.. candidate columns
   MODE_CAND = 3,    // greedy: candidate columns only; candidate rows read phi^miss from a table
   MODE_PLAIN = 4,   // batched scoring: y = alpha A x, no mask
-  MODE_LOOK = 5     // greedy lookahead: column pairs (phi^miss, candidate) under S + {c_1..c_d}
+  MODE_LOOK = 5     // greedy lookahead: phi^miss under S, then the walks through c_j avoiding S + {c_1..c_{j-1}}
 };
 
 struct SweepArgs {

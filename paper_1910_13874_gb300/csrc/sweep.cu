@@ -209,24 +209,19 @@ struct Scatter {
 // Number of FP64 column sums a mode keeps.
 template <int MODE, int C>
 struct Sums {
-  static constexpr int N = MODE == MODE_TOTALS ? 1 : MODE == MODE_SCORE ? 1 : MODE == MODE_FUSED ? C - 1
-                           : MODE == MODE_CAND ? C : MODE == MODE_LOOK ? C / 2 : 0;
-  // the sum fed by column c, or -1 (MODE_FUSED: columns 1..; MODE_LOOK: the odd columns, the
-  // candidates)
+  static constexpr int N = MODE == MODE_TOTALS ? 1 : MODE == MODE_SCORE ? 1
+                           : (MODE == MODE_FUSED || MODE == MODE_LOOK) ? C - 1 : MODE == MODE_CAND ? C : 0;
+  // the sum fed by column c, or -1 (MODE_FUSED and MODE_LOOK: columns 1.., the candidates)
   __device__ __forceinline__ static int slot(int c) {
-    if constexpr (MODE == MODE_LOOK) {
-      return (c & 1) ? c >> 1 : -1;
-    } else {
-      constexpr int first = MODE == MODE_FUSED ? 1 : 0;
-      return c >= first && c - first < N ? c - first : -1;
-    }
+    constexpr int first = (MODE == MODE_FUSED || MODE == MODE_LOOK) ? 1 : 0;
+    return c >= first && c - first < N ? c - first : -1;
   }
 };
 
 // Number of candidate ids a mode reads (the only rows whose epilogue differs from y = alpha s).
 template <int MODE, int C>
 struct Cands {
-  static constexpr int N = MODE == MODE_FUSED ? C - 1 : MODE == MODE_CAND ? C : MODE == MODE_LOOK ? C / 2 : 0;
+  static constexpr int N = (MODE == MODE_FUSED || MODE == MODE_LOOK) ? C - 1 : MODE == MODE_CAND ? C : 0;
 };
 
 // Per-lane column sums over the rows of one unit. FP64 vectors sum in FP64. FP32 vectors sum with
@@ -279,20 +274,68 @@ __device__ __forceinline__ void candidate_rows(const SweepArgs& a, const int* __
 #pragma unroll
     for (int k = 0; k < CPL; ++k)
       if (valid && s_cand[c0 + k] == r) y[k] = __ldg(min + r);
-  } else if constexpr (MODE == MODE_LOOK) {
-    // level d = c / 2 runs under S + {c_1..c_d}: column 2d is its phi^miss, column 2d+1 the
-    // walks through c_{d+1}, whose own row takes column 2d's value
+  }
+}
+
+// MODE_LOOK epilogue for row r: D = C - 1 levels of one lookahead run, T_d = S + {c_1..c_d}.
+// Column 0 is phi^miss under S; column j >= 1 counts the walks through c_j that avoid T_{j-1}
+// (at c_j's own row: all of phi^miss(T_{j-1}), every such walk ending there visits c_j). A walk
+// that avoids S either avoids c_1..c_d or has a first c_j among them, so
+//   phi^miss(T_d) = column 0 - columns 1..d,
+// which gives every level's phi^miss (table d, d = 0..D-1) and c_j's own-row value without
+// columns of their own. The differences are clamped at 0 (their exact value is never negative).
+// The lane holds columns c0..c0+CPL-1 of the row's group, whose column blocks lie in natural
+// order over its first lanes (duplicates beyond them); every lane of the warp calls it.
+template <typename T, int C, int CPL>
+__device__ __forceinline__ void look_rows(const SweepArgs& a, const int* __restrict__ s_cand, int r, bool valid,
+                                          bool store, int c0, int base, T (&y)[CPL], bool maybe_cand) {
+  constexpr int NB = C / CPL;  // column blocks of a group
+  T y0 = y[0];                 // column 0 sits in block 0, on the group's first lane
+  T run = T(0);                // running sum of columns 1.. (starts with the blocks before this lane's)
+  if constexpr (NB > 1) {
+    const int blk = c0 / CPL;
+    y0 = __shfl_sync(kFull, y[0], base);
+    T inc = T(0);
 #pragma unroll
-    for (int k = 0; k < CPL; ++k) {
-      const int d = (c0 + k) >> 1;
-      for (int j = 0; j < d; ++j)
-        if (valid && s_cand[j] == r) y[k] = T(0);
+    for (int k = 0; k < CPL; ++k)
+      if (c0 + k >= 1) inc += y[k];
+#pragma unroll
+    for (int o = 1; o < NB; o <<= 1) {
+      const T t = __shfl_up_sync(kFull, inc, o);
+      if (blk >= o) inc += t;
     }
-    const T left = __shfl_up_sync(kFull, y[CPL - 1], 1);  // column 2d of a lane holding only 2d+1
+    const T t = __shfl_up_sync(kFull, inc, 1);
+    run = blk > 0 ? t : T(0);
+  }
+  bool special = false;  // r is one of the run's candidates (only units that hold one look)
+  if (maybe_cand) {
 #pragma unroll
-    for (int k = 0; k < CPL; ++k) {
-      const int c = c0 + k;
-      if (valid && (c & 1) && s_cand[c >> 1] == r) y[k] = CPL == 1 ? left : y[k > 0 ? k - 1 : 0];
+    for (int j = 0; j < C - 1; ++j) special |= valid && s_cand[j] == r;
+  }
+  const bool rare = maybe_cand && __any_sync(kFull, special);
+  T* M = static_cast<T*>(a.Mout);
+#pragma unroll
+  for (int k = 0; k < CPL; ++k) {
+    const int d = c0 + k;
+    const T before = run;  // columns 1..d-1
+    if (d >= 1) run += y[k];
+    if (store && d <= C - 2) {  // table d = phi^miss(T_d): column 0 minus columns 1..d, 0 on c_1..c_d
+      T m = y0 - run;
+      m = m > T(0) ? m : T(0);
+      if (rare && special)
+        for (int j = 0; j < d; ++j)
+          if (s_cand[j] == r) m = T(0);
+      M[a.mout_stride * d + r] = m;
+    }
+    // r = c_m: column m takes phi^miss(T_{m-1}) at r; columns beyond m run under sets that hold r
+    if (rare && special && d >= 1) {
+      if (s_cand[d - 1] == r) {
+        const T e = y0 - before;
+        y[k] = e > T(0) ? e : T(0);
+      } else {
+        for (int j = 0; j < d - 1; ++j)
+          if (s_cand[j] == r) y[k] = T(0);
+      }
     }
   }
 }
@@ -339,7 +382,9 @@ __device__ __forceinline__ void epilogue(const SweepArgs& a, const int* __restri
     T y[CPL];
 #pragma unroll
     for (int k = 0; k < CPL; ++k) y[k] = inS ? T(0) : alpha * s[k];
-    if (Cands<MODE, C>::N > 0 && maybe_cand) {
+    if constexpr (MODE == MODE_LOOK) {
+      look_rows<T, C, CPL>(a, s_cand, r, valid, store, c0, base, y, maybe_cand);
+    } else if (Cands<MODE, C>::N > 0 && maybe_cand) {
       bool special = false;
 #pragma unroll
       for (int j = 0; j < Cands<MODE, C>::N; ++j) special |= s_cand[j] == r;
@@ -347,12 +392,6 @@ __device__ __forceinline__ void epilogue(const SweepArgs& a, const int* __restri
     }
     if constexpr (MODE == MODE_FUSED) {
       if (store && c0 == 0) static_cast<T*>(a.Mout)[r] = y[0];
-    } else if constexpr (MODE == MODE_LOOK) {
-      if (store) {
-#pragma unroll
-        for (int k = 0; k < CPL; ++k)
-          if (((c0 + k) & 1) == 0) static_cast<T*>(a.Mout)[a.mout_stride * ((c0 + k) >> 1) + r] = y[k];
-      }
     }
     if (store) {
       if constexpr (Sums<MODE, C>::N > 0) {
@@ -576,7 +615,9 @@ __device__ __forceinline__ void run_unit(const SweepArgs& a, const Src& src, int
     return;
   }
   switch (u.z) {
-    case 0: short_rows<T, C, MODE, 0>(a, src, u, uidx, lane, rp, s_cand); break;
+    // the lookahead's 8-column rows of degree <= 2 take two lanes each: one lane holding all eight
+    // columns of two rows overflows the register budget of five CTAs per SM
+    case 0: short_rows<T, C, MODE, (MODE == MODE_LOOK && C == 8 && sizeof(T) == 4) ? 1 : 0>(a, src, u, uidx, lane, rp, s_cand); break;
     case 1: short_rows<T, C, MODE, 1>(a, src, u, uidx, lane, rp, s_cand); break;
     case 2: short_rows<T, C, MODE, 2>(a, src, u, uidx, lane, rp, s_cand); break;
     case 3: short_rows<T, C, MODE, 3>(a, src, u, uidx, lane, rp, s_cand); break;
@@ -703,11 +744,10 @@ int sweep_sums(int mode, int cols) {
     case MODE_SCORE:
       return 1;
     case MODE_FUSED:
+    case MODE_LOOK:
       return cols - 1;
     case MODE_CAND:
       return cols;
-    case MODE_LOOK:
-      return cols / 2;
     default:
       return 0;
   }
@@ -721,7 +761,6 @@ gedwalk_status configure_sweep(int mode, bool fp64, int cols) {
   }
   GW_CASE(MODE_LOOK, float, 4)
   GW_CASE(MODE_LOOK, float, 8)
-  GW_CASE(MODE_LOOK, float, 16)
   GW_CASE(MODE_LOOK, double, 4)
   GW_CASE(MODE_CAND, float, 4)
   GW_CASE(MODE_CAND, double, 4)
@@ -750,7 +789,6 @@ gedwalk_status launch_sweep(int mode, bool fp64, int cols, const SweepArgs& a, c
   GW_CASE(MODE_CAND, double, 8)
   GW_CASE(MODE_LOOK, float, 4)
   GW_CASE(MODE_LOOK, float, 8)
-  GW_CASE(MODE_LOOK, float, 16)
   GW_CASE(MODE_LOOK, double, 4)
   GW_CASE(MODE_PLAIN, float, 4)
   GW_CASE(MODE_PLAIN, float, 8)
