@@ -426,7 +426,11 @@ typedef struct {
 
 GEDWALK_API gedwalk_status gedwalk_serve_counters_read(gedwalk_server_t srv, gedwalk_serve_counters* out);
 
-/* Stops the scheduler after the requests in flight finish; pending requests are dropped. */
+/* Stops the server. Requests already admitted finish; requests still waiting
+ * for admission end with GEDWALK_ERR_BUSY (a poll reports it). Returns after
+ * the server's threads have stopped and every gedwalk_serve_poll call blocked
+ * on this server has returned; srv is then freed, and no call on it may start
+ * after, or at the same time as, this call. */
 GEDWALK_API gedwalk_status gedwalk_serve_destroy(gedwalk_server_t srv);
 
 /*

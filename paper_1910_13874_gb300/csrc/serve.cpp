@@ -96,6 +96,7 @@ struct Server {
   uint64_t next_ticket = 1;
   gedwalk_serve_counters st{};
   bool stop = false;
+  int32_t pollers = 0;  // gedwalk_serve_poll calls inside the server (destroy waits for them)
 
   // A lane's charge: what its workspace holds, or more while it has work (the batch it scores now,
   // or the next batch its queue forms).
@@ -403,6 +404,15 @@ gedwalk_status gedwalk_serve_poll(gedwalk_server_t h, uint64_t ticket, int32_t w
   Server* srv = reinterpret_cast<Server*>(h);
   if (!srv || !done) return fail(GEDWALK_ERR_INVALID, "server or done is NULL");
   std::unique_lock<std::mutex> lk(srv->mu);
+  // counted while inside (the mutex is held again whenever it changes): destroy frees the server
+  // only once no poll is left in it
+  struct Inside {
+    Server* s;
+    explicit Inside(Server* v) : s(v) { ++s->pollers; }
+    ~Inside() {
+      if (--s->pollers == 0 && s->stop) s->cv_done.notify_all();
+    }
+  } inside(srv);
   auto it = srv->table.find(ticket);
   if (it == srv->table.end()) return fail(GEDWALK_ERR_NOT_FOUND, "unknown ticket %llu", (unsigned long long)ticket);
   ReqPtr q = it->second;
@@ -463,14 +473,30 @@ gedwalk_status gedwalk_serve_destroy(gedwalk_server_t h) {
   {
     std::lock_guard<std::mutex> lk(srv->mu);
     srv->stop = true;
-    srv->pending.clear();
-    srv->pending_max.clear();
+    // requests still waiting for admission end here, with BUSY, so that their pollers return
+    for (std::deque<ReqPtr>* dq : {&srv->pending, &srv->pending_max}) {
+      for (const ReqPtr& q : *dq) {
+        q->status = GEDWALK_ERR_BUSY;
+        q->error = "the server was destroyed before the request was admitted";
+        q->done = true;
+        q->t_done = Clock::now();
+      }
+      dq->clear();
+    }
+    srv->cv_done.notify_all();
     srv->cv_work.notify_all();
   }
+  // admitted requests finish: the lanes drain their queues and the workers their jobs
   for (auto& l : srv->lanes)
     if (l->th.joinable()) l->th.join();
   for (auto& w : srv->workers)
     if (w->th.joinable()) w->th.join();
+  {
+    // every request is done now; polls blocked on one of them wake up and leave
+    std::unique_lock<std::mutex> lk(srv->mu);
+    srv->cv_done.notify_all();
+    srv->cv_done.wait(lk, [&] { return srv->pollers == 0; });
+  }
   for (auto& l : srv->lanes) {
     cudaStreamSynchronize(l->stream);
     cudaStreamDestroy(l->stream);
