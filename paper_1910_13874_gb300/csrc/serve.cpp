@@ -314,17 +314,6 @@ gedwalk_status gedwalk_serve_create(const gedwalk_graph_t* graphs, int32_t n_gra
     if (!graphs[i]) return fail(GEDWALK_ERR_INVALID, "graph %d is NULL", i);
     srv->graphs.push_back(G(graphs[i]));
   }
-  for (int32_t i = 0; i < n_graphs; ++i) {
-    std::unique_ptr<Lane> lane(new Lane());
-    lane->graph = i;
-    GW_CUDA(cudaStreamCreateWithFlags(&lane->stream, cudaStreamNonBlocking));
-    srv->lanes.push_back(std::move(lane));
-  }
-  for (int i = 0; i < kMaxWorkers; ++i) {
-    std::unique_ptr<Worker> w(new Worker());
-    GW_CUDA(cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking));
-    srv->workers.push_back(std::move(w));
-  }
   // the batched path needs each graph's column width tuned and its walk-total table ready
   for (int32_t i = 0; i < n_graphs; ++i) {
     Graph& g = *srv->graphs[i];
@@ -333,6 +322,26 @@ gedwalk_status gedwalk_serve_create(const gedwalk_graph_t* graphs, int32_t n_gra
     GW_TRY(resolve(g, nullptr, 0.0, &r));
     GW_TRY(ensure_totals(g, r.alpha, r.L + 1, nullptr));
     GW_TRY(autotune_batch(g, g.ws, r));
+  }
+  // one stream per lane and worker; on a failure the ones already made are destroyed
+  cudaError_t ce = cudaSuccess;
+  for (int32_t i = 0; i < n_graphs && ce == cudaSuccess; ++i) {
+    std::unique_ptr<Lane> lane(new Lane());
+    lane->graph = i;
+    ce = cudaStreamCreateWithFlags(&lane->stream, cudaStreamNonBlocking);
+    srv->lanes.push_back(std::move(lane));
+  }
+  for (int i = 0; i < kMaxWorkers && ce == cudaSuccess; ++i) {
+    std::unique_ptr<Worker> w(new Worker());
+    ce = cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking);
+    srv->workers.push_back(std::move(w));
+  }
+  if (ce != cudaSuccess) {
+    for (auto& l : srv->lanes)
+      if (l->stream) cudaStreamDestroy(l->stream);
+    for (auto& w : srv->workers)
+      if (w->stream) cudaStreamDestroy(w->stream);
+    return fail(GEDWALK_ERR_DEVICE, "cudaStreamCreateWithFlags failed: %s", cudaGetErrorString(ce));
   }
   Server* s = srv.get();
   for (int32_t i = 0; i < n_graphs; ++i) s->lanes[i]->th = std::thread([s, i] { s->lane_loop(i); });
