@@ -110,11 +110,14 @@ enum {
 };
 
 /* Fills *p with the defaults: alpha 0, epsilon 1e-4, L 0, FP32, EPS_OVER_K, no flags, stream 0,
- * eta 0.1, seed 0, the combinatorial bound, lookahead 0, spec_cols 0. */
+ * eta 0.1, seed 0, the combinatorial bound, lookahead 0, spec_cols 0. (alpha, epsilon and the
+ * epsilon/k rule are those of Section 3.1.2 and Algorithm 2; the rest has no counterpart in the
+ * paper.) */
 GEDWALK_API void gedwalk_params_default(gedwalk_params* p);
 
 /*
- * Device memory hook. alloc(bytes, stream, ctx) returns device memory or NULL;
+ * Device memory hook (no counterpart in the paper). alloc(bytes, stream, ctx) returns device
+ * memory or NULL;
  * release(ptr, bytes, stream, ctx) frees it. Passing NULL restores the
  * built-in cudaMalloc/cudaFree. The Python binding installs PyTorch's caching
  * allocator here when it loads the library. The hook applies to every later
@@ -172,13 +175,16 @@ GEDWALK_API gedwalk_status gedwalk_graph_upload_weighted(const int32_t* row_ptr,
                                              gedwalk_graph_t* out);
 
 /* *weighted = 1 for a graph from gedwalk_graph_upload_weighted; *delta the degree of the
- * combinatorial bound (d_max, or the largest weighted degree). Either pointer may be NULL. */
+ * combinatorial bound (Eq. comb-bound: d_max, or for the weighted walks of Section 5.4 the
+ * largest weighted degree). Either pointer may be NULL. */
 GEDWALK_API gedwalk_status gedwalk_graph_info_weighted(gedwalk_graph_t g, int32_t* weighted, double* delta);
 
-/* Releases a graph and all device memory tied to it. NULL is accepted. */
+/* Releases a graph and all device memory tied to it. NULL is accepted. (Resource management: no
+ * counterpart in the paper.) */
 GEDWALK_API gedwalk_status gedwalk_graph_free(gedwalk_graph_t g);
 
-/* n, nnz (directed entries), d_max and the default alpha 1/(1+d_max). Any pointer may be NULL. */
+/* n, nnz (directed entries), d_max and the default alpha 1/(1+d_max), which lies below 1/d_max as
+ * the combinatorial bound requires (Section 3.1.2, Eq. comb-bound). Any pointer may be NULL. */
 GEDWALK_API gedwalk_status gedwalk_graph_info(gedwalk_graph_t g, int32_t* n, int64_t* nnz, int32_t* dmax, double* alpha_default);
 
 /*
@@ -251,6 +257,7 @@ GEDWALK_API gedwalk_status gedwalk_score_batch(gedwalk_graph_t g, const int32_t*
                                    const gedwalk_params* params, double* scores, int32_t* L_used);
 
 /*
+ * (Measurement of the batched scoring of gedwalk_score_batch; no counterpart in the paper.)
  * The batched-scoring autotuner's record for this graph (empty before the first
  * gedwalk_score_batch): for each column-block width tried, cols[j] and the
  * measured sweep time per column us_per_col[j] (microseconds, one unmasked
@@ -261,7 +268,8 @@ GEDWALK_API gedwalk_status gedwalk_score_batch(gedwalk_graph_t g, const int32_t*
 GEDWALK_API gedwalk_status gedwalk_batch_tuning(gedwalk_graph_t g, int32_t* cols, double* us_per_col, int32_t cap,
                                     int32_t* count, int32_t* chosen);
 
-/* Pins the batched-scoring column-block width of this graph to cols (8, 16, 32 or 64; the
+/* (Tuning of gedwalk_score_batch; no counterpart in the paper.)
+ * Pins the batched-scoring column-block width of this graph to cols (8, 16, 32 or 64; the
  * autotuner does not run), or with 0 lets the next gedwalk_score_batch tune it again. For runs
  * whose timing would mislead the tuner, such as under a profiler. */
 GEDWALK_API gedwalk_status gedwalk_batch_set_width(gedwalk_graph_t g, int32_t cols);
@@ -329,6 +337,7 @@ GEDWALK_API gedwalk_status gedwalk_maximize(gedwalk_graph_t g, int32_t k, const 
                                 int32_t init_len);
 
 /*
+ * (Measurement; the paper expects its lazy greedy to evaluate few vertices, Section 3.2.3.)
  * Counters of the last gedwalk_maximize on this graph: exact-gain evaluations
  * (candidate columns), candidate batches, sweep-kernel launches and the
  * batches whose speculation (candidates chosen before the new S was known)
@@ -349,6 +358,10 @@ GEDWALK_API gedwalk_status gedwalk_maximize_lengths(gedwalk_graph_t g, int32_t* 
 
 /* ---------------------------------------------------------------------------
  * Serving: a continuous-batching request loop over device-resident graphs.
+ * Its requests are the paper's two problems (Section 2.1): scoring a given
+ * group, problem (i), as gedwalk_score_batch computes it, and maximising a
+ * group of size k, problem (ii), as gedwalk_maximize does. The loop itself
+ * (queues, batching, admission by memory) has no counterpart in the paper.
  * Score requests for the same graph that are pending together are packed as
  * columns of one batched SpMM; maximise requests run on their own streams and
  * overlap with the scoring. Admission is by memory: a request is admitted
@@ -373,7 +386,8 @@ GEDWALK_API gedwalk_status gedwalk_serve_create(const gedwalk_graph_t* graphs, i
                                     int32_t max_batch, gedwalk_server_t* out);
 
 /*
- * Queues a request. kind GEDWALK_REQ_SCORE scores S (s_len members);
+ * Queues a request: problem (i) or (ii) of Section 2.1.
+ * kind GEDWALK_REQ_SCORE scores S (s_len members);
  * GEDWALK_REQ_MAXIMIZE runs gedwalk_maximize with k = s_len_or_k (S ignored).
  * params: NULL = defaults (its stream field is ignored). *ticket identifies the
  * request. BUSY when the queue holds 1<<20 requests already. INVALID when the
@@ -384,6 +398,7 @@ GEDWALK_API gedwalk_status gedwalk_serve_submit(gedwalk_server_t srv, int32_t gr
                                     int32_t s_len_or_k, const gedwalk_params* params, uint64_t* ticket);
 
 /*
+ * (Serving infrastructure; no counterpart in the paper.)
  * Waits up to wait_us microseconds (0 = do not wait, < 0 = wait without limit)
  * for a request. *done = 1 and results written when finished: score, group
  * (int32[k], maximize only), gains (double[k], maximize only; may be NULL),
@@ -394,12 +409,14 @@ GEDWALK_API gedwalk_status gedwalk_serve_submit(gedwalk_server_t srv, int32_t gr
 GEDWALK_API gedwalk_status gedwalk_serve_poll(gedwalk_server_t srv, uint64_t ticket, int32_t wait_us, double* score,
                                   int32_t* group, double* gains, double* latency_us, int32_t* done);
 
-/* Counters: requests completed, batched SpMM launches, score requests packed into them, and the
+/* (Serving measurement; no counterpart in the paper.)
+ * Counters: requests completed, batched SpMM launches, score requests packed into them, and the
  * peak of the charged device bytes (see gedwalk_serve_counters). */
 GEDWALK_API gedwalk_status gedwalk_serve_stats(gedwalk_server_t srv, int64_t* completed, int64_t* batches, int64_t* batched_requests,
                                    int64_t* peak_bytes);
 
 /*
+ * (Serving measurement; no counterpart in the paper.)
  * Memory admission in detail. Each scoring lane and maximise worker owns a workspace whose device
  * buffers grow to its largest request and stay allocated. The server charges each workspace the
  * bytes it holds or, while it has work, the larger of those and the exact footprint of that work.
@@ -426,7 +443,8 @@ typedef struct {
 
 GEDWALK_API gedwalk_status gedwalk_serve_counters_read(gedwalk_server_t srv, gedwalk_serve_counters* out);
 
-/* Stops the server. Requests already admitted finish; requests still waiting
+/* (Serving infrastructure; no counterpart in the paper.)
+ * Stops the server. Requests already admitted finish; requests still waiting
  * for admission end with GEDWALK_ERR_BUSY (a poll reports it). Returns after
  * the server's threads have stopped and every gedwalk_serve_poll call blocked
  * on this server has returned; srv is then freed, and no call on it may start
@@ -473,9 +491,13 @@ typedef struct {
   int64_t launches;        /* every kernel launch of the library since the last reset */
   int64_t sweep_launches;  /* sweep-kernel launches timed */
   double sweep_ms;         /* summed device time of those launches (CUDA events on their stream) */
-  double sweep_bytes;      /* summed algorithmic bytes of those launches (see the design notes) */
+  double sweep_bytes;      /* summed algorithmic bytes of those launches: per launch the CSR (4 nnz
+                              + 4 (n+1)), x read and y written once (2 C s n for C columns of s
+                              bytes), the S mask (n/8) where masked, the phi^miss rows written
+                              (s n fused, (C-1) s n lookahead) and the vertex scales (s n, weighted) */
   /* the sweep instantiation with the largest summed time: */
-  int32_t top_mode;        /* 0 totals, 1 two-state score, 2 fused greedy, 3 candidates, 4 batched */
+  int32_t top_mode;        /* 0 totals, 1 two-state score, 2 fused greedy, 3 candidates, 4 batched,
+                              5 greedy lookahead */
   int32_t top_cols;        /* columns per row */
   int32_t top_fp64;        /* 1 for FP64 rows */
   int32_t top_pad;
@@ -484,13 +506,16 @@ typedef struct {
   double top_bytes;
 } gedwalk_profile_stats;
 
-/* enable != 0 starts timing sweep launches; every call resets the counters. */
+/* (Measurement; no counterpart in the paper.) enable != 0 starts timing sweep launches; every
+ * call resets the counters. */
 GEDWALK_API gedwalk_status gedwalk_profile(int32_t enable);
 
-/* Waits for the timed launches to finish and reports the counters. */
+/* (Measurement; no counterpart in the paper.) Waits for the timed launches to finish and reports
+ * the counters. */
 GEDWALK_API gedwalk_status gedwalk_profile_read(gedwalk_profile_stats* out);
 
-/* Message for the calling thread's last failing call ("" if none). */
+/* Message for the calling thread's last failing call ("" if none). (Error reporting; no
+ * counterpart in the paper.) */
 GEDWALK_API const char* gedwalk_last_error(void);
 
 #ifdef __cplusplus

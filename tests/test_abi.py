@@ -32,6 +32,27 @@ def test_header_declares_the_boundary():
         assert must in names
 
 
+def _declaration_comments():
+    """(name, the comment blocks between the previous declaration and this one) per entry point."""
+    text = open(HEADER).read()
+    out, prev = [], 0
+    for m in re.finditer(r"GEDWALK_API\s+[\w\s\*]+?\b(gedwalk_\w+)\s*\(", text):
+        blocks = " ".join(re.findall(r"/\*.*?\*/", text[prev:m.start()], re.S))
+        out.append((m.group(1), re.sub(r"\s*\n\s*\*?\s*", " ", blocks)))  # one line, no margin stars
+        prev = text.index(";", m.end())
+    return out
+
+
+def test_every_entry_point_cites_its_passage_or_says_it_has_none():
+    cite = re.compile(r"Section \d|Eq\. |Algorithm \d|Lemma |Def\. |Prop\. |Appendix |problem \(|"
+                      r"no counterpart")
+    decls = _declaration_comments()
+    assert len(decls) == len(_declared())
+    for name, comment in decls:
+        assert comment.strip(), name
+        assert cite.search(comment), name
+
+
 def test_library_exports_every_declared_symbol(lib):
     from paper_1910_13874_gb300 import gedwalk
 
