@@ -49,12 +49,15 @@ EXPORTS = [
 
 
 class GedWalkError(RuntimeError):
+    """A failing call: .status is the gedwalk_status code, the message the library's last error."""
+
     def __init__(self, status: int, message: str):
         super().__init__(f"{_STATUS_NAMES.get(status, status)}: {message}")
         self.status = status
 
 
 class ServeCounters(ctypes.Structure):
+    """gedwalk_serve_counters: a server's admission and batching counters (int64 each)."""
     _fields_ = [(name, ctypes.c_int64) for name in (
         "completed", "batches", "batched_requests", "peak_bytes", "budget", "charged_bytes", "idle_held_bytes",
         "admitted_at_submit", "admitted_after_wait", "peak_maximize_running", "releases", "released_bytes",
@@ -62,6 +65,7 @@ class ServeCounters(ctypes.Structure):
 
 
 class ProfileStats(ctypes.Structure):
+    """gedwalk_profile_stats: launch count and event-timed sweep launches."""
     _fields_ = [
         ("launches", ctypes.c_int64),
         ("sweep_launches", ctypes.c_int64),
@@ -78,6 +82,7 @@ class ProfileStats(ctypes.Structure):
 
 
 class Params(ctypes.Structure):
+    """gedwalk_params, field for field; build one with make_params()."""
     _fields_ = [
         ("alpha", ctypes.c_double),
         ("epsilon", ctypes.c_double),
@@ -190,6 +195,9 @@ def make_params(alpha: float = 0.0, epsilon: float = 1e-4, L: int = 0, precision
                 eps_rule: str = "over_k", gains_all: bool = False, stream: int = 0, stochastic: bool = False,
                 eta: float = 0.1, seed: int = 0, adaptive: bool = False, bound: str = "combinatorial",
                 lookahead: int = 0, spec_cols: int = 0, device_loop: bool = False) -> Params:
+    """gedwalk_params from keywords: precision "fp32"/"fp64", eps_rule "over_k"/"plain", bound
+    "combinatorial"/"spectral", the flags as booleans; 0 keeps the library's default (alpha
+    1/(1+d_max), L from the bound, lookahead 7 in FP32 and 3 in FP64)."""
     p = Params()
     load().gedwalk_params_default(ctypes.byref(p))
     p.alpha = alpha
@@ -250,6 +258,7 @@ def profile(enable: bool = True):
 
 
 def profile_read() -> dict:
+    """Waits for the timed sweep launches and returns gedwalk_profile_stats as a dict."""
     st = ProfileStats()
     _check(load().gedwalk_profile_read(ctypes.byref(st)))
     return {"launches": st.launches, "sweep_launches": st.sweep_launches, "sweep_ms": st.sweep_ms,
@@ -295,14 +304,17 @@ class Graph:
 
     @classmethod
     def from_host(cls, g, trusted: bool = False, weighted: bool = False, vertex_scale=None, directed: bool = False):
+        """Uploads a host graph with row_ptr / col_idx arrays (such as graphgen's)."""
         return cls(g.row_ptr, g.col_idx, trusted=trusted, weighted=weighted, vertex_scale=vertex_scale,
                    directed=directed)
 
     @property
     def handle(self):
+        """The gedwalk_graph_t (ctypes.c_void_p)."""
         return self._h
 
     def free(self):
+        """Releases the graph's device memory (gedwalk_graph_free); later calls on it fail."""
         if getattr(self, "_h", None) is not None and self._h.value:
             load().gedwalk_graph_free(self._h)
             self._h = None
@@ -392,6 +404,7 @@ class Graph:
         return grp[:k].copy(), gains[:k].copy(), score.value, L.value
 
     def maximize_stats(self):
+        """Counters of the last maximize: evaluations, batches, sweeps, spec_misses."""
         vals = [ctypes.c_int64() for _ in range(4)]
         _check(load().gedwalk_maximize_stats(self._h, *[ctypes.byref(v) for v in vals]))
         return dict(zip(("evaluations", "batches", "sweeps", "spec_misses"), (v.value for v in vals)))
@@ -434,6 +447,7 @@ class Server:
         self._kmax = {}
 
     def submit_score(self, graph: int, S, params: Optional[Params] = None, **kw) -> int:
+        """Queues the scoring of group S on graph index `graph`; returns its ticket."""
         p = params or make_params(**kw)
         s = _i32(S)
         t = ctypes.c_uint64()
@@ -443,6 +457,7 @@ class Server:
         return t.value
 
     def submit_maximize(self, graph: int, k: int, params: Optional[Params] = None, **kw) -> int:
+        """Queues a greedy maximisation of size k on graph index `graph`; returns its ticket."""
         p = params or make_params(**kw)
         t = ctypes.c_uint64()
         dummy = np.zeros(1, np.int32)
@@ -472,6 +487,7 @@ class Server:
         return {name: getattr(c, name) for name, _ in ServeCounters._fields_}
 
     def close(self):
+        """Stops the server (gedwalk_serve_destroy): admitted requests finish, waiting ones end BUSY."""
         if getattr(self, "_h", None) is not None and self._h.value:
             load().gedwalk_serve_destroy(self._h)
             self._h = None
