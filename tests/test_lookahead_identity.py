@@ -63,8 +63,8 @@ def _recurrence(A, S, cand, L):
         t = T[-1].copy()
         t[c] = True
         T.append(t)
-    m = (~inS).astype(np.int64)
-    z = np.zeros((D + 1, n), dtype=np.int64)
+    m = (~inS).astype(A.dtype)  # integer counts, or weighted sums for a weighted matrix
+    z = np.zeros((D + 1, n), dtype=A.dtype)
     for j, c in enumerate(cand, start=1):
         z[j, c] = 1
     out = []
@@ -112,3 +112,38 @@ def test_guess_adjacent_to_earlier_guess_and_star_centre():
         levels, zr = rec[i - 1]
         assert np.array_equal(levels, miss) and np.array_equal(zr[1:], z[1:]), i
         assert miss[1][1] == 0 and miss[1][2] == 0  # under S + {centre} no walk of length >= 1 remains
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_levels_of_weighted_walks(seed):
+    # Section 5.4's weighted walks with w(v,u) = s_v s_u: a walk counts with the product of its
+    # entry weights. The partition by the first guess visited is the same, so the identity and
+    # the recurrences hold for the weighted sums; the sweeps apply them to true values.
+    g = gg.random_graph_small(6, 0.6, 10 + seed)
+    A = _adj(g)
+    rng = np.random.default_rng(seed)
+    s = rng.uniform(0.2, 1.0, g.n)
+    W = A * np.outer(s, s)
+    perm = rng.permutation(g.n)
+    S, cand = [int(perm[0])], [int(x) for x in perm[1:4]]
+    n, D, L = g.n, len(cand), 4
+    for i in range(1, L + 1):
+        miss = np.zeros((D + 1, n))
+        z = np.zeros((D + 1, n))
+        for w in _walks(A, i):
+            if set(S) & set(w):
+                continue
+            wt = np.prod([W[w[t], w[t + 1]] for t in range(i)])
+            first = next((j for j, c in enumerate(cand, start=1) if c in w), None)
+            for d in range(D + 1):
+                if first is None or first > d:
+                    miss[d, w[-1]] += wt
+            if first is not None:
+                z[first, w[-1]] += wt
+        for d in range(D + 1):
+            assert np.allclose(miss[d], miss[0] - z[1:d + 1].sum(axis=0), rtol=1e-12, atol=1e-15), (i, d)
+    # the recurrence with weights as coefficients (W in place of A) gives the enumerated sums
+    rec = _recurrence(W, S, cand, L)
+    levels, zr = rec[L - 1]
+    assert np.allclose(levels, miss, rtol=1e-12, atol=1e-15)
+    assert np.allclose(zr[1:], z[1:], rtol=1e-12, atol=1e-15)
